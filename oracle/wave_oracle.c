@@ -1,0 +1,197 @@
+/*
+ * FP64 CPU oracle for the time-stepped 3D acoustic wave update.
+ *
+ * TEST INFRASTRUCTURE ONLY. Nothing in the product path may link, load or
+ * call this file; only the tests, the package smoke check and the CPU
+ * baseline leg of the benchmark do. It shares no code, header, table or
+ * constant with the CUDA library.
+ *
+ * What it computes (plain definition, no blocking, no fusion):
+ *
+ *   Eq. 1 (Sec. 2): the 25-point, radius-4 star approximation of the
+ *   Laplacian,
+ *       L u(i,j,k) = sum_{m=0..4} c_xm [u(i+m,j,k) + u(i-m,j,k)]
+ *                               + c_ym [u(i,j+m,k) + u(i,j-m,k)]
+ *                               + c_zm [u(i,j,k+m) + u(i,j,k-m)]
+ *   with c_am = w_m / h_a^2 for m >= 1. The m = 0 term of Eq. 1 adds the
+ *   centre twice, so c_a0 = w_0 / (2 h_a^2). The w_m are the 8th-order
+ *   central second-derivative weights (-205/72, 8/5, -1/5, 8/315, -1/560);
+ *   the paper calls them only "discretization parameters" and gives R = 4
+ *   (Sec. 4.1).
+ *
+ *   Sec. 2 applies Eq. 1 at every grid point once per time iteration to
+ *   advance the acoustic isotropic wave equation u_tt = v^2 lap(u). The
+ *   paper does not print the time update; the oracle uses the second-order
+ *   leapfrog
+ *       u_next = 2 u - u_prev + v^2 dt^2 L u,
+ *   then adds the point source  u_next[src] += v^2[src] dt^2 s(t_n),
+ *   t_n = (step0 + n) dt, with the Ricker wavelet
+ *       s(t) = amp (1 - 2 pi^2 f^2 (t - t0)^2) exp(-pi^2 f^2 (t - t0)^2),
+ *   then records  traces[n][r] = u_next[rec_r], then rotates the fields.
+ *
+ *   Boundary: points outside the nx*ny*nz interior read as zero (zero
+ *   Dirichlet halo of width R = 4). The paper's CPML layer (Sec. 2, Sec. 4.1)
+ *   is not part of this path. A periodic mode wraps indices instead; it exists
+ *   only so the tests can check dispersion and energy on Fourier modes.
+ *
+ * Layout: x fastest, then y, then z (Sec. 4.1 stores the grid as a flat 1D
+ * array with X innermost); index (k*ny + j)*nx + i.
+ *
+ * Pins (tests/test_oracle_pins.py): weights from an exact rational solve,
+ * polynomial exactness up to degree 9 and the predicted degree-10 error,
+ * 8th-order convergence, the exact discrete dispersion relation, the
+ * stability limit, discrete energy conservation, mirror symmetry, Ricker
+ * closed-form values, and a dense-matrix brute force on tiny grids.
+ */
+#include <math.h>
+#include <stddef.h>
+#include <stdint.h>
+#include <stdlib.h>
+#include <string.h>
+
+#define ORACLE_R 4
+
+static const double ORACLE_W[ORACLE_R + 1] = {
+    -205.0 / 72.0, 8.0 / 5.0, -1.0 / 5.0, 8.0 / 315.0, -1.0 / 560.0};
+
+void oracle_weights(double *w) {
+  for (int m = 0; m <= ORACLE_R; m++) w[m] = ORACLE_W[m];
+}
+
+/* Value of u at (i,j,k); zero outside the interior unless periodic. */
+static double oracle_at(const double *u, int nx, int ny, int nz, int i, int j,
+                        int k, int periodic) {
+  if (periodic) {
+    i = ((i % nx) + nx) % nx;
+    j = ((j % ny) + ny) % ny;
+    k = ((k % nz) + nz) % nz;
+  } else if (i < 0 || i >= nx || j < 0 || j >= ny || k < 0 || k >= nz) {
+    return 0.0;
+  }
+  return u[((size_t)k * ny + j) * nx + i];
+}
+
+/* The Eq. 1 coefficients c_am for one axis of spacing h. */
+static void oracle_axis_coeffs(double h, double *c) {
+  c[0] = ORACLE_W[0] / (2.0 * h * h);
+  for (int m = 1; m <= ORACLE_R; m++) c[m] = ORACLE_W[m] / (h * h);
+}
+
+/* Eq. 1 at one point. */
+static double oracle_lap_point(const double *u, int nx, int ny, int nz,
+                               int i, int j, int k, const double *cx,
+                               const double *cy, const double *cz,
+                               int periodic) {
+  double s = 0.0;
+  for (int m = 0; m <= ORACLE_R; m++) {
+    s += cx[m] * (oracle_at(u, nx, ny, nz, i + m, j, k, periodic) +
+                  oracle_at(u, nx, ny, nz, i - m, j, k, periodic));
+    s += cy[m] * (oracle_at(u, nx, ny, nz, i, j + m, k, periodic) +
+                  oracle_at(u, nx, ny, nz, i, j - m, k, periodic));
+    s += cz[m] * (oracle_at(u, nx, ny, nz, i, j, k + m, periodic) +
+                  oracle_at(u, nx, ny, nz, i, j, k - m, periodic));
+  }
+  return s;
+}
+
+/* out = L u over the whole interior (Eq. 1). */
+void oracle_laplacian(int nx, int ny, int nz, double dx, double dy, double dz,
+                      const double *u, double *out, int periodic) {
+  double cx[ORACLE_R + 1], cy[ORACLE_R + 1], cz[ORACLE_R + 1];
+  oracle_axis_coeffs(dx, cx);
+  oracle_axis_coeffs(dy, cy);
+  oracle_axis_coeffs(dz, cz);
+#pragma omp parallel for schedule(static)
+  for (int k = 0; k < nz; k++)
+    for (int j = 0; j < ny; j++)
+      for (int i = 0; i < nx; i++)
+        out[((size_t)k * ny + j) * nx + i] =
+            oracle_lap_point(u, nx, ny, nz, i, j, k, cx, cy, cz, periodic);
+}
+
+/* Ricker wavelet with peak frequency f, centred at t0, amplitude amp. */
+double oracle_ricker(double t, double f, double t0, double amp) {
+  const double pi = 3.14159265358979323846;
+  double a = pi * pi * f * f * (t - t0) * (t - t0);
+  return amp * (1.0 - 2.0 * a) * exp(-a);
+}
+
+/*
+ * Leapfrog stability limit of the scheme (von Neumann). The Fourier symbol
+ * of L is  -sum_a (1/h_a^2) (-w0 - 2 sum_m w_m cos(m theta_a));  its largest
+ * magnitude is reached at theta_a = pi on every axis, where it equals
+ * S * sum_a 1/h_a^2 with S = |w0| + 2 sum_m |w_m| (the weights alternate in
+ * sign). The recurrence u_next = 2u - u_prev - v^2 dt^2 K u stays bounded
+ * while v^2 dt^2 K <= 4, so dt_max = 2 / (vmax sqrt(S sum_a 1/h_a^2)).
+ */
+double oracle_cfl_dt(double dx, double dy, double dz, double vmax) {
+  double s = fabs(ORACLE_W[0]);
+  for (int m = 1; m <= ORACLE_R; m++) s += 2.0 * fabs(ORACLE_W[m]);
+  double inv = 1.0 / (dx * dx) + 1.0 / (dy * dy) + 1.0 / (dz * dz);
+  return 2.0 / (vmax * sqrt(s * inv));
+}
+
+/*
+ * Advance the state (u, u_prev) by nsteps leapfrog steps.
+ *
+ *   vel       nx*ny*nz velocities (m/s)
+ *   u, u_prev nx*ny*nz fields at steps step0 and step0-1; on return they
+ *             hold steps step0+nsteps and step0+nsteps-1
+ *   src       if has_source, the Ricker source at (sx,sy,sz) with peak
+ *             frequency f, delay t0 and amplitude amp; if wavelet is not
+ *             NULL it replaces the Ricker values: s(t_n) = wavelet[n]
+ *   rec       nrec*3 int32 (x,y,z) receiver positions; traces is nsteps*nrec
+ *   periodic  wrap indices instead of the zero halo (tests only)
+ *
+ * Returns 0, or -1 on invalid input or allocation failure.
+ */
+int oracle_propagate(int nx, int ny, int nz, double dx, double dy, double dz,
+                     double dt, const double *vel, double *u, double *u_prev,
+                     int64_t step0, int nsteps, int has_source, int sx, int sy,
+                     int sz, double f, double t0, double amp,
+                     const double *wavelet, const int32_t *rec, int nrec,
+                     double *traces, int periodic) {
+  if (nx < 1 || ny < 1 || nz < 1 || nsteps < 0) return -1;
+  size_t n = (size_t)nx * ny * nz;
+  double *c = (double *)malloc(n * sizeof(double));
+  double *unext = (double *)malloc(n * sizeof(double));
+  if (!c || !unext) {
+    free(c);
+    free(unext);
+    return -1;
+  }
+  for (size_t p = 0; p < n; p++) c[p] = vel[p] * vel[p] * dt * dt;
+  double cx[ORACLE_R + 1], cy[ORACLE_R + 1], cz[ORACLE_R + 1];
+  oracle_axis_coeffs(dx, cx);
+  oracle_axis_coeffs(dy, cy);
+  oracle_axis_coeffs(dz, cz);
+
+  for (int s = 0; s < nsteps; s++) {
+#pragma omp parallel for schedule(static)
+    for (int k = 0; k < nz; k++)
+      for (int j = 0; j < ny; j++)
+        for (int i = 0; i < nx; i++) {
+          size_t p = ((size_t)k * ny + j) * nx + i;
+          double lap =
+              oracle_lap_point(u, nx, ny, nz, i, j, k, cx, cy, cz, periodic);
+          unext[p] = 2.0 * u[p] - u_prev[p] + c[p] * lap;
+        }
+    if (has_source) {
+      size_t ps = ((size_t)sz * ny + sy) * nx + sx;
+      double t = (double)(step0 + s) * dt;
+      double w = wavelet ? wavelet[s] : oracle_ricker(t, f, t0, amp);
+      unext[ps] += c[ps] * w;
+    }
+    for (int r = 0; r < nrec; r++) {
+      size_t pr = ((size_t)rec[3 * r + 2] * ny + rec[3 * r + 1]) * nx +
+                  rec[3 * r + 0];
+      traces[(size_t)s * nrec + r] = unext[pr];
+    }
+    /* rotate: u_prev <- u, u <- u_next (copies keep the caller's buffers) */
+    memcpy(u_prev, u, n * sizeof(double));
+    memcpy(u, unext, n * sizeof(double));
+  }
+  free(c);
+  free(unext);
+  return 0;
+}
