@@ -1,0 +1,378 @@
+"""Benchmark of the FP32 wave stepper on one GB300 (or N independent replicas).
+
+One bench step = one time step of the whole hot path (Eq. 1 Laplacian +
+leapfrog update + Ricker source injection + receiver sampling) over the
+1024 x 1024 x 512 random 8-layer workload; K steps are one call of
+wave_propagate. The metric is Gpts/s = interior points x steps / time.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+                  [--workload 1024x1024x512|512cube|64cube]
+
+Prints one JSON line (rank 0). See the printed keys: value (device-timed,
+inputs resident in HBM), e2e (host buffers through the C ABI, copies inside
+the timed region), roofline of the sweep kernel, cpu_baseline (the FP64
+oracle on this machine's host cores over a bounded sample), clocks.
+"""
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+import workloads as wl  # noqa: E402
+
+METRIC = ("Gpts/s & % HBM roofline (r=4 3D wave, FP32 vs BF16 store); "
+          "serve p50/p99 latency")
+BYTES_PER_POINT = 16  # FP32: read u, u_prev, v^2dt^2, write u_next
+WORKLOADS = {"1024x1024x512": wl.CFG_1024, "512cube": wl.CFG_512, "64cube": wl.CFG_SMALL}
+KERNEL_SOURCES = ["paper_2404_04441_gb300/csrc/sweep.cuh", "paper_2404_04441_gb300/csrc/ptx.cuh"]
+TRAFFIC_FILE = "profiles/sweep_f32_traffic.txt"
+GRAPH_STEPS = 32
+
+
+def kernel_hash():
+    h = hashlib.sha256()
+    for p in KERNEL_SOURCES:
+        with open(os.path.join(ROOT, p), "rb") as f:
+            h.update(f.read())
+    return h.hexdigest()[:16]
+
+
+def read_traffic(workload_name):
+    """Per-launch DRAM bytes of the sweep kernel from the committed ncu summary,
+    or None if absent or taken on different kernel sources."""
+    path = os.path.join(ROOT, TRAFFIC_FILE)
+    if not os.path.exists(path):
+        return None
+    vals = {}
+    for line in open(path):
+        if ":" in line and not line.startswith("#"):
+            k, v = line.split(":", 1)
+            vals[k.strip()] = v.strip()
+    if vals.get("kernel_source_sha256_16") != kernel_hash():
+        return None
+    key = "dram_bytes_per_launch[%s]" % workload_name
+    return float(vals[key]) if key in vals else None
+
+
+def measured_peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(path):
+        with open(path) as f:
+            return json.load(f), "measured"
+    return {"hbm_gbs": 6800.0}, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi sampling of SM clocks and throttle reasons during a region."""
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.gpu = gpu_index
+        self.proc = None
+        self.lines = []
+        self.thread = None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.gpu), "--query-gpu=" + self.FIELDS,
+                 "--format=csv,noheader,nounits", "-lms", "100"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except (OSError, ValueError):
+            self.proc = None
+            return
+        self.thread = threading.Thread(target=self._read, daemon=True)
+        self.thread.start()
+        time.sleep(0.3)
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append((time.time(), line.strip()))
+
+    def stop(self):
+        if self.proc is None:
+            return
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        if self.thread:
+            self.thread.join(timeout=2)
+
+    def summary(self, t0, t1):
+        sm, smax, power, reasons = [], [], [], set()
+        names = ("hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap")
+        for ts, line in self.lines:
+            if not (t0 <= ts <= t1):
+                continue
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                smax.append(float(parts[2]))
+                power.append(float(parts[3]))
+            except ValueError:
+                continue
+            for name, val in zip(names, parts[5:9]):
+                if val.lower() == "active":
+                    reasons.add(name)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": [], "samples": 0}
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(smax),
+                "power_w_max": max(power), "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def dist_env():
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return rank, world, local
+
+
+def oracle_sample(vel, cfg, dt, budget_s, nsteps_cap=None):
+    """Time the FP64 oracle on z-slabs of the workload (full x-y extent), growing
+    the slab until one call takes a meaningful share of budget_s. Returns
+    (Gpts/s, cores, sample description, seconds)."""
+    import oracle
+    nx, ny, nz = cfg["shape"]
+    sp = cfg["spacing"]
+    shot = (*cfg["source"], cfg["f_peak"], -1.0, 1.0)
+    planes = 4
+    rng = np.random.default_rng(5)
+    while True:
+        sl = vel[:planes]
+        u0 = rng.uniform(-1, 1, size=sl.shape)
+        up0 = rng.uniform(-1, 1, size=sl.shape)
+        src = shot if shot[2] < planes else None
+        t = time.perf_counter()
+        oracle.propagate(sl, sp, dt, 1, u=u0, u_prev=up0, source=src)
+        el = time.perf_counter() - t
+        if el * 4 >= budget_s or planes >= nz:
+            break
+        planes = min(nz, planes * 2)
+    steps = max(1, int(budget_s / max(el, 1e-6)))
+    if nsteps_cap:
+        steps = min(steps, nsteps_cap)
+    t = time.perf_counter()
+    oracle.propagate(sl, sp, dt, steps, u=u0, u_prev=up0, source=src)
+    el = time.perf_counter() - t
+    pts = nx * ny * planes * steps
+    sample = "%dx%dx%d slab (z = 0..%d) of the workload, %d oracle steps from a random state" % (
+        nx, ny, planes, planes - 1, steps)
+    return pts / el / 1e9, oracle.threads_used(), sample, el
+
+
+def run_reference(args, cfg):
+    """The reference arm: the FP64 CPU oracle on this machine's host cores."""
+    rank, world, _ = dist_env()
+    if rank != 0:
+        return 0
+    import oracle
+    nx, ny, nz = cfg["shape"]
+    vel = wl.velocity_for(cfg)
+    sp = cfg["spacing"]
+    dt = cfg["cfl_fraction"] * oracle.cfl_dt(sp, float(vel.max()))
+    total_budget = 150.0
+    per_step = total_budget / max(1, args.steps + args.warmup)
+    # size a slab so one oracle step takes about per_step seconds
+    planes = 1
+    rng = np.random.default_rng(5)
+    u = rng.uniform(-1, 1, size=(planes, ny, nx))
+    t = time.perf_counter()
+    oracle.propagate(vel[:1], sp, dt, 1, u=u, u_prev=u)
+    one = time.perf_counter() - t
+    planes = int(max(1, min(nz, per_step / max(one, 1e-6))))
+    sl = vel[:planes]
+    u = rng.uniform(-1, 1, size=sl.shape)
+    up = rng.uniform(-1, 1, size=sl.shape)
+    src = (*cfg["source"], cfg["f_peak"], -1.0, 1.0) if cfg["source"][2] < planes else None
+    for _ in range(args.warmup):
+        u, up, _ = oracle.propagate(sl, sp, dt, 1, u=u, u_prev=up, source=src)
+    t = time.perf_counter()
+    for _ in range(args.steps):
+        u, up, _ = oracle.propagate(sl, sp, dt, 1, u=u, u_prev=up, source=src)
+    el = time.perf_counter() - t
+    pts = nx * ny * planes
+    value = pts * args.steps / el / 1e9
+    sample = "%dx%dx%d slab of the workload per step" % (nx, ny, planes)
+    cores = oracle.threads_used()
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": "Gpts/s",
+        "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": el / args.steps * 1e3, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": cfg["name"], "grid": list(cfg["shape"]),
+                   "sample": sample},
+        "cpu_baseline": {"value": value, "unit": "Gpts/s", "cores": cores, "kind": "oracle",
+                         "sample": sample},
+        "e2e": {"value": value, "unit": "Gpts/s", "h2d_bytes_per_step": 0,
+                "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=1000)
+    ap.add_argument("--warmup", type=int, default=10)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default="1024x1024x512", choices=sorted(WORKLOADS))
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--variant", type=int, default=None, help="sweep kernel variant (tuning)")
+    args = ap.parse_args()
+    args.warmup = max(args.warmup, 3)
+    cfg = WORKLOADS[args.workload]
+    if args.impl == "reference":
+        return run_reference(args, cfg)
+    if args.variant is not None:
+        os.environ["GBWAVE_VARIANT"] = str(args.variant)
+
+    import torch
+    import paper_2404_04441_gb300 as gw
+
+    rank, world, local = dist_env()
+    if not torch.cuda.is_available():
+        raise RuntimeError("bench.py needs a CUDA device")
+    torch.cuda.set_device(local)
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    gw.load()
+
+    nx, ny, nz = cfg["shape"]
+    npts = nx * ny * nz
+    sp = cfg["spacing"]
+    vel = wl.velocity_for(cfg)
+    dt = cfg["cfl_fraction"] * gw.wave_cfl_dt(sp, float(vel.max()))
+    rec = wl.receiver_plane(nx, ny, cfg["rec_z"], cfg["rec_stride"])
+    nrec = rec.shape[0]
+    shot = (*cfg["source"], cfg["f_peak"], -1.0, 1.0)
+    K, W = args.steps, args.warmup
+
+    stream = torch.cuda.current_stream()
+    vel_d = torch.from_numpy(vel).cuda()
+    rec_d = torch.from_numpy(rec).cuda()
+    traces_d = torch.empty((max(K, W), nrec), dtype=torch.float32, device="cuda")
+    solver = gw.WaveSolver((nx, ny, nz), sp, dt, vel_d, stream=stream.cuda_stream)
+    info = solver.launch_info()
+
+    def barrier():
+        if world > 1:
+            torch.distributed.barrier()
+
+    # ---- device-resident timing -------------------------------------------------
+    solver.propagate(shot, W, rec_d, traces_d)
+    solver.synchronize()
+    solver.reset()
+    sampler = ClockSampler(local)
+    sampler.start()
+    barrier()
+    torch.cuda.synchronize()
+    ev0 = torch.cuda.Event(enable_timing=True)
+    ev1 = torch.cuda.Event(enable_timing=True)
+    tw0 = time.time()
+    ev0.record(stream)
+    solver.propagate(shot, K, rec_d, traces_d)
+    ev1.record(stream)
+    ev1.synchronize()
+    tw1 = time.time()
+    barrier()
+    torch.cuda.synchronize()
+    sampler.stop()
+    solver.synchronize()
+    ms = ev0.elapsed_time(ev1)
+    if world > 1:
+        t = torch.tensor([ms], device="cuda")
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        ms = float(t.item())
+    clocks = sampler.summary(tw0, tw1)
+    value = world * npts * K / (ms * 1e-3) / 1e9
+    launches = (K // GRAPH_STEPS) * (GRAPH_STEPS + 1) + ((K % GRAPH_STEPS) + 1 if K % GRAPH_STEPS else 0)
+    tr_ok = bool(torch.isfinite(traces_d[:K]).all().item())
+    solver.close()
+    del traces_d
+
+    # ---- end to end through the C ABI with host buffers -------------------------
+    e2e = None
+    if not args.no_e2e:
+        vel_h = torch.from_numpy(vel).pin_memory()
+        rec_h = torch.from_numpy(rec).pin_memory()
+        tr_h = torch.empty((K, nrec), dtype=torch.float32).pin_memory()
+        barrier()
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        s2 = gw.WaveSolver((nx, ny, nz), sp, dt, vel_h, stream=stream.cuda_stream)
+        s2.propagate(shot, K, rec_h, tr_h)
+        s2.close()
+        torch.cuda.synchronize()
+        el = time.perf_counter() - t0
+        if world > 1:
+            t = torch.tensor([el], device="cuda")
+            torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+            el = float(t.item())
+        e2e = {"value": world * npts * K / el / 1e9, "unit": "Gpts/s",
+               "h2d_bytes_per_step": (vel.nbytes + rec.nbytes) / K,
+               "d2h_bytes_per_step": nrec * 4,
+               "note": "wave_create(host velocity) + wave_propagate(host receivers, "
+                       "host traces) + wave_destroy, all K steps"}
+
+    # ---- roofline of the sweep kernel -------------------------------------------
+    peaks, peak_kind = measured_peaks()
+    per_launch_s = ms * 1e-3 / K
+    achieved = BYTES_PER_POINT * npts / per_launch_s / 1e9
+    roofline = {"bound": "hbm", "achieved": achieved, "peak": peaks["hbm_gbs"], "unit": "GB/s",
+                "frac": achieved / peaks["hbm_gbs"], "traffic": read_traffic(cfg["name"]),
+                "peak_kind": peak_kind + " (MEASURED_PEAKS.json hbm_gbs)" if peak_kind == "measured"
+                else "fallback",
+                "algorithmic_bytes_per_launch": BYTES_PER_POINT * npts,
+                "kernel": "wave_sweep_kernel"}
+
+    cpu = None
+    if rank == 0 and not args.no_cpu_baseline:
+        g, cores, sample, el = oracle_sample(vel, cfg, dt, budget_s=15.0)
+        cpu = {"value": g, "unit": "Gpts/s", "cores": cores, "kind": "oracle",
+               "sample": sample, "seconds": round(el, 2)}
+
+    if world > 1:
+        torch.distributed.barrier()
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": value, "unit": "Gpts/s", "n_gpus": world,
+            "steps": K, "warmup": W, "ms_per_step": ms / K, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": cfg["name"], "grid": [nx, ny, nz], "spacing_m": list(sp),
+                       "dt_s": dt, "nsteps_timed": K, "receivers": nrec,
+                       "source": list(cfg["source"]), "f_peak_hz": cfg["f_peak"],
+                       "parallelism": "replicas" if world > 1 else "single",
+                       "l2": "inputs larger than L2 (16 B/pt x %d pts = %.2f GB per step)"
+                             % (npts, BYTES_PER_POINT * npts / 1e9),
+                       "launch": info},
+            "e2e": e2e, "gpu_launches": launches, "roofline": roofline,
+            "cpu_baseline": cpu, "clocks": clocks, "traces_finite": tr_ok,
+        }
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        torch.distributed.destroy_process_group()
+    return 0
+
+
+if __name__ == "__main__":
+    sys.exit(main())

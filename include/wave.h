@@ -1,0 +1,169 @@
+/*
+ * gbwave: time-stepped 3D acoustic wave propagation on one GB300 (sm_103a).
+ *
+ * The operation (Sec. 2, Eq. 1; Sec. 4.1 for R = 4 and the x-innermost
+ * layout): at every interior grid point and every time step,
+ *
+ *     L u = sum_{a in x,y,z} (1/h_a^2) ( w0 u + sum_{m=1..4} w_m (u(+m e_a) + u(-m e_a)) )
+ *     u_next = 2 u - u_prev + v^2 dt^2 L u                 (second-order leapfrog)
+ *
+ * with w = (-205/72, 8/5, -1/5, 8/315, -1/560) (Eq. 1's c_am = w_m / h_a^2;
+ * its m = 0 term counts the centre twice, c_a0 = w0 / (2 h_a^2)). Points
+ * outside the interior read as zero (zero Dirichlet halo of width 4); the
+ * paper's CPML layer (Sec. 2) is not implemented here. After the update of
+ * step n a Ricker point source adds v^2 dt^2 s(t_n) at the source point,
+ * t_n = n dt, s(t) = amp (1 - 2 pi^2 f^2 (t-t0)^2) exp(-pi^2 f^2 (t-t0)^2),
+ * and every receiver records u_next at its point.
+ *
+ * Conventions shared by every entry point:
+ *  - Grids are interior points only, x fastest, then y, then z (z = depth).
+ *    Dense user arrays are nx*ny*nz float32 with index (k*ny + j)*nx + i.
+ *  - Pointers may be host or device memory; the library asks the CUDA runtime
+ *    which (cudaPointerGetAttributes). A call that reads a host buffer has
+ *    finished reading it when it returns; a call that writes a host buffer
+ *    returns after the data is there (it synchronizes the context's stream).
+ *    Calls that touch device buffers only are asynchronous on that stream.
+ *  - The caller owns every buffer it passes; the context owns the wavefields
+ *    and its internal tables and frees them in wave_destroy.
+ *  - All work is enqueued on the stream given to wave_create (a cudaStream_t,
+ *    NULL = the legacy default stream). A context is not thread-safe;
+ *    separate contexts are independent.
+ *  - Functions return WAVE_OK (0) or a negative status; none aborts. Inputs
+ *    are validated before anything is launched.
+ *  - Device-side waits are bounded: a kernel whose copy pipeline stalls for
+ *    about two seconds records WAVE_ETIMEOUT, which the next synchronizing
+ *    call (wave_synchronize, wave_get_field to host, ...) returns.
+ */
+#ifndef GBWAVE_WAVE_H
+#define GBWAVE_WAVE_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+enum {
+  WAVE_OK = 0,
+  WAVE_EINVAL = -1,    /* bad argument (sizes, positions, pointers, NaN or v <= 0) */
+  WAVE_ENOMEM = -2,    /* device allocation failed */
+  WAVE_ECUDA = -3,     /* a CUDA runtime/driver call failed */
+  WAVE_EUNSTABLE = -4, /* dt above the leapfrog stability limit (wave_cfl_dt) */
+  WAVE_ETIMEOUT = -5,  /* a bounded device wait gave up */
+  WAVE_EBUSY = -6,     /* result not ready yet */
+  WAVE_ENAN = -7,      /* non-finite values in the output */
+  WAVE_ENOTSUP = -8    /* option not supported by this build */
+};
+
+/* Storage precision of the wavefield (argument of wave_create). */
+enum { WAVE_STORAGE_F32 = 0 };
+
+typedef struct wave_ctx wave_ctx; /* opaque; owns the device wavefields */
+
+typedef struct {
+  int32_t nx, ny, nz; /* interior points per axis, each >= 1 */
+} wave_grid;
+
+typedef struct {
+  double dx, dy, dz; /* grid spacing in metres, each > 0 */
+} wave_spacing;
+
+typedef struct {
+  int32_t sx, sy, sz; /* source point, inside the interior */
+  double f_peak;      /* Ricker peak frequency in Hz (> 0) */
+  double t0;          /* Ricker delay in seconds; t0 < 0 selects 1 / f_peak */
+  double amp;         /* Ricker amplitude */
+} wave_shot;
+
+/*
+ * Largest stable time step of the scheme for velocities up to vmax:
+ * dt_max = 2 / (vmax sqrt(S (1/dx^2 + 1/dy^2 + 1/dz^2))), S = |w0| + 2 sum |w_m|
+ * (von Neumann analysis of the leapfrog recurrence on the highest mode of
+ * Eq. 1). Returns a negative value for invalid arguments.
+ */
+double wave_cfl_dt(const wave_spacing *h, double vmax);
+
+/*
+ * Create a context for one grid and velocity model.
+ *   g, h      grid size and spacing (read during the call)
+ *   dt        time step in seconds; must be in (0, wave_cfl_dt(h, max v)]
+ *   velocity  nx*ny*nz float32 velocities in m/s, dense, x fastest; host or
+ *             device; every value finite and > 0. The context keeps
+ *             v^2 dt^2 (FP32), not the pointer.
+ *   storage   WAVE_STORAGE_F32 (other values: WAVE_ENOTSUP)
+ *   stream    cudaStream_t all work of this context is enqueued on
+ *   out       receives the new context (NULL on failure)
+ * The wavefields start at zero, step counter 0. Returns WAVE_EINVAL,
+ * WAVE_EUNSTABLE, WAVE_ENOMEM, WAVE_ENOTSUP or WAVE_ECUDA on failure.
+ */
+int wave_create(const wave_grid *g, const wave_spacing *h, double dt,
+                const float *velocity, int storage, void *stream,
+                wave_ctx **out);
+
+/* Advance nsteps (>= 0) leapfrog steps with no source and no receivers. */
+int wave_step(wave_ctx *ctx, int nsteps);
+
+/*
+ * Advance nsteps (>= 0) steps with the Ricker source of *shot (NULL: no
+ * source) and record receivers.
+ *   rec_xyz  nrec*3 int32 receiver points (x, y, z), host or device; each
+ *            inside the interior (WAVE_EINVAL otherwise); may repeat
+ *   traces   nsteps*nrec float32, host or device, caller-owned; row n holds
+ *            the receivers after step n of this call (time (step0+n+1) dt,
+ *            step0 = the context's step counter at entry)
+ * The source time of the call's step n is t = (step0 + n) dt.
+ */
+int wave_propagate(wave_ctx *ctx, const wave_shot *shot, int nsteps,
+                   const int32_t *rec_xyz, int nrec, float *traces);
+
+/*
+ * Copy a wavefield out as nx*ny*nz float32 (dense, x fastest).
+ *   which  0 = u at the current step, 1 = u at the previous step
+ */
+int wave_get_field(const wave_ctx *ctx, int which, float *out);
+
+/*
+ * Replace the state: u (current step) and u_prev (previous step), each
+ * nx*ny*nz float32 dense (host or device), and the step counter.
+ */
+int wave_set_state(wave_ctx *ctx, const float *u, const float *u_prev,
+                   int64_t step);
+
+/* Current step counter (number of steps taken since creation/reset/set_state). */
+int wave_get_step(const wave_ctx *ctx, int64_t *step);
+
+/* Zero both wavefields and the step counter. */
+int wave_reset(wave_ctx *ctx);
+
+/* Wait for the context's stream; return any error a kernel recorded. */
+int wave_synchronize(wave_ctx *ctx);
+
+/* Free everything the context owns (waits for its stream first). NULL is a no-op. */
+void wave_destroy(wave_ctx *ctx);
+
+/* Static message for a status code. */
+const char *wave_strerror(int status);
+
+/*
+ * Launch geometry of the stencil sweep for this context (for reports and
+ * benchmarks): CTA tile in x and y, z planes per CTA, grid size, resident
+ * CTAs per SM. Any output pointer may be NULL.
+ */
+int wave_get_launch_info(const wave_ctx *ctx, int *tile_x, int *tile_y,
+                         int *z_chunk, int *grid_ctas, int *ctas_per_sm);
+
+/*
+ * Diagnostic of the bounded device wait used by every kernel of this
+ * library: launches one thread that waits on a shared-memory barrier nothing
+ * arrives on, with a limit of limit_ns nanoseconds (clamped to 1 ms .. 10 s).
+ * Synchronizes the stream. Returns WAVE_ETIMEOUT when the wait gave up as
+ * designed, WAVE_ECUDA if it reported completion or a CUDA call failed.
+ */
+int wave_selftest_wait(int64_t limit_ns, void *stream);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* GBWAVE_WAVE_H */

@@ -10,7 +10,6 @@ this module only marshals numpy arrays. See the header of ``wave_oracle.c``
 for what each function computes and which passage it follows.
 """
 import ctypes
-import os
 
 import numpy as np
 
@@ -40,6 +39,8 @@ def _load():
             + [ctypes.c_int] * 3 + [ctypes.c_double] * 3
             + [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int, ctypes.c_void_p, ctypes.c_int])
         lib.oracle_propagate.restype = ctypes.c_int
+        lib.oracle_threads.argtypes = []
+        lib.oracle_threads.restype = ctypes.c_int
         _lib = lib
     return _lib
 
@@ -125,11 +126,5 @@ def propagate(vel, spacing, dt, nsteps, u=None, u_prev=None, step0=0,
 
 
 def threads_used():
-    """Number of OpenMP threads the oracle runs with (OMP_NUM_THREADS or all cores)."""
-    env = os.environ.get("OMP_NUM_THREADS")
-    if env:
-        try:
-            return int(env.split(",")[0])
-        except ValueError:
-            pass
-    return os.cpu_count() or 1
+    """Number of OpenMP threads the oracle's parallel loops run with."""
+    return int(_load().oracle_threads())

@@ -44,6 +44,9 @@
  * closed-form values, and a dense-matrix brute force on tiny grids.
  */
 #include <math.h>
+#ifdef _OPENMP
+#include <omp.h>
+#endif
 #include <stddef.h>
 #include <stdint.h>
 #include <stdlib.h>
@@ -53,6 +56,15 @@
 
 static const double ORACLE_W[ORACLE_R + 1] = {
     -205.0 / 72.0, 8.0 / 5.0, -1.0 / 5.0, 8.0 / 315.0, -1.0 / 560.0};
+
+/* Number of OpenMP threads the parallel loops run with. */
+int oracle_threads(void) {
+#ifdef _OPENMP
+  return omp_get_max_threads();
+#else
+  return 1;
+#endif
+}
 
 void oracle_weights(double *w) {
   for (int m = 0; m <= ORACLE_R; m++) w[m] = ORACLE_W[m];

@@ -1,0 +1,269 @@
+"""Python binding of the gbwave C ABI (include/wave.h).
+
+Argument marshalling only: every step of the wave update runs in the CUDA
+library ``_build/libgbwave.so``. If that library is missing, ``load()``
+raises; there is no CPU fallback.
+
+Arrays may be torch tensors (CUDA or CPU) or numpy arrays; they are passed to
+the library as raw pointers (``data_ptr()`` / ``ctypes.data``), and the
+library decides from the pointer whether it is host or device memory. The
+CUDA stream defaults to torch's current stream.
+"""
+import ctypes
+import os
+
+__all__ = [
+    "WaveError", "load", "wave_cfl_dt", "wave_create", "wave_step", "wave_propagate",
+    "wave_get_field", "wave_set_state", "wave_get_step", "wave_reset",
+    "wave_synchronize", "wave_destroy", "wave_strerror", "wave_get_launch_info",
+    "wave_selftest_wait", "WaveSolver", "library_path",
+]
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_LIB_PATH = os.path.join(_HERE, "_build", "libgbwave.so")
+_lib = None
+
+WAVE_OK = 0
+STATUS = {0: "WAVE_OK", -1: "WAVE_EINVAL", -2: "WAVE_ENOMEM", -3: "WAVE_ECUDA",
+          -4: "WAVE_EUNSTABLE", -5: "WAVE_ETIMEOUT", -6: "WAVE_EBUSY", -7: "WAVE_ENAN",
+          -8: "WAVE_ENOTSUP"}
+
+
+class WaveError(RuntimeError):
+    def __init__(self, code, where):
+        self.code = code
+        msg = _lib.wave_strerror(code).decode() if _lib is not None else str(code)
+        super().__init__("%s: %s (%s)" % (where, msg, STATUS.get(code, code)))
+
+
+class _Grid(ctypes.Structure):
+    _fields_ = [("nx", ctypes.c_int32), ("ny", ctypes.c_int32), ("nz", ctypes.c_int32)]
+
+
+class _Spacing(ctypes.Structure):
+    _fields_ = [("dx", ctypes.c_double), ("dy", ctypes.c_double), ("dz", ctypes.c_double)]
+
+
+class _Shot(ctypes.Structure):
+    _fields_ = [("sx", ctypes.c_int32), ("sy", ctypes.c_int32), ("sz", ctypes.c_int32),
+                ("f_peak", ctypes.c_double), ("t0", ctypes.c_double), ("amp", ctypes.c_double)]
+
+
+def library_path():
+    return _LIB_PATH
+
+
+def load(path=None):
+    """Load the CUDA library (raises if it has not been built)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    path = path or _LIB_PATH
+    if not os.path.exists(path):
+        raise RuntimeError(
+            "gbwave CUDA library not found at %s; build it with "
+            "`python -c 'import __graft_entry__ as g; g.build()'`" % path)
+    lib = ctypes.CDLL(path)
+    vp, ip = ctypes.c_void_p, ctypes.c_int
+    lib.wave_cfl_dt.argtypes = [ctypes.POINTER(_Spacing), ctypes.c_double]
+    lib.wave_cfl_dt.restype = ctypes.c_double
+    lib.wave_create.argtypes = [ctypes.POINTER(_Grid), ctypes.POINTER(_Spacing),
+                                ctypes.c_double, vp, ip, vp, ctypes.POINTER(vp)]
+    lib.wave_step.argtypes = [vp, ip]
+    lib.wave_propagate.argtypes = [vp, ctypes.POINTER(_Shot), ip, vp, ip, vp]
+    lib.wave_get_field.argtypes = [vp, ip, vp]
+    lib.wave_set_state.argtypes = [vp, vp, vp, ctypes.c_int64]
+    lib.wave_get_step.argtypes = [vp, ctypes.POINTER(ctypes.c_int64)]
+    lib.wave_reset.argtypes = [vp]
+    lib.wave_synchronize.argtypes = [vp]
+    lib.wave_destroy.argtypes = [vp]
+    lib.wave_destroy.restype = None
+    lib.wave_strerror.argtypes = [ip]
+    lib.wave_strerror.restype = ctypes.c_char_p
+    lib.wave_get_launch_info.argtypes = [vp] + [ctypes.POINTER(ctypes.c_int)] * 5
+    lib.wave_selftest_wait.argtypes = [ctypes.c_int64, vp]
+    for name in ("wave_create", "wave_step", "wave_propagate", "wave_get_field",
+                 "wave_set_state", "wave_get_step", "wave_reset", "wave_synchronize",
+                 "wave_get_launch_info", "wave_selftest_wait"):
+        getattr(lib, name).restype = ctypes.c_int
+    _lib = lib
+    return lib
+
+
+def _check(code, where):
+    if code != WAVE_OK:
+        raise WaveError(code, where)
+
+
+def _ptr(a, dtype_name, count, what):
+    """Raw pointer of a contiguous torch tensor / numpy array with ``count`` elements."""
+    if a is None:
+        return None
+    mod = type(a).__module__
+    if mod.startswith("torch"):
+        import torch
+        want = {"float32": torch.float32, "int32": torch.int32}[dtype_name]
+        if a.dtype != want or not a.is_contiguous():
+            raise ValueError("%s must be a contiguous %s tensor" % (what, dtype_name))
+        if a.numel() < count:
+            raise ValueError("%s has %d elements, needs %d" % (what, a.numel(), count))
+        return a.data_ptr()
+    import numpy as np
+    if not isinstance(a, np.ndarray):
+        raise TypeError("%s must be a torch tensor or numpy array" % what)
+    if a.dtype != np.dtype(dtype_name) or not a.flags["C_CONTIGUOUS"]:
+        raise ValueError("%s must be a C-contiguous %s array" % (what, dtype_name))
+    if a.size < count:
+        raise ValueError("%s has %d elements, needs %d" % (what, a.size, count))
+    if not a.flags["WRITEABLE"] and what in ("traces", "out"):
+        raise ValueError("%s must be writeable" % what)
+    return a.ctypes.data
+
+
+def _default_stream():
+    try:
+        import torch
+        if torch.cuda.is_available():
+            return torch.cuda.current_stream().cuda_stream
+    except ImportError:
+        pass
+    return 0
+
+
+def wave_cfl_dt(spacing, vmax):
+    """Largest stable dt for spacing (dx, dy, dz) and velocity vmax."""
+    lib = load()
+    return lib.wave_cfl_dt(ctypes.byref(_Spacing(*map(float, spacing))), float(vmax))
+
+
+def wave_create(grid, spacing, dt, velocity, storage=0, stream=None):
+    """Create a context; ``grid`` = (nx, ny, nz); velocity has nx*ny*nz float32."""
+    lib = load()
+    nx, ny, nz = map(int, grid)
+    g = _Grid(nx, ny, nz)
+    h = _Spacing(*map(float, spacing))
+    vptr = _ptr(velocity, "float32", nx * ny * nz, "velocity")
+    out = ctypes.c_void_p()
+    st = _default_stream() if stream is None else int(stream)
+    _check(lib.wave_create(ctypes.byref(g), ctypes.byref(h), float(dt), vptr, int(storage),
+                           st, ctypes.byref(out)), "wave_create")
+    return out
+
+
+def wave_step(ctx, nsteps):
+    _check(load().wave_step(ctx, int(nsteps)), "wave_step")
+
+
+def wave_propagate(ctx, shot, nsteps, rec=None, traces=None):
+    """Advance ``nsteps`` with source ``shot`` = (sx, sy, sz, f_peak, t0, amp) or None.
+
+    ``rec``: int32 (nrec, 3) receiver points; ``traces``: float32 (nsteps, nrec) output.
+    """
+    lib = load()
+    if rec is not None and (len(rec.shape) != 2 or rec.shape[1] != 3):
+        raise ValueError("rec must have shape (nrec, 3)")
+    nrec = 0 if rec is None else int(rec.shape[0])
+    rptr = _ptr(rec, "int32", 3 * nrec, "rec") if nrec else None
+    tptr = _ptr(traces, "float32", int(nsteps) * nrec, "traces") if nrec else None
+    sp = None
+    if shot is not None:
+        sx, sy, sz, f, t0, amp = shot
+        sp = ctypes.byref(_Shot(int(sx), int(sy), int(sz), float(f),
+                                -1.0 if t0 is None else float(t0), float(amp)))
+    _check(lib.wave_propagate(ctx, sp, int(nsteps), rptr, int(nrec), tptr), "wave_propagate")
+
+
+def wave_get_field(ctx, which, out, count):
+    _check(load().wave_get_field(ctx, int(which), _ptr(out, "float32", count, "out")),
+           "wave_get_field")
+
+
+def wave_set_state(ctx, u, u_prev, step, count):
+    _check(load().wave_set_state(ctx, _ptr(u, "float32", count, "u"),
+                                 _ptr(u_prev, "float32", count, "u_prev"), int(step)),
+           "wave_set_state")
+
+
+def wave_get_step(ctx):
+    s = ctypes.c_int64()
+    _check(load().wave_get_step(ctx, ctypes.byref(s)), "wave_get_step")
+    return s.value
+
+
+def wave_reset(ctx):
+    _check(load().wave_reset(ctx), "wave_reset")
+
+
+def wave_synchronize(ctx):
+    _check(load().wave_synchronize(ctx), "wave_synchronize")
+
+
+def wave_destroy(ctx):
+    if ctx:
+        load().wave_destroy(ctx)
+
+
+def wave_selftest_wait(limit_ns, stream=None):
+    """Run the bounded-wait self-test; returns the library status (WAVE_ETIMEOUT expected)."""
+    st = _default_stream() if stream is None else int(stream)
+    return load().wave_selftest_wait(int(limit_ns), st)
+
+
+def wave_strerror(code):
+    return load().wave_strerror(int(code)).decode()
+
+
+def wave_get_launch_info(ctx):
+    vals = [ctypes.c_int() for _ in range(5)]
+    _check(load().wave_get_launch_info(ctx, *[ctypes.byref(v) for v in vals]),
+           "wave_get_launch_info")
+    keys = ("tile_x", "tile_y", "z_chunk", "grid_ctas", "ctas_per_sm")
+    return dict(zip(keys, (v.value for v in vals)))
+
+
+class WaveSolver:
+    """Owning wrapper of one context (destroyed with the object)."""
+
+    def __init__(self, grid, spacing, dt, velocity, storage=0, stream=None):
+        self.grid = tuple(int(v) for v in grid)
+        self.spacing = tuple(float(v) for v in spacing)
+        self.dt = float(dt)
+        self.count = self.grid[0] * self.grid[1] * self.grid[2]
+        self.ctx = wave_create(self.grid, self.spacing, self.dt, velocity, storage, stream)
+
+    def step(self, nsteps):
+        wave_step(self.ctx, nsteps)
+
+    def propagate(self, shot, nsteps, rec=None, traces=None):
+        wave_propagate(self.ctx, shot, nsteps, rec, traces)
+
+    def get_field(self, which, out):
+        wave_get_field(self.ctx, which, out, self.count)
+        return out
+
+    def set_state(self, u, u_prev, step=0):
+        wave_set_state(self.ctx, u, u_prev, step, self.count)
+
+    @property
+    def step_count(self):
+        return wave_get_step(self.ctx)
+
+    def reset(self):
+        wave_reset(self.ctx)
+
+    def synchronize(self):
+        wave_synchronize(self.ctx)
+
+    def launch_info(self):
+        return wave_get_launch_info(self.ctx)
+
+    def close(self):
+        if getattr(self, "ctx", None):
+            wave_destroy(self.ctx)
+            self.ctx = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

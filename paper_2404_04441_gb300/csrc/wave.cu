@@ -1,0 +1,682 @@
+// C-ABI implementation of gbwave (declared in include/wave.h): context and
+// buffer management, validation, TMA descriptors, launch geometry, CUDA
+// graphs of the step loop, and the setup kernels.
+#include <cuda.h>
+#include <cuda_runtime.h>
+#include <cudaTypedefs.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstdint>
+#include <cstdio>
+#include <cstdlib>
+#include <cstring>
+#include <new>
+#include <vector>
+
+#include "../../include/wave.h"
+#include "sweep.cuh"
+
+using namespace gbw;
+
+namespace {
+
+// 8th-order central second-derivative weights w_0..w_4 (Eq. 1's
+// discretization parameters, c_am = w_m / h_a^2).
+constexpr double kW[5] = {-205.0 / 72.0, 8.0 / 5.0, -1.0 / 5.0, 8.0 / 315.0,
+                          -1.0 / 560.0};
+
+// Kernel variants (tile x, tile y, rows per thread, prefetch depth, CTAs/SM).
+using CfgA = SweepCfg<64, 16, 1, 4, 2>;
+using CfgB = SweepCfg<64, 16, 2, 4, 2>;
+using CfgC = SweepCfg<64, 32, 2, 4, 1>;
+using CfgD = SweepCfg<32, 16, 1, 4, 3>;
+
+struct Variant {
+  const void *func;
+  int tx, ty, threads;
+  size_t smem;
+  void (*launch)(dim3, cudaStream_t, const CUtensorMap &, const CUtensorMap &,
+                 const CUtensorMap &, const SweepArgs &);
+};
+
+template <class C>
+void launch_sweep(dim3 grid, cudaStream_t st, const CUtensorMap &tu,
+                  const CUtensorMap &tup, const CUtensorMap &tc,
+                  const SweepArgs &a) {
+  wave_sweep_kernel<C><<<grid, C::THREADS, C::SMEM_BYTES, st>>>(tu, tup, tc, a);
+}
+
+template <class C>
+Variant make_variant() {
+  return Variant{reinterpret_cast<const void *>(&wave_sweep_kernel<C>), C::TX,
+                 C::TY, C::THREADS, C::SMEM_BYTES, &launch_sweep<C>};
+}
+
+Variant pick_variant(int which) {
+  switch (which) {
+    case 1: return make_variant<CfgB>();
+    case 2: return make_variant<CfgC>();
+    case 3: return make_variant<CfgD>();
+    default: return make_variant<CfgA>();
+  }
+}
+
+__global__ void advance_kernel(StepDesc *d, int k) { d->n += k; }
+
+// Waits on a barrier no one arrives on; records 2 if the wait gave up.
+__global__ void selftest_wait_kernel(uint64_t limit_ns, int *out) {
+  __shared__ uint64_t bar;
+  mbar_init(&bar, 1);
+  fence_barrier_init();
+  const bool done = mbar_wait_bounded(&bar, 0, limit_ns);
+  *out = done ? 1 : 2;
+}
+
+// Velocity scan over the dense-in-x pitched buffer: max, and count of values
+// that are not finite and positive.
+__global__ void scan_velocity_kernel(const float *v, int nx, int px,
+                                     long long rows, unsigned *vmax_bits,
+                                     unsigned long long *nbad) {
+  unsigned local_max = 0;
+  unsigned long long local_bad = 0;
+  const long long total = rows * (long long)nx;
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+       i < total; i += (long long)gridDim.x * blockDim.x) {
+    const long long r = i / nx;
+    const int x = (int)(i - r * nx);
+    const float val = v[r * px + x];
+    if (!(val > 0.f) || !isfinite(val)) {
+      ++local_bad;
+    } else {
+      local_max = max(local_max, __float_as_uint(val));
+    }
+  }
+  for (int o = 16; o > 0; o >>= 1) {
+    local_max = max(local_max, __shfl_xor_sync(0xffffffffu, local_max, o));
+    local_bad += __shfl_xor_sync(0xffffffffu, local_bad, o);
+  }
+  if ((threadIdx.x & 31) == 0) {
+    atomicMax(vmax_bits, local_max);
+    if (local_bad) atomicAdd(nbad, local_bad);
+  }
+}
+
+// c = v^2 dt^2 in place (FP64 product, rounded once to FP32).
+__global__ void velocity_to_c_kernel(float *c, long long n, double dt2) {
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
+       i += (long long)gridDim.x * blockDim.x) {
+    const double v = c[i];
+    c[i] = (float)(v * v * dt2);
+  }
+}
+
+struct DeviceBuf {
+  void *p = nullptr;
+  size_t cap = 0;
+};
+
+}  // namespace
+
+struct wave_ctx {
+  int nx = 0, ny = 0, nz = 0, px = 0;
+  double dx = 0, dy = 0, dz = 0, dt = 0;
+  cudaStream_t stream = nullptr;
+  cudaStream_t capture_stream = nullptr;
+  int device = 0;
+  float *buf[2] = {nullptr, nullptr};  // buf[cur] = u, buf[cur ^ 1] = u_prev
+  float *c = nullptr;
+  int cur = 0;
+  int64_t step = 0;
+  StepDesc *d_desc = nullptr;
+  void *d_scratch = nullptr;  // 16 bytes for the velocity scan
+  CUtensorMap tm_halo[2], tm_tile[2], tm_c;
+  Variant var{};
+  dim3 grid;
+  int zchunk = 0, ctas_per_sm = 0, ntiles = 0;
+  SweepArgs args{};
+  DeviceBuf wavelet, rec, rec_start, traces;
+  cudaGraphExec_t graph[2] = {nullptr, nullptr};
+  int graph_steps = 32;
+  StepDesc host_desc{};
+  std::vector<int4> h_rec;
+  std::vector<int> h_rec_start;
+  std::vector<float> h_wavelet;
+};
+
+namespace {
+
+int cuda_status(cudaError_t e) {
+  if (e == cudaSuccess) return WAVE_OK;
+  if (e == cudaErrorMemoryAllocation) return WAVE_ENOMEM;
+  return WAVE_ECUDA;
+}
+
+#define WAVE_TRY_CUDA(expr)                         \
+  do {                                              \
+    cudaError_t e_ = (expr);                        \
+    if (e_ != cudaSuccess) return cuda_status(e_);  \
+  } while (0)
+
+bool is_device_ptr(const void *p) {
+  cudaPointerAttributes at;
+  if (cudaPointerGetAttributes(&at, p) != cudaSuccess) {
+    cudaGetLastError();
+    return false;
+  }
+  return at.type == cudaMemoryTypeDevice || at.type == cudaMemoryTypeManaged;
+}
+
+int ensure(DeviceBuf &b, size_t bytes, cudaStream_t st) {
+  if (b.cap >= bytes) return WAVE_OK;
+  if (b.p) {
+    // Work queued earlier may still read the old buffer.
+    WAVE_TRY_CUDA(cudaStreamSynchronize(st));
+    cudaFree(b.p);
+    b.p = nullptr;
+    b.cap = 0;
+  }
+  size_t cap = std::max<size_t>(bytes, 256);
+  WAVE_TRY_CUDA(cudaMalloc(&b.p, cap));
+  b.cap = cap;
+  return WAVE_OK;
+}
+
+PFN_cuTensorMapEncodeTiled_v12000 get_encode() {
+  static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
+  if (!fn) {
+    void *p = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000,
+                                         cudaEnableDefault, &q) == cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      fn = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(p);
+  }
+  return fn;
+}
+
+// 3D FP32 tensor map over a (nz, ny, px)-pitched field with logical x extent
+// nx; elements outside [0,nx) x [0,ny) x [0,nz) read as zero.
+int make_map(CUtensorMap *m, const float *base, const wave_ctx *c, int box_x,
+             int box_y) {
+  auto enc = get_encode();
+  if (!enc) return WAVE_ECUDA;
+  cuuint64_t dims[3] = {(cuuint64_t)c->nx, (cuuint64_t)c->ny,
+                        (cuuint64_t)c->nz};
+  cuuint64_t strides[2] = {(cuuint64_t)c->px * 4,
+                           (cuuint64_t)c->px * 4 * (cuuint64_t)c->ny};
+  cuuint32_t box[3] = {(cuuint32_t)box_x, (cuuint32_t)box_y, 1};
+  cuuint32_t estr[3] = {1, 1, 1};
+  CUresult r = enc(m, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 3,
+                   const_cast<float *>(base), dims, strides, box, estr,
+                   CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
+                   CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                   CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  return r == CUDA_SUCCESS ? WAVE_OK : WAVE_ECUDA;
+}
+
+int build_maps(wave_ctx *c) {
+  const int tx = c->var.tx, ty = c->var.ty;
+  for (int b = 0; b < 2; ++b) {
+    int st = make_map(&c->tm_halo[b], c->buf[b], c, tx + 2 * kR, ty + 2 * kR);
+    if (st) return st;
+    st = make_map(&c->tm_tile[b], c->buf[b], c, tx, ty);
+    if (st) return st;
+  }
+  return make_map(&c->tm_c, c->c, c, tx, ty);
+}
+
+// Planes per CTA: minimise (waves of CTAs) x (planes + pre-roll cost), a
+// rough model of a launch whose CTAs all take time proportional to their
+// stage count.
+int choose_zchunk(int nz, long long ctas_xy, long long resident) {
+  int best = nz;
+  double best_cost = 1e300;
+  for (int k = 1; k <= nz; ++k) {
+    const int zc = (nz + k - 1) / k;
+    const int chunks = (nz + zc - 1) / zc;
+    const long long ctas = ctas_xy * chunks;
+    const long long waves = (ctas + resident - 1) / resident;
+    const double cost = (double)waves * (zc + 6.0);
+    if (cost < best_cost - 1e-9) {
+      best_cost = cost;
+      best = zc;
+    }
+  }
+  return best;
+}
+
+void set_coeffs(wave_ctx *c) {
+  SweepArgs &a = c->args;
+  a.nx = c->nx;
+  a.ny = c->ny;
+  a.nz = c->nz;
+  a.px = c->px;
+  a.zchunk = c->zchunk;
+  a.ntx = (int)c->grid.x;
+  const double ix = 1.0 / (c->dx * c->dx), iy = 1.0 / (c->dy * c->dy),
+               iz = 1.0 / (c->dz * c->dz);
+  a.c0 = (float)(kW[0] * (ix + iy + iz));
+  for (int m = 1; m <= 4; ++m) {
+    a.cx[m - 1] = (float)(kW[m] * ix);
+    a.cy[m - 1] = (float)(kW[m] * iy);
+    a.cz[m - 1] = (float)(kW[m] * iz);
+  }
+  a.desc = c->d_desc;
+}
+
+// Enqueue one step on stream st: u = buf[cur], u_prev = buf[cur ^ 1].
+void enqueue_step(wave_ctx *c, cudaStream_t st, int cur, int koff) {
+  SweepArgs a = c->args;
+  a.unext = c->buf[cur ^ 1];
+  a.koff = koff;
+  c->var.launch(c->grid, st, c->tm_halo[cur], c->tm_tile[cur ^ 1], c->tm_c, a);
+}
+
+int build_graph(wave_ctx *c, int parity) {
+  cudaGraph_t g = nullptr;
+  WAVE_TRY_CUDA(cudaStreamBeginCapture(c->capture_stream,
+                                       cudaStreamCaptureModeThreadLocal));
+  for (int k = 0; k < c->graph_steps; ++k)
+    enqueue_step(c, c->capture_stream, parity ^ (k & 1), k);
+  advance_kernel<<<1, 1, 0, c->capture_stream>>>(c->d_desc, c->graph_steps);
+  cudaError_t e = cudaStreamEndCapture(c->capture_stream, &g);
+  if (e != cudaSuccess) return cuda_status(e);
+  e = cudaGraphInstantiate(&c->graph[parity], g, 0);
+  cudaGraphDestroy(g);
+  return cuda_status(e);
+}
+
+// Run nsteps steps whose per-call state (StepDesc) is already uploaded.
+int run_steps(wave_ctx *c, int nsteps) {
+  int done = 0;
+  while (nsteps - done >= c->graph_steps) {
+    if (!c->graph[c->cur]) {
+      int st = build_graph(c, c->cur);
+      if (st) return st;
+    }
+    WAVE_TRY_CUDA(cudaGraphLaunch(c->graph[c->cur], c->stream));
+    done += c->graph_steps;  // even count: parity unchanged
+  }
+  const int rem = nsteps - done;
+  if (rem > 0) {
+    int cur = c->cur;
+    for (int k = 0; k < rem; ++k, cur ^= 1) enqueue_step(c, c->stream, cur, k);
+    advance_kernel<<<1, 1, 0, c->stream>>>(c->d_desc, rem);
+    c->cur = cur;
+  }
+  WAVE_TRY_CUDA(cudaGetLastError());
+  c->step += nsteps;
+  return WAVE_OK;
+}
+
+int read_device_error(const wave_ctx *c) {
+  int err = 0;
+  WAVE_TRY_CUDA(cudaMemcpyAsync(&err, &c->d_desc->error, sizeof(int),
+                                cudaMemcpyDeviceToHost, c->stream));
+  WAVE_TRY_CUDA(cudaStreamSynchronize(c->stream));
+  if (err == kErrTimeout) return WAVE_ETIMEOUT;
+  return err ? WAVE_ECUDA : WAVE_OK;
+}
+
+int upload_desc(wave_ctx *c) {
+  // Everything but the error word (which persists until read).
+  WAVE_TRY_CUDA(cudaMemcpyAsync(c->d_desc, &c->host_desc,
+                                offsetof(StepDesc, error),
+                                cudaMemcpyHostToDevice, c->stream));
+  return WAVE_OK;
+}
+
+double ricker(double t, double f, double t0, double amp) {
+  const double pi = 3.14159265358979323846;
+  const double a = pi * pi * f * f * (t - t0) * (t - t0);
+  return amp * (1.0 - 2.0 * a) * std::exp(-a);
+}
+
+bool finite_pos(double v) { return std::isfinite(v) && v > 0.0; }
+
+}  // namespace
+
+extern "C" {
+
+double wave_cfl_dt(const wave_spacing *h, double vmax) {
+  if (!h || !finite_pos(h->dx) || !finite_pos(h->dy) || !finite_pos(h->dz) ||
+      !finite_pos(vmax))
+    return -1.0;
+  double s = std::fabs(kW[0]);
+  for (int m = 1; m <= 4; ++m) s += 2.0 * std::fabs(kW[m]);
+  const double inv =
+      1.0 / (h->dx * h->dx) + 1.0 / (h->dy * h->dy) + 1.0 / (h->dz * h->dz);
+  return 2.0 / (vmax * std::sqrt(s * inv));
+}
+
+const char *wave_strerror(int st) {
+  switch (st) {
+    case WAVE_OK: return "ok";
+    case WAVE_EINVAL: return "invalid argument";
+    case WAVE_ENOMEM: return "out of device memory";
+    case WAVE_ECUDA: return "CUDA error";
+    case WAVE_EUNSTABLE: return "dt above the leapfrog stability limit";
+    case WAVE_ETIMEOUT: return "device wait timed out";
+    case WAVE_EBUSY: return "not ready";
+    case WAVE_ENAN: return "non-finite values";
+    case WAVE_ENOTSUP: return "not supported";
+    default: return "unknown status";
+  }
+}
+
+void wave_destroy(wave_ctx *c) {
+  if (!c) return;
+  if (c->stream || c->buf[0]) cudaStreamSynchronize(c->stream);
+  for (int p = 0; p < 2; ++p)
+    if (c->graph[p]) cudaGraphExecDestroy(c->graph[p]);
+  cudaFree(c->buf[0]);
+  cudaFree(c->buf[1]);
+  cudaFree(c->c);
+  cudaFree(c->d_desc);
+  cudaFree(c->d_scratch);
+  cudaFree(c->wavelet.p);
+  cudaFree(c->rec.p);
+  cudaFree(c->rec_start.p);
+  cudaFree(c->traces.p);
+  if (c->capture_stream) cudaStreamDestroy(c->capture_stream);
+  delete c;
+}
+
+static int create_impl(wave_ctx *c, const float *velocity) {
+  const size_t plane = (size_t)c->px * c->ny;
+  const size_t nfield = plane * c->nz;
+  const size_t bytes = nfield * sizeof(float);
+  cudaStream_t st = c->stream;
+  WAVE_TRY_CUDA(cudaGetDevice(&c->device));
+  WAVE_TRY_CUDA(cudaStreamCreateWithFlags(&c->capture_stream,
+                                          cudaStreamNonBlocking));
+  WAVE_TRY_CUDA(cudaMalloc((void **)&c->buf[0], bytes));
+  WAVE_TRY_CUDA(cudaMalloc((void **)&c->buf[1], bytes));
+  WAVE_TRY_CUDA(cudaMalloc((void **)&c->c, bytes));
+  WAVE_TRY_CUDA(cudaMalloc((void **)&c->d_desc, sizeof(StepDesc)));
+  WAVE_TRY_CUDA(cudaMalloc(&c->d_scratch, 16));
+  WAVE_TRY_CUDA(cudaMemsetAsync(c->buf[0], 0, bytes, st));
+  WAVE_TRY_CUDA(cudaMemsetAsync(c->buf[1], 0, bytes, st));
+  WAVE_TRY_CUDA(cudaMemsetAsync(c->c, 0, bytes, st));
+  WAVE_TRY_CUDA(cudaMemsetAsync(c->d_desc, 0, sizeof(StepDesc), st));
+  WAVE_TRY_CUDA(cudaMemsetAsync(c->d_scratch, 0, 16, st));
+
+  // Velocity into the c buffer (pitched), then validate and convert.
+  WAVE_TRY_CUDA(cudaMemcpy2DAsync(c->c, (size_t)c->px * 4, velocity,
+                                  (size_t)c->nx * 4, (size_t)c->nx * 4,
+                                  (size_t)c->ny * c->nz, cudaMemcpyDefault, st));
+  unsigned *vmax_bits = reinterpret_cast<unsigned *>(c->d_scratch);
+  unsigned long long *nbad =
+      reinterpret_cast<unsigned long long *>((char *)c->d_scratch + 8);
+  int sms = 0;
+  WAVE_TRY_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount,
+                                       c->device));
+  scan_velocity_kernel<<<sms * 4, 256, 0, st>>>(
+      c->c, c->nx, c->px, (long long)c->ny * c->nz, vmax_bits, nbad);
+  WAVE_TRY_CUDA(cudaGetLastError());
+  unsigned char res[16];
+  WAVE_TRY_CUDA(cudaMemcpyAsync(res, c->d_scratch, 16, cudaMemcpyDeviceToHost, st));
+  WAVE_TRY_CUDA(cudaStreamSynchronize(st));
+  unsigned vb;
+  unsigned long long bad;
+  std::memcpy(&vb, res, 4);
+  std::memcpy(&bad, res + 8, 8);
+  if (bad) return WAVE_EINVAL;
+  float vmax;
+  std::memcpy(&vmax, &vb, 4);
+  wave_spacing h{c->dx, c->dy, c->dz};
+  const double lim = wave_cfl_dt(&h, (double)vmax);
+  if (!(c->dt <= lim * (1.0 + 1e-12))) return WAVE_EUNSTABLE;
+  velocity_to_c_kernel<<<sms * 4, 256, 0, st>>>(c->c, (long long)nfield,
+                                                c->dt * c->dt);
+  WAVE_TRY_CUDA(cudaGetLastError());
+
+  // Launch geometry.
+  const char *ev = std::getenv("GBWAVE_VARIANT");
+  c->var = pick_variant(ev ? std::atoi(ev) : 0);
+  WAVE_TRY_CUDA(cudaFuncSetAttribute(c->var.func,
+                                     cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                     (int)c->var.smem));
+  WAVE_TRY_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(
+      &c->ctas_per_sm, c->var.func, c->var.threads, c->var.smem));
+  if (c->ctas_per_sm < 1) return WAVE_ECUDA;
+  const int ntx = (c->nx + c->var.tx - 1) / c->var.tx;
+  const int nty = (c->ny + c->var.ty - 1) / c->var.ty;
+  c->ntiles = ntx * nty;
+  c->zchunk = choose_zchunk(c->nz, (long long)c->ntiles,
+                            (long long)sms * c->ctas_per_sm);
+  c->grid = dim3(ntx, nty, (c->nz + c->zchunk - 1) / c->zchunk);
+  if (c->grid.y > 65535 || c->grid.z > 65535) return WAVE_EINVAL;
+  set_coeffs(c);
+  int stt = build_maps(c);
+  if (stt) return stt;
+  const char *gs = std::getenv("GBWAVE_GRAPH_STEPS");
+  if (gs) c->graph_steps = std::max(2, (std::atoi(gs) / 2) * 2);
+
+  if (!is_device_ptr(velocity)) WAVE_TRY_CUDA(cudaStreamSynchronize(st));
+  return WAVE_OK;
+}
+
+int wave_create(const wave_grid *g, const wave_spacing *h, double dt,
+                const float *velocity, int storage, void *stream,
+                wave_ctx **out) {
+  if (!out) return WAVE_EINVAL;
+  *out = nullptr;
+  if (!g || !h || !velocity) return WAVE_EINVAL;
+  if (g->nx < 1 || g->ny < 1 || g->nz < 1) return WAVE_EINVAL;
+  if (!finite_pos(h->dx) || !finite_pos(h->dy) || !finite_pos(h->dz) ||
+      !finite_pos(dt))
+    return WAVE_EINVAL;
+  if (storage != WAVE_STORAGE_F32) return WAVE_ENOTSUP;
+  // Row pitch in floats: a multiple of 4 so rows are 16-byte aligned (TMA).
+  const long long px = ((long long)g->nx + 3) / 4 * 4;
+  if (px * (long long)g->ny * (long long)g->nz > (1ll << 36)) return WAVE_EINVAL;
+  wave_ctx *c = new (std::nothrow) wave_ctx();
+  if (!c) return WAVE_ENOMEM;
+  c->nx = g->nx;
+  c->ny = g->ny;
+  c->nz = g->nz;
+  c->px = (int)px;
+  c->dx = h->dx;
+  c->dy = h->dy;
+  c->dz = h->dz;
+  c->dt = dt;
+  c->stream = reinterpret_cast<cudaStream_t>(stream);
+  const int st = create_impl(c, velocity);
+  if (st != WAVE_OK) {
+    cudaGetLastError();
+    wave_destroy(c);
+    return st;
+  }
+  *out = c;
+  return WAVE_OK;
+}
+
+int wave_step(wave_ctx *c, int nsteps) {
+  if (!c || nsteps < 0) return WAVE_EINVAL;
+  if (nsteps == 0) return WAVE_OK;
+  StepDesc &d = c->host_desc;
+  std::memset(&d, 0, sizeof(d));
+  int st = upload_desc(c);
+  if (st) return st;
+  return run_steps(c, nsteps);
+}
+
+int wave_propagate(wave_ctx *c, const wave_shot *shot, int nsteps,
+                   const int32_t *rec_xyz, int nrec, float *traces) {
+  if (!c || nsteps < 0 || nrec < 0) return WAVE_EINVAL;
+  if (nrec > 0 && (!rec_xyz || !traces)) return WAVE_EINVAL;
+  if (shot) {
+    if (shot->sx < 0 || shot->sx >= c->nx || shot->sy < 0 ||
+        shot->sy >= c->ny || shot->sz < 0 || shot->sz >= c->nz)
+      return WAVE_EINVAL;
+    if (!finite_pos(shot->f_peak) || !std::isfinite(shot->t0) ||
+        !std::isfinite(shot->amp))
+      return WAVE_EINVAL;
+  }
+  if (nsteps == 0) return WAVE_OK;
+  cudaStream_t st = c->stream;
+
+  // Receivers: bring to the host, validate, sort by (tile, z) into CSR.
+  std::vector<int32_t> hrec((size_t)nrec * 3);
+  if (nrec > 0) {
+    if (is_device_ptr(rec_xyz)) {
+      WAVE_TRY_CUDA(cudaMemcpyAsync(hrec.data(), rec_xyz, hrec.size() * 4,
+                                    cudaMemcpyDeviceToHost, st));
+      WAVE_TRY_CUDA(cudaStreamSynchronize(st));
+    } else {
+      std::memcpy(hrec.data(), rec_xyz, hrec.size() * 4);
+    }
+  }
+  const int tx = c->var.tx, ty = c->var.ty, ntx = (int)c->grid.x;
+  c->h_rec.resize(nrec);
+  c->h_rec_start.assign(c->ntiles + 1, 0);
+  std::vector<int> tile_of(nrec);
+  for (int r = 0; r < nrec; ++r) {
+    const int x = hrec[3 * r], y = hrec[3 * r + 1], z = hrec[3 * r + 2];
+    if (x < 0 || x >= c->nx || y < 0 || y >= c->ny || z < 0 || z >= c->nz)
+      return WAVE_EINVAL;
+    const int t = (y / ty) * ntx + (x / tx);
+    tile_of[r] = t;
+    c->h_rec[r] = make_int4(z, (y % ty) * tx + (x % tx), r, t);
+  }
+  std::sort(c->h_rec.begin(), c->h_rec.end(), [](const int4 &a, const int4 &b) {
+    if (a.w != b.w) return a.w < b.w;
+    if (a.x != b.x) return a.x < b.x;
+    return a.z < b.z;
+  });
+  for (int r = 0; r < nrec; ++r) c->h_rec_start[tile_of[r] + 1]++;
+  for (int t = 0; t < c->ntiles; ++t)
+    c->h_rec_start[t + 1] += c->h_rec_start[t];
+
+  // Source wavelet for this call's steps, FP64 on the host, stored FP32.
+  StepDesc &d = c->host_desc;
+  std::memset(&d, 0, sizeof(d));
+  int s;
+  if (shot) {
+    c->h_wavelet.resize(nsteps);
+    const double t0 = shot->t0 < 0 ? 1.0 / shot->f_peak : shot->t0;
+    for (int k = 0; k < nsteps; ++k)
+      c->h_wavelet[k] = (float)ricker((double)(c->step + k) * c->dt,
+                                      shot->f_peak, t0, shot->amp);
+    if ((s = ensure(c->wavelet, (size_t)nsteps * 4, st))) return s;
+    WAVE_TRY_CUDA(cudaMemcpyAsync(c->wavelet.p, c->h_wavelet.data(),
+                                  (size_t)nsteps * 4, cudaMemcpyHostToDevice, st));
+    d.wavelet = (const float *)c->wavelet.p;
+    d.src_active = 1;
+    d.sx = shot->sx;
+    d.sy = shot->sy;
+    d.sz = shot->sz;
+  }
+  const bool host_traces = nrec > 0 && !is_device_ptr(traces);
+  if (nrec > 0) {
+    if ((s = ensure(c->rec, (size_t)nrec * sizeof(int4), st))) return s;
+    if ((s = ensure(c->rec_start, (size_t)(c->ntiles + 1) * 4, st))) return s;
+    WAVE_TRY_CUDA(cudaMemcpyAsync(c->rec.p, c->h_rec.data(),
+                                  (size_t)nrec * sizeof(int4),
+                                  cudaMemcpyHostToDevice, st));
+    WAVE_TRY_CUDA(cudaMemcpyAsync(c->rec_start.p, c->h_rec_start.data(),
+                                  (size_t)(c->ntiles + 1) * 4,
+                                  cudaMemcpyHostToDevice, st));
+    if (host_traces) {
+      if ((s = ensure(c->traces, (size_t)nsteps * nrec * 4, st))) return s;
+      d.traces = (float *)c->traces.p;
+    } else {
+      d.traces = traces;
+    }
+    d.rec = (const int4 *)c->rec.p;
+    d.rec_start = (const int *)c->rec_start.p;
+    d.nrec = nrec;
+  }
+  if ((s = upload_desc(c))) return s;
+  if ((s = run_steps(c, nsteps))) return s;
+  if (host_traces) {
+    WAVE_TRY_CUDA(cudaMemcpyAsync(traces, c->traces.p, (size_t)nsteps * nrec * 4,
+                                  cudaMemcpyDeviceToHost, st));
+    return read_device_error(c);
+  }
+  // The host-side tables were staged by the copies above; make sure pageable
+  // sources are consumed before the vectors change on the next call.
+  return WAVE_OK;
+}
+
+int wave_get_field(const wave_ctx *c, int which, float *out) {
+  if (!c || !out || (which != 0 && which != 1)) return WAVE_EINVAL;
+  const float *src = c->buf[which == 0 ? c->cur : (c->cur ^ 1)];
+  WAVE_TRY_CUDA(cudaMemcpy2DAsync(out, (size_t)c->nx * 4, src,
+                                  (size_t)c->px * 4, (size_t)c->nx * 4,
+                                  (size_t)c->ny * c->nz, cudaMemcpyDefault,
+                                  c->stream));
+  if (!is_device_ptr(out)) return read_device_error(c);
+  return WAVE_OK;
+}
+
+int wave_set_state(wave_ctx *c, const float *u, const float *u_prev,
+                   int64_t step) {
+  if (!c || !u || !u_prev || step < 0) return WAVE_EINVAL;
+  c->cur = 0;
+  const float *src[2] = {u, u_prev};
+  for (int b = 0; b < 2; ++b)
+    WAVE_TRY_CUDA(cudaMemcpy2DAsync(c->buf[b], (size_t)c->px * 4, src[b],
+                                    (size_t)c->nx * 4, (size_t)c->nx * 4,
+                                    (size_t)c->ny * c->nz, cudaMemcpyDefault,
+                                    c->stream));
+  c->step = step;
+  if (!is_device_ptr(u) || !is_device_ptr(u_prev))
+    WAVE_TRY_CUDA(cudaStreamSynchronize(c->stream));
+  return WAVE_OK;
+}
+
+int wave_get_step(const wave_ctx *c, int64_t *step) {
+  if (!c || !step) return WAVE_EINVAL;
+  *step = c->step;
+  return WAVE_OK;
+}
+
+int wave_reset(wave_ctx *c) {
+  if (!c) return WAVE_EINVAL;
+  const size_t bytes = (size_t)c->px * c->ny * c->nz * 4;
+  WAVE_TRY_CUDA(cudaMemsetAsync(c->buf[0], 0, bytes, c->stream));
+  WAVE_TRY_CUDA(cudaMemsetAsync(c->buf[1], 0, bytes, c->stream));
+  c->cur = 0;
+  c->step = 0;
+  return WAVE_OK;
+}
+
+int wave_synchronize(wave_ctx *c) {
+  if (!c) return WAVE_EINVAL;
+  return read_device_error(c);
+}
+
+int wave_get_launch_info(const wave_ctx *c, int *tile_x, int *tile_y,
+                         int *z_chunk, int *grid_ctas, int *ctas_per_sm) {
+  if (!c) return WAVE_EINVAL;
+  if (tile_x) *tile_x = c->var.tx;
+  if (tile_y) *tile_y = c->var.ty;
+  if (z_chunk) *z_chunk = c->zchunk;
+  if (grid_ctas) *grid_ctas = (int)(c->grid.x * c->grid.y * c->grid.z);
+  if (ctas_per_sm) *ctas_per_sm = c->ctas_per_sm;
+  return WAVE_OK;
+}
+
+int wave_selftest_wait(int64_t limit_ns, void *stream) {
+  cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+  limit_ns = std::min<int64_t>(std::max<int64_t>(limit_ns, 1000000), 10000000000ll);
+  int *d = nullptr;
+  WAVE_TRY_CUDA(cudaMalloc(&d, sizeof(int)));
+  int h = 0;
+  cudaError_t e = cudaMemsetAsync(d, 0, sizeof(int), st);
+  if (e == cudaSuccess) {
+    selftest_wait_kernel<<<1, 1, 0, st>>>((uint64_t)limit_ns, d);
+    e = cudaGetLastError();
+  }
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(&h, d, sizeof(int), cudaMemcpyDeviceToHost, st);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+  cudaFree(d);
+  if (e != cudaSuccess) return cuda_status(e);
+  return h == 2 ? WAVE_ETIMEOUT : WAVE_ECUDA;
+}
+
+}  // extern "C"
