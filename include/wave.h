@@ -53,7 +53,8 @@ enum {
   WAVE_ETIMEOUT = -5,  /* a bounded device wait gave up */
   WAVE_EBUSY = -6,     /* result not ready yet */
   WAVE_ENAN = -7,      /* non-finite values in the output */
-  WAVE_ENOTSUP = -8    /* option not supported by this build */
+  WAVE_ENOTSUP = -8,   /* option not supported by this build */
+  WAVE_ETOOBIG = -9    /* request exceeds the fixed scratch of wave_propagate_noalloc */
 };
 
 /* Storage precision of the wavefield (argument of wave_create). */
@@ -161,6 +162,54 @@ int wave_get_launch_info(const wave_ctx *ctx, int *tile_x, int *tile_y,
  * designed, WAVE_ECUDA if it reported completion or a CUDA call failed.
  */
 int wave_selftest_wait(int64_t limit_ns, void *stream);
+
+/*
+ * Allocation-free propagation. The paper has no counterpart to this entry
+ * point; it exists for callers that must not allocate device memory: code
+ * running inside an application whose memory pool already owns the whole
+ * GPU (a cudaMalloc there fails or fragments the pool), plugins held to a
+ * fixed memory budget, and services that forbid allocation once they have
+ * started. It runs the same leapfrog sweep as wave_propagate, but on buffers
+ * the caller owns, and keeps its small tables (step descriptor, receiver
+ * table, source wavelet) in one fixed array of WAVE_NOALLOC_SCRATCH_BYTES
+ * that the library declares statically: every GPU that loads the library
+ * holds that array until the process exits. It calls no cudaMalloc, no
+ * cudaFree and no allocating library routine, and allocates no host heap.
+ *
+ *   g, h, dt     as for wave_create; nx must be a multiple of 4 (rows of the
+ *                caller's dense arrays must start on 16-byte boundaries)
+ *   velocity     device, nx*ny*nz float32 m/s, dense, 16-byte aligned
+ *   u, u_prev    device, nx*ny*nz float32 each, dense, 16-byte aligned; the
+ *                state at steps step0 and step0-1 on entry. The sweep writes
+ *                each new step over the older buffer, so on return the
+ *                newest step is in u if *newest == 0 and in u_prev if
+ *                *newest == 1 (nsteps odd); the other buffer holds the step
+ *                before it
+ *   shot         Ricker source or NULL; source time of step n is (step0+n) dt
+ *   rec_xyz      nrec*3 int32, host or device; traces: device, nsteps*nrec
+ *
+ * Limits: the tables must fit the array: 512 + (16 * nrec) +
+ * (4 * nsteps rounded up to 256, if shot) + (4 * (tiles + 1) rounded up to
+ * 256, if nrec > 0) bytes, tiles = ceil(nx/64) * ceil(ny/16); otherwise the
+ * call returns WAVE_ETOOBIG before launching anything. With 4 MiB this is,
+ * for example, 65536 receivers and 100000 steps on a 1024 x 1024 grid.
+ *
+ * The first call on each device finds the array's device address
+ * (cudaGetSymbolAddress) and sets the kernel's shared-memory limit, with that
+ * device current; make that first call before any stream capture. Every
+ * call shares the one array and overwrites what the last call left there;
+ * calls whose work overlaps on the GPU (other streams, other host threads)
+ * race on it, so serialize them. The call validates the velocities
+ * (finite, > 0, dt within wave_cfl_dt) and synchronizes the stream before
+ * it returns, so a timed-out device wait comes back as WAVE_ETIMEOUT.
+ */
+#define WAVE_NOALLOC_SCRATCH_BYTES (4u << 20)
+
+int wave_propagate_noalloc(const wave_grid *g, const wave_spacing *h, double dt,
+                           const float *velocity, float *u, float *u_prev,
+                           const wave_shot *shot, int64_t step0, int nsteps,
+                           const int32_t *rec_xyz, int nrec, float *traces,
+                           void *stream, int *newest);
 
 #ifdef __cplusplus
 }

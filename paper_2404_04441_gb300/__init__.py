@@ -16,7 +16,7 @@ __all__ = [
     "WaveError", "load", "wave_cfl_dt", "wave_create", "wave_step", "wave_propagate",
     "wave_get_field", "wave_set_state", "wave_get_step", "wave_reset",
     "wave_synchronize", "wave_destroy", "wave_strerror", "wave_get_launch_info",
-    "wave_selftest_wait", "WaveSolver", "library_path",
+    "wave_selftest_wait", "wave_propagate_noalloc", "WaveSolver", "library_path",
 ]
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
@@ -26,7 +26,7 @@ _lib = None
 WAVE_OK = 0
 STATUS = {0: "WAVE_OK", -1: "WAVE_EINVAL", -2: "WAVE_ENOMEM", -3: "WAVE_ECUDA",
           -4: "WAVE_EUNSTABLE", -5: "WAVE_ETIMEOUT", -6: "WAVE_EBUSY", -7: "WAVE_ENAN",
-          -8: "WAVE_ENOTSUP"}
+          -8: "WAVE_ENOTSUP", -9: "WAVE_ETOOBIG"}
 
 
 class WaveError(RuntimeError):
@@ -82,9 +82,12 @@ def load(path=None):
     lib.wave_strerror.restype = ctypes.c_char_p
     lib.wave_get_launch_info.argtypes = [vp] + [ctypes.POINTER(ctypes.c_int)] * 5
     lib.wave_selftest_wait.argtypes = [ctypes.c_int64, vp]
+    lib.wave_propagate_noalloc.argtypes = [
+        ctypes.POINTER(_Grid), ctypes.POINTER(_Spacing), ctypes.c_double, vp, vp, vp,
+        ctypes.POINTER(_Shot), ctypes.c_int64, ip, vp, ip, vp, vp, ctypes.POINTER(ip)]
     for name in ("wave_create", "wave_step", "wave_propagate", "wave_get_field",
                  "wave_set_state", "wave_get_step", "wave_reset", "wave_synchronize",
-                 "wave_get_launch_info", "wave_selftest_wait"):
+                 "wave_get_launch_info", "wave_selftest_wait", "wave_propagate_noalloc"):
         getattr(lib, name).restype = ctypes.c_int
     _lib = lib
     return lib
@@ -201,6 +204,37 @@ def wave_synchronize(ctx):
 def wave_destroy(ctx):
     if ctx:
         load().wave_destroy(ctx)
+
+
+def wave_propagate_noalloc(grid, spacing, dt, velocity, u, u_prev, shot, step0, nsteps,
+                           rec=None, traces=None, stream=None):
+    """Allocation-free propagation on caller-owned device buffers.
+
+    Returns ``newest``: 0 if ``u`` holds the newest step on return, 1 if
+    ``u_prev`` does. Raises WaveError on a non-zero status (WAVE_ETOOBIG when
+    the request does not fit the library's fixed scratch array).
+    """
+    lib = load()
+    nx, ny, nz = map(int, grid)
+    count = nx * ny * nz
+    if rec is not None and (len(rec.shape) != 2 or rec.shape[1] != 3):
+        raise ValueError("rec must have shape (nrec, 3)")
+    nrec = 0 if rec is None else int(rec.shape[0])
+    sp = None
+    if shot is not None:
+        sx, sy, sz, f, t0, amp = shot
+        sp = ctypes.byref(_Shot(int(sx), int(sy), int(sz), float(f),
+                                -1.0 if t0 is None else float(t0), float(amp)))
+    newest = ctypes.c_int(0)
+    st = _default_stream() if stream is None else int(stream)
+    _check(lib.wave_propagate_noalloc(
+        ctypes.byref(_Grid(nx, ny, nz)), ctypes.byref(_Spacing(*map(float, spacing))),
+        float(dt), _ptr(velocity, "float32", count, "velocity"),
+        _ptr(u, "float32", count, "u"), _ptr(u_prev, "float32", count, "u_prev"), sp,
+        int(step0), int(nsteps), _ptr(rec, "int32", 3 * nrec, "rec") if nrec else None, nrec,
+        _ptr(traces, "float32", int(nsteps) * nrec, "traces") if nrec else None, st,
+        ctypes.byref(newest)), "wave_propagate_noalloc")
+    return newest.value
 
 
 def wave_selftest_wait(limit_ns, stream=None):

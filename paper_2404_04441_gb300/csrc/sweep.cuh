@@ -50,6 +50,7 @@ struct SweepArgs {
   float *unext;        // output: the u_prev buffer, overwritten in place
   StepDesc *desc;
   int koff;            // step offset of this launch within a graph chunk
+  float dt2;           // dt^2, used only when the c field holds velocities
 };
 
 template <int TX_, int TY_, int VY_, int PF_, int MINB_>
@@ -75,7 +76,10 @@ struct SweepCfg {
   static_assert(UW <= 256 && UH <= 256, "TMA box limit");
 };
 
-template <class C>
+// kVelocityField = false: tm_c maps v^2 dt^2. true: tm_c maps the velocity
+// itself and the kernel forms v^2 dt^2 from it (the allocation-free entry
+// point, which has no buffer of its own to hold v^2 dt^2).
+template <class C, bool kVelocityField = false>
 __global__ void __launch_bounds__(C::THREADS, C::MINB)
     wave_sweep_kernel(const __grid_constant__ CUtensorMap tm_u,
                       const __grid_constant__ CUtensorMap tm_up,
@@ -208,7 +212,13 @@ __global__ void __launch_bounds__(C::THREADS, C::MINB)
       }
       const int pofs = (ty * C::VY + v) * C::TX + 4 * tx;
       const float4 upv = lds4(pp + pofs);
-      const float4 cv = lds4(pc + pofs);
+      float4 cv = lds4(pc + pofs);
+      if (kVelocityField) {
+        cv.x = cv.x * cv.x * a.dt2;
+        cv.y = cv.y * cv.y * a.dt2;
+        cv.z = cv.z * cv.z * a.dt2;
+        cv.w = cv.w * cv.w * a.dt2;
+      }
       float4 o;
       o.x = fmaf(cv.x, acc[0], fmaf(2.f, xs[4], -upv.x));
       o.y = fmaf(cv.y, acc[1], fmaf(2.f, xs[5], -upv.y));

@@ -361,6 +361,7 @@ const char *wave_strerror(int st) {
     case WAVE_EBUSY: return "not ready";
     case WAVE_ENAN: return "non-finite values";
     case WAVE_ENOTSUP: return "not supported";
+    case WAVE_ETOOBIG: return "request exceeds the fixed scratch array";
     default: return "unknown status";
   }
 }
@@ -680,3 +681,255 @@ int wave_selftest_wait(int64_t limit_ns, void *stream) {
 }
 
 }  // extern "C"
+
+// ---------------------------------------------------------------------------
+// Allocation-free entry point (wave_propagate_noalloc).
+//
+// Its tables live in g_noalloc_scratch, a fixed device array declared here;
+// the host builds their image in g_noalloc_image (also static) and copies it
+// over in one transfer per call. Layout (byte offsets):
+//   [0, 256)      StepDesc
+//   [256, 272)    velocity scan result: max bits (u32), bad count (u64 at 264)
+//   [512, ...)    wavelet (nsteps floats), rec_start (tiles + 1 ints),
+//                 receivers (nrec int4), each block starting on 256 bytes
+namespace {
+
+using NoallocCfg = CfgA;
+constexpr size_t kNoallocBytes = WAVE_NOALLOC_SCRATCH_BYTES;
+constexpr int kNoallocMaxDevices = 64;
+constexpr size_t kNoallocScanOff = 256;
+constexpr size_t kNoallocTablesOff = 512;
+constexpr size_t kNoallocMaxRec = kNoallocBytes / sizeof(int4);
+
+__device__ __align__(256) unsigned char g_noalloc_scratch[kNoallocBytes];
+alignas(256) unsigned char g_noalloc_image[kNoallocBytes];
+int32_t g_noalloc_rec_raw[kNoallocMaxRec * 3];
+unsigned char g_noalloc_scan[16];
+
+struct NoallocDevice {
+  unsigned char *scratch;  // device address of g_noalloc_scratch
+  int sms, ctas_per_sm;
+};
+NoallocDevice g_noalloc_dev[kNoallocMaxDevices];
+
+size_t round256(size_t x) { return (x + 255) & ~size_t(255); }
+
+// Once per device, with that device current.
+int noalloc_setup(int dev, NoallocDevice **out) {
+  if (dev < 0 || dev >= kNoallocMaxDevices) return WAVE_ECUDA;
+  NoallocDevice &d = g_noalloc_dev[dev];
+  if (!d.scratch) {
+    void *p = nullptr;
+    WAVE_TRY_CUDA(cudaGetSymbolAddress(&p, g_noalloc_scratch));
+    const void *fn =
+        reinterpret_cast<const void *>(&wave_sweep_kernel<NoallocCfg, true>);
+    WAVE_TRY_CUDA(cudaFuncSetAttribute(
+        fn, cudaFuncAttributeMaxDynamicSharedMemorySize,
+        (int)NoallocCfg::SMEM_BYTES));
+    int sms = 0, per = 0;
+    WAVE_TRY_CUDA(
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+    WAVE_TRY_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(
+        &per, fn, NoallocCfg::THREADS, NoallocCfg::SMEM_BYTES));
+    if (per < 1) return WAVE_ECUDA;
+    d.sms = sms;
+    d.ctas_per_sm = per;
+    d.scratch = static_cast<unsigned char *>(p);
+  }
+  *out = &d;
+  return WAVE_OK;
+}
+
+// Tensor map over a caller-owned dense field (row pitch nx floats).
+int noalloc_map(CUtensorMap *m, const float *base, int nx, int ny, int nz,
+                int box_x, int box_y) {
+  auto enc = get_encode();
+  if (!enc) return WAVE_ECUDA;
+  cuuint64_t dims[3] = {(cuuint64_t)nx, (cuuint64_t)ny, (cuuint64_t)nz};
+  cuuint64_t strides[2] = {(cuuint64_t)nx * 4, (cuuint64_t)nx * 4 * ny};
+  cuuint32_t box[3] = {(cuuint32_t)box_x, (cuuint32_t)box_y, 1};
+  cuuint32_t estr[3] = {1, 1, 1};
+  CUresult r = enc(m, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 3,
+                   const_cast<float *>(base), dims, strides, box, estr,
+                   CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
+                   CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                   CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  return r == CUDA_SUCCESS ? WAVE_OK : WAVE_ECUDA;
+}
+
+}  // namespace
+
+extern "C" int wave_propagate_noalloc(const wave_grid *g, const wave_spacing *h,
+                                      double dt, const float *velocity,
+                                      float *u, float *u_prev,
+                                      const wave_shot *shot, int64_t step0,
+                                      int nsteps, const int32_t *rec_xyz,
+                                      int nrec, float *traces, void *stream,
+                                      int *newest) {
+  using C = NoallocCfg;
+  if (!newest) return WAVE_EINVAL;
+  *newest = 0;
+  if (!g || !h || !velocity || !u || !u_prev) return WAVE_EINVAL;
+  const int nx = g->nx, ny = g->ny, nz = g->nz;
+  if (nx < 1 || ny < 1 || nz < 1 || nx % 4 != 0) return WAVE_EINVAL;
+  if ((long long)nx * ny * nz > (1ll << 36)) return WAVE_EINVAL;
+  if (!finite_pos(h->dx) || !finite_pos(h->dy) || !finite_pos(h->dz) ||
+      !finite_pos(dt) || nsteps < 0 || nrec < 0 || step0 < 0)
+    return WAVE_EINVAL;
+  if (nrec > 0 && (!rec_xyz || !traces)) return WAVE_EINVAL;
+  if (shot && (shot->sx < 0 || shot->sx >= nx || shot->sy < 0 ||
+               shot->sy >= ny || shot->sz < 0 || shot->sz >= nz ||
+               !finite_pos(shot->f_peak) || !std::isfinite(shot->t0) ||
+               !std::isfinite(shot->amp)))
+    return WAVE_EINVAL;
+  for (const void *p : {(const void *)velocity, (const void *)u,
+                        (const void *)u_prev})
+    if (reinterpret_cast<uintptr_t>(p) % 16 != 0) return WAVE_EINVAL;
+  const int ntx = (nx + C::TX - 1) / C::TX, nty = (ny + C::TY - 1) / C::TY;
+  const size_t ntiles = (size_t)ntx * nty;
+  const size_t off_w = kNoallocTablesOff;
+  const size_t off_rs = off_w + (shot ? round256((size_t)nsteps * 4) : 0);
+  const size_t off_r = off_rs + (nrec > 0 ? round256((ntiles + 1) * 4) : 0);
+  const size_t end = off_r + (size_t)nrec * sizeof(int4);
+  if (end > kNoallocBytes) return WAVE_ETOOBIG;
+  if (!is_device_ptr(velocity) || !is_device_ptr(u) || !is_device_ptr(u_prev) ||
+      (nrec > 0 && !is_device_ptr(traces)))
+    return WAVE_EINVAL;
+
+  int dev = 0;
+  WAVE_TRY_CUDA(cudaGetDevice(&dev));
+  NoallocDevice *nd = nullptr;
+  int st = noalloc_setup(dev, &nd);
+  if (st) return st;
+  cudaStream_t cs = reinterpret_cast<cudaStream_t>(stream);
+  unsigned char *scr = nd->scratch;
+
+  // Receivers to the host (static buffer), then bounds.
+  if (nrec > 0) {
+    if (is_device_ptr(rec_xyz)) {
+      WAVE_TRY_CUDA(cudaMemcpyAsync(g_noalloc_rec_raw, rec_xyz,
+                                    (size_t)nrec * 12, cudaMemcpyDeviceToHost,
+                                    cs));
+      WAVE_TRY_CUDA(cudaStreamSynchronize(cs));
+    } else {
+      std::memcpy(g_noalloc_rec_raw, rec_xyz, (size_t)nrec * 12);
+    }
+    for (int r = 0; r < nrec; ++r) {
+      const int x = g_noalloc_rec_raw[3 * r], y = g_noalloc_rec_raw[3 * r + 1],
+                z = g_noalloc_rec_raw[3 * r + 2];
+      if (x < 0 || x >= nx || y < 0 || y >= ny || z < 0 || z >= nz)
+        return WAVE_EINVAL;
+    }
+  }
+
+  // Velocity scan (max, invalid count) into the scratch's scan block.
+  WAVE_TRY_CUDA(cudaMemsetAsync(scr + kNoallocScanOff, 0, 16, cs));
+  scan_velocity_kernel<<<nd->sms * 4, 256, 0, cs>>>(
+      velocity, nx, nx, (long long)ny * nz,
+      reinterpret_cast<unsigned *>(scr + kNoallocScanOff),
+      reinterpret_cast<unsigned long long *>(scr + kNoallocScanOff + 8));
+  WAVE_TRY_CUDA(cudaGetLastError());
+  WAVE_TRY_CUDA(cudaMemcpyAsync(g_noalloc_scan, scr + kNoallocScanOff, 16,
+                                cudaMemcpyDeviceToHost, cs));
+  WAVE_TRY_CUDA(cudaStreamSynchronize(cs));
+  unsigned vb;
+  unsigned long long bad;
+  std::memcpy(&vb, g_noalloc_scan, 4);
+  std::memcpy(&bad, g_noalloc_scan + 8, 8);
+  if (bad) return WAVE_EINVAL;
+  float vmax;
+  std::memcpy(&vmax, &vb, 4);
+  if (!(dt <= wave_cfl_dt(h, (double)vmax) * (1.0 + 1e-12)))
+    return WAVE_EUNSTABLE;
+  if (nsteps == 0) return WAVE_OK;
+
+  // Host image of the tables; every field the kernels read is written here,
+  // so nothing depends on what an earlier call left in the array.
+  std::memset(g_noalloc_image, 0, kNoallocTablesOff);
+  StepDesc d{};
+  if (shot) {
+    float *w = reinterpret_cast<float *>(g_noalloc_image + off_w);
+    const double t0 = shot->t0 < 0 ? 1.0 / shot->f_peak : shot->t0;
+    for (int k = 0; k < nsteps; ++k)
+      w[k] = (float)ricker((double)(step0 + k) * dt, shot->f_peak, t0,
+                           shot->amp);
+    d.wavelet = reinterpret_cast<const float *>(scr + off_w);
+    d.src_active = 1;
+    d.sx = shot->sx;
+    d.sy = shot->sy;
+    d.sz = shot->sz;
+  }
+  if (nrec > 0) {
+    int *rs = reinterpret_cast<int *>(g_noalloc_image + off_rs);
+    int4 *re = reinterpret_cast<int4 *>(g_noalloc_image + off_r);
+    std::memset(rs, 0, (ntiles + 1) * 4);
+    for (int r = 0; r < nrec; ++r) {
+      const int x = g_noalloc_rec_raw[3 * r], y = g_noalloc_rec_raw[3 * r + 1],
+                z = g_noalloc_rec_raw[3 * r + 2];
+      const int t = (y / C::TY) * ntx + (x / C::TX);
+      re[r] = make_int4(z, (y % C::TY) * C::TX + (x % C::TX), r, t);
+      rs[t + 1]++;
+    }
+    std::sort(re, re + nrec, [](const int4 &a, const int4 &b) {
+      if (a.w != b.w) return a.w < b.w;
+      if (a.x != b.x) return a.x < b.x;
+      return a.z < b.z;
+    });
+    for (size_t t = 0; t < ntiles; ++t) rs[t + 1] += rs[t];
+    d.traces = traces;
+    d.rec = reinterpret_cast<const int4 *>(scr + off_r);
+    d.rec_start = reinterpret_cast<const int *>(scr + off_rs);
+    d.nrec = nrec;
+  }
+  std::memcpy(g_noalloc_image, &d, sizeof(d));
+  WAVE_TRY_CUDA(cudaMemcpyAsync(scr, g_noalloc_image, end,
+                                cudaMemcpyHostToDevice, cs));
+
+  // Launch geometry and tensor maps over the caller's buffers.
+  float *buf[2] = {u, u_prev};
+  CUtensorMap halo[2], tile[2], vmap;
+  for (int b = 0; b < 2; ++b) {
+    if ((st = noalloc_map(&halo[b], buf[b], nx, ny, nz, C::TX + 2 * kR,
+                          C::TY + 2 * kR)))
+      return st;
+    if ((st = noalloc_map(&tile[b], buf[b], nx, ny, nz, C::TX, C::TY)))
+      return st;
+  }
+  if ((st = noalloc_map(&vmap, velocity, nx, ny, nz, C::TX, C::TY))) return st;
+  const int zchunk = choose_zchunk(nz, (long long)ntiles,
+                                   (long long)nd->sms * nd->ctas_per_sm);
+  const dim3 grid(ntx, nty, (nz + zchunk - 1) / zchunk);
+  if (grid.y > 65535 || grid.z > 65535) return WAVE_EINVAL;
+  SweepArgs a{};
+  a.nx = nx;
+  a.ny = ny;
+  a.nz = nz;
+  a.px = nx;
+  a.zchunk = zchunk;
+  a.ntx = ntx;
+  const double ix = 1.0 / (h->dx * h->dx), iy = 1.0 / (h->dy * h->dy),
+               iz = 1.0 / (h->dz * h->dz);
+  a.c0 = (float)(kW[0] * (ix + iy + iz));
+  for (int m = 1; m <= 4; ++m) {
+    a.cx[m - 1] = (float)(kW[m] * ix);
+    a.cy[m - 1] = (float)(kW[m] * iy);
+    a.cz[m - 1] = (float)(kW[m] * iz);
+  }
+  a.desc = reinterpret_cast<StepDesc *>(scr);
+  a.dt2 = (float)(dt * dt);
+  for (int k = 0; k < nsteps; ++k) {
+    const int cur = k & 1;
+    a.unext = buf[cur ^ 1];
+    a.koff = k;
+    wave_sweep_kernel<C, true><<<grid, C::THREADS, C::SMEM_BYTES, cs>>>(
+        halo[cur], tile[cur ^ 1], vmap, a);
+  }
+  WAVE_TRY_CUDA(cudaGetLastError());
+  int err = 0;
+  WAVE_TRY_CUDA(cudaMemcpyAsync(&err, &a.desc->error, sizeof(int),
+                                cudaMemcpyDeviceToHost, cs));
+  WAVE_TRY_CUDA(cudaStreamSynchronize(cs));
+  *newest = nsteps & 1;
+  if (err == kErrTimeout) return WAVE_ETIMEOUT;
+  return err ? WAVE_ECUDA : WAVE_OK;
+}
