@@ -41,9 +41,15 @@ struct StepDesc {
   int error;              // first error recorded by a kernel (0 = none)
 };
 
+constexpr int kMaxLayers = 16;
+
 struct SweepArgs {
   int nx, ny, nz, px;  // interior sizes; px = row pitch in floats (mult. of 4)
-  int zchunk;          // planes per CTA (blockIdx.z selects the range)
+  // z layers: CTAs with blockIdx.z == l stream planes [zl[l], zl[l+1]).
+  // Layers are launched in order, so large layers first and small ones last
+  // shorten the partial last wave of CTAs.
+  int nlayers;
+  int zl[kMaxLayers + 1];
   int ntx;             // tiles along x (tile id = by * ntx + bx)
   float c0;            // w0 * (1/dx^2 + 1/dy^2 + 1/dz^2)
   float cx[4], cy[4], cz[4];  // w_m / h_a^2 for m = 1..4
@@ -98,8 +104,8 @@ __global__ void __launch_bounds__(C::THREADS, C::MINB)
   const int ty = tid / C::NTX;
   const int x0 = blockIdx.x * C::TX;
   const int y0 = blockIdx.y * C::TY;
-  const int zb = blockIdx.z * a.zchunk;
-  const int ze = min(zb + a.zchunk, a.nz);
+  const int zb = a.zl[blockIdx.z];
+  const int ze = a.zl[blockIdx.z + 1];
   const int NS = (ze - zb) + 2 * kR;  // stages: 8 to fill the queue, then one per plane
 
   // Per-call state.
@@ -118,6 +124,7 @@ __global__ void __launch_bounds__(C::THREADS, C::MINB)
     rend = d->rec_start[tile + 1];
     while (rcur < rend && rec[rcur].x < zb) ++rcur;
   }
+  int rz = (rcur < rend) ? rec[rcur].x : 0x7fffffff;  // z of the next receiver
   float *trow = (nrec > 0) ? d->traces + (size_t)n * nrec : nullptr;
 
   if (tid == 0) {
@@ -146,121 +153,132 @@ __global__ void __launch_bounds__(C::THREADS, C::MINB)
   if (tid == 0)
     for (int s = 0; s < C::PF && s < NS; ++s) issue(s);
 
-  // q[v][k] holds u of this thread's 4 points on row v at plane j-4+k.
-  float4 q[C::VY][2 * kR + 1];
+  // q[v][k]: u of this thread's 4 points on row v. The loop below is unrolled
+  // by 9, the queue length, so a plane keeps one register for its whole
+  // lifetime: plane P = zb-4+s is written into q[v][s % 9] and read back by
+  // static index (no shifting moves). With SU == 9 the u ring slot of a
+  // stage is likewise s % 9.
+  float4 q[C::VY][9];
 #pragma unroll
   for (int v = 0; v < C::VY; ++v)
 #pragma unroll
-    for (int k = 0; k <= 2 * kR; ++k) q[v][k] = make_float4(0.f, 0.f, 0.f, 0.f);
+    for (int k = 0; k < 9; ++k) q[v][k] = make_float4(0.f, 0.f, 0.f, 0.f);
 
   const int col = 4 * tx + kR;  // smem column of this thread's first point
   int s = 0;
-  for (; s < NS; ++s) {
-    // One barrier per plane: it publishes that stage s has landed for every
-    // thread (a uniform verdict, so a timeout leaves the loop everywhere) and
-    // that every thread is done with plane s-1, whose slots the next issue
-    // may overwrite.
-    const bool ok =
-        mbar_wait_bounded(&bars[s % C::NB], (s / C::NB) & 1, kWaitLimitNs);
-    if (__syncthreads_or(!ok)) break;
-    if (tid == 0 && s + C::PF < NS) issue(s + C::PF);
-    // Push the front plane (j+4) into the queue.
-    const float *uf = su + (s % C::SU) * C::U_SLOT;
+  for (int s0 = 0; s0 < NS; s0 += 9) {
 #pragma unroll
-    for (int v = 0; v < C::VY; ++v) {
-#pragma unroll
-      for (int k = 0; k < 2 * kR; ++k) q[v][k] = q[v][k + 1];
-      q[v][2 * kR] = lds4(uf + (ty * C::VY + v + kR) * C::UW + col);
-    }
-    const int j = zb - 2 * kR + s;
-    if (j < zb) continue;
-
-    const float *uc = su + ((s - kR) % C::SU) * C::U_SLOT;  // plane j
-    const float *pp = sp + (s % C::SP) * C::P_SLOT;
-    const float *pc = sc + (s % C::SP) * C::P_SLOT;
-    float4 res[C::VY];
-#pragma unroll
-    for (int v = 0; v < C::VY; ++v) {
-      const int r = ty * C::VY + v + kR;  // smem row of this point row
-      const float4 a0 = lds4(uc + r * C::UW + col - 4);
-      const float4 a1 = lds4(uc + r * C::UW + col);
-      const float4 a2 = lds4(uc + r * C::UW + col + 4);
-      const float xs[12] = {a0.x, a0.y, a0.z, a0.w, a1.x, a1.y,
-                            a1.z, a1.w, a2.x, a2.y, a2.z, a2.w};
-      float acc[4];
-#pragma unroll
-      for (int e = 0; e < 4; ++e) acc[e] = a.c0 * xs[4 + e];
-#pragma unroll
-      for (int m = 1; m <= kR; ++m) {
-        const float4 ym = lds4(uc + (r - m) * C::UW + col);
-        const float4 yp = lds4(uc + (r + m) * C::UW + col);
-        const float4 zm = q[v][kR - m];
-        const float4 zp = q[v][kR + m];
-        const float cxm = a.cx[m - 1], cym = a.cy[m - 1], czm = a.cz[m - 1];
-        acc[0] = fmaf(cxm, xs[4 - m] + xs[4 + m], acc[0]);
-        acc[1] = fmaf(cxm, xs[5 - m] + xs[5 + m], acc[1]);
-        acc[2] = fmaf(cxm, xs[6 - m] + xs[6 + m], acc[2]);
-        acc[3] = fmaf(cxm, xs[7 - m] + xs[7 + m], acc[3]);
-        acc[0] = fmaf(cym, ym.x + yp.x, acc[0]);
-        acc[1] = fmaf(cym, ym.y + yp.y, acc[1]);
-        acc[2] = fmaf(cym, ym.z + yp.z, acc[2]);
-        acc[3] = fmaf(cym, ym.w + yp.w, acc[3]);
-        acc[0] = fmaf(czm, zm.x + zp.x, acc[0]);
-        acc[1] = fmaf(czm, zm.y + zp.y, acc[1]);
-        acc[2] = fmaf(czm, zm.z + zp.z, acc[2]);
-        acc[3] = fmaf(czm, zm.w + zp.w, acc[3]);
-      }
-      const int pofs = (ty * C::VY + v) * C::TX + 4 * tx;
-      const float4 upv = lds4(pp + pofs);
-      float4 cv = lds4(pc + pofs);
-      if (kVelocityField) {
-        cv.x = cv.x * cv.x * a.dt2;
-        cv.y = cv.y * cv.y * a.dt2;
-        cv.z = cv.z * cv.z * a.dt2;
-        cv.w = cv.w * cv.w * a.dt2;
-      }
-      float4 o;
-      o.x = fmaf(cv.x, acc[0], fmaf(2.f, xs[4], -upv.x));
-      o.y = fmaf(cv.y, acc[1], fmaf(2.f, xs[5], -upv.y));
-      o.z = fmaf(cv.z, acc[2], fmaf(2.f, xs[6], -upv.z));
-      o.w = fmaf(cv.w, acc[3], fmaf(2.f, xs[7], -upv.w));
-      if (src_here && j == sz && sy == ty * C::VY + v) {
-        const int e = sx - 4 * tx;
-        if (e == 0) o.x = fmaf(cv.x, wsrc, o.x);
-        if (e == 1) o.y = fmaf(cv.y, wsrc, o.y);
-        if (e == 2) o.z = fmaf(cv.z, wsrc, o.z);
-        if (e == 3) o.w = fmaf(cv.w, wsrc, o.w);
-      }
-      res[v] = o;
-      const int y = y0 + ty * C::VY + v;
-      const int x = x0 + 4 * tx;
-      if (y < a.ny && x < a.px)
-        __stcs(reinterpret_cast<float4 *>(a.unext + ((size_t)j * a.ny + y) *
-                                                        a.px + x),
-               o);
-    }
-
-    // Receivers on this plane: stage the plane, then one thread per entry.
-    if (rcur < rend && rec[rcur].x == j) {
+    for (int p = 0; p < 9; ++p) {
+      s = s0 + p;
+      if (s >= NS) break;
+      // One barrier per plane: it publishes that stage s has landed for
+      // every thread (a uniform verdict, so a timeout leaves the loop
+      // everywhere) and that every thread is done with plane s-1, whose
+      // slots the next issue may overwrite.
+      const bool ok =
+          mbar_wait_bounded(&bars[s % C::NB], (s / C::NB) & 1, kWaitLimitNs);
+      if (__syncthreads_or(!ok)) goto wait_failed;
+      if (tid == 0 && s + C::PF < NS) issue(s + C::PF);
+      // Front plane (j+4) into the queue.
+      const int fslot = (C::SU == 9) ? p : (s % C::SU);
+      const float *uf = su + fslot * C::U_SLOT;
 #pragma unroll
       for (int v = 0; v < C::VY; ++v)
-        *reinterpret_cast<float4 *>(sr + (ty * C::VY + v) * C::TX + 4 * tx) =
-            res[v];
-      __syncthreads();
-      int last = rcur;
-      while (last < rend && rec[last].x == j) ++last;
-      for (int e = rcur + tid; e < last; e += C::THREADS) {
-        const int4 r4 = rec[e];
-        trow[r4.z] = sr[r4.y];
+        q[v][p] = lds4(uf + (ty * C::VY + v + kR) * C::UW + col);
+      const int j = zb - 2 * kR + s;
+      if (j < zb) continue;
+
+      const int cslot = (C::SU == 9) ? (p + 5) % 9 : ((s + C::SU - kR) % C::SU);
+      const float *uc = su + cslot * C::U_SLOT;  // plane j
+      const float *pp = sp + (s % C::SP) * C::P_SLOT;
+      const float *pc = sc + (s % C::SP) * C::P_SLOT;
+      float4 res[C::VY];
+#pragma unroll
+      for (int v = 0; v < C::VY; ++v) {
+        const int r = ty * C::VY + v + kR;  // smem row of this point row
+        const float4 a0 = lds4(uc + r * C::UW + col - 4);
+        const float4 a1 = lds4(uc + r * C::UW + col);
+        const float4 a2 = lds4(uc + r * C::UW + col + 4);
+        const float xs[12] = {a0.x, a0.y, a0.z, a0.w, a1.x, a1.y,
+                              a1.z, a1.w, a2.x, a2.y, a2.z, a2.w};
+        float acc[4];
+#pragma unroll
+        for (int e = 0; e < 4; ++e) acc[e] = a.c0 * xs[4 + e];
+#pragma unroll
+        for (int m = 1; m <= kR; ++m) {
+          const float4 ym = lds4(uc + (r - m) * C::UW + col);
+          const float4 yp = lds4(uc + (r + m) * C::UW + col);
+          const float4 zm = q[v][(p + 5 - m + 9) % 9];
+          const float4 zp = q[v][(p + 5 + m) % 9];
+          const float cxm = a.cx[m - 1], cym = a.cy[m - 1], czm = a.cz[m - 1];
+          acc[0] = fmaf(cxm, xs[4 - m] + xs[4 + m], acc[0]);
+          acc[1] = fmaf(cxm, xs[5 - m] + xs[5 + m], acc[1]);
+          acc[2] = fmaf(cxm, xs[6 - m] + xs[6 + m], acc[2]);
+          acc[3] = fmaf(cxm, xs[7 - m] + xs[7 + m], acc[3]);
+          acc[0] = fmaf(cym, ym.x + yp.x, acc[0]);
+          acc[1] = fmaf(cym, ym.y + yp.y, acc[1]);
+          acc[2] = fmaf(cym, ym.z + yp.z, acc[2]);
+          acc[3] = fmaf(cym, ym.w + yp.w, acc[3]);
+          acc[0] = fmaf(czm, zm.x + zp.x, acc[0]);
+          acc[1] = fmaf(czm, zm.y + zp.y, acc[1]);
+          acc[2] = fmaf(czm, zm.z + zp.z, acc[2]);
+          acc[3] = fmaf(czm, zm.w + zp.w, acc[3]);
+        }
+        const int pofs = (ty * C::VY + v) * C::TX + 4 * tx;
+        const float4 upv = lds4(pp + pofs);
+        float4 cv = lds4(pc + pofs);
+        if (kVelocityField) {
+          cv.x = cv.x * cv.x * a.dt2;
+          cv.y = cv.y * cv.y * a.dt2;
+          cv.z = cv.z * cv.z * a.dt2;
+          cv.w = cv.w * cv.w * a.dt2;
+        }
+        float4 o;
+        o.x = fmaf(cv.x, acc[0], fmaf(2.f, xs[4], -upv.x));
+        o.y = fmaf(cv.y, acc[1], fmaf(2.f, xs[5], -upv.y));
+        o.z = fmaf(cv.z, acc[2], fmaf(2.f, xs[6], -upv.z));
+        o.w = fmaf(cv.w, acc[3], fmaf(2.f, xs[7], -upv.w));
+        if (src_here && j == sz && sy == ty * C::VY + v) {
+          const int e = sx - 4 * tx;
+          if (e == 0) o.x = fmaf(cv.x, wsrc, o.x);
+          if (e == 1) o.y = fmaf(cv.y, wsrc, o.y);
+          if (e == 2) o.z = fmaf(cv.z, wsrc, o.z);
+          if (e == 3) o.w = fmaf(cv.w, wsrc, o.w);
+        }
+        res[v] = o;
+        const int y = y0 + ty * C::VY + v;
+        const int x = x0 + 4 * tx;
+        if (y < a.ny && x < a.px)
+          __stcs(reinterpret_cast<float4 *>(a.unext + ((size_t)j * a.ny + y) *
+                                                          a.px + x),
+                 o);
       }
-      rcur = last;
+
+      // Receivers on this plane: stage the plane, then one thread per entry.
+      if (j == rz) {
+#pragma unroll
+        for (int v = 0; v < C::VY; ++v)
+          *reinterpret_cast<float4 *>(sr + (ty * C::VY + v) * C::TX + 4 * tx) =
+              res[v];
+        __syncthreads();
+        int last = rcur;
+        while (last < rend && rec[last].x == j) ++last;
+        for (int e = rcur + tid; e < last; e += C::THREADS) {
+          const int4 r4 = rec[e];
+          trow[r4.z] = sr[r4.y];
+        }
+        rcur = last;
+        rz = (rcur < rend) ? rec[rcur].x : 0x7fffffff;
+      }
     }
   }
+  return;
 
-  if (s < NS) {
-    // A wait gave up: record it, then drain the stages still in flight
-    // (issued: [0, s + PF)) so no TMA write lands in shared memory after this
-    // CTA has exited.
+wait_failed:
+  {
+    // A wait gave up at stage s: record it, then drain the stages still in
+    // flight (issued: [0, s + PF)) so no TMA write lands in shared memory
+    // after this CTA has exited.
     if (tid == 0) {
       atomicCAS(&a.desc->error, 0, kErrTimeout);
       const int issued = min(NS, s + C::PF);

@@ -11,6 +11,7 @@
 #include <cstdio>
 #include <cstdlib>
 #include <cstring>
+#include <functional>
 #include <new>
 #include <vector>
 
@@ -27,10 +28,15 @@ constexpr double kW[5] = {-205.0 / 72.0, 8.0 / 5.0, -1.0 / 5.0, 8.0 / 315.0,
                           -1.0 / 560.0};
 
 // Kernel variants (tile x, tile y, rows per thread, prefetch depth, CTAs/SM).
+// Variant 0 is the default: measured fastest on GB300 at 512^3 and
+// 1024 x 1024 x 512 (4 CTAs of 4 warps per SM).
+using Cfg0 = SweepCfg<32, 16, 1, 4, 4>;
 using CfgA = SweepCfg<64, 16, 1, 4, 2>;
-using CfgB = SweepCfg<64, 16, 2, 4, 2>;
-using CfgC = SweepCfg<64, 32, 2, 4, 1>;
-using CfgD = SweepCfg<32, 16, 1, 4, 3>;
+using Cfg2 = SweepCfg<32, 8, 1, 4, 6>;
+using Cfg3 = SweepCfg<32, 32, 1, 4, 2>;
+using Cfg4 = SweepCfg<64, 8, 1, 4, 3>;
+using Cfg5 = SweepCfg<16, 16, 1, 4, 6>;
+using Cfg6 = SweepCfg<32, 16, 1, 3, 4>;
 
 struct Variant {
   const void *func;
@@ -55,10 +61,13 @@ Variant make_variant() {
 
 Variant pick_variant(int which) {
   switch (which) {
-    case 1: return make_variant<CfgB>();
-    case 2: return make_variant<CfgC>();
-    case 3: return make_variant<CfgD>();
-    default: return make_variant<CfgA>();
+    case 1: return make_variant<CfgA>();
+    case 2: return make_variant<Cfg2>();
+    case 3: return make_variant<Cfg3>();
+    case 4: return make_variant<Cfg4>();
+    case 5: return make_variant<Cfg5>();
+    case 6: return make_variant<Cfg6>();
+    default: return make_variant<Cfg0>();
   }
 }
 
@@ -226,24 +235,78 @@ int build_maps(wave_ctx *c) {
   return make_map(&c->tm_c, c->c, c, tx, ty);
 }
 
-// Planes per CTA: minimise (waves of CTAs) x (planes + pre-roll cost), a
-// rough model of a launch whose CTAs all take time proportional to their
-// stage count.
-int choose_zchunk(int nz, long long ctas_xy, long long resident) {
-  int best = nz;
-  double best_cost = 1e300;
-  for (int k = 1; k <= nz; ++k) {
-    const int zc = (nz + k - 1) / k;
-    const int chunks = (nz + zc - 1) / zc;
-    const long long ctas = ctas_xy * chunks;
-    const long long waves = (ctas + resident - 1) / resident;
-    const double cost = (double)waves * (zc + 6.0);
-    if (cost < best_cost - 1e-9) {
-      best_cost = cost;
-      best = zc;
+// Makespan of one launch in plane units: CTAs start in launch order (layer
+// by layer, tiles within a layer) on the earliest free of `slots` resident
+// slots and take (planes + kPreRoll) each; kPreRoll prices the 8 u-only
+// stages that refill the register queue at the start of every CTA.
+double layer_makespan(const std::vector<int> &chunks, long long ntiles,
+                      long long slots) {
+  constexpr double kPreRoll = 4.0;
+  std::vector<double> heap((size_t)std::min<long long>(slots, 1 << 20), 0.0);
+  double end = 0.0;
+  for (int c : chunks) {
+    for (long long t = 0; t < ntiles; ++t) {
+      std::pop_heap(heap.begin(), heap.end(), std::greater<double>());
+      const double e = heap.back() + c + kPreRoll;
+      heap.back() = e;
+      std::push_heap(heap.begin(), heap.end(), std::greater<double>());
+      end = std::max(end, e);
     }
   }
-  return best;
+  return end;
+}
+
+// Split nz into at most kMaxLayers z layers: uniform splits and "k equal
+// chunks then a tail of small chunks", scored by layer_makespan.
+std::vector<int> plan_layers(int nz, long long ntiles, long long slots) {
+  std::vector<std::vector<int>> cands;
+  for (int k = 1; k <= std::min(nz, kMaxLayers); ++k) {
+    const int zc = (nz + k - 1) / k;
+    std::vector<int> ch;
+    for (int z = 0; z < nz; z += zc) ch.push_back(std::min(zc, nz - z));
+    cands.push_back(ch);
+  }
+  for (int a = 16; a < nz; a += 8) {
+    for (int b : {8, 16, 24, 32, 48, 64}) {
+      if (b >= a) continue;
+      for (int tail = 1; tail <= 4; ++tail) {
+        if (a + tail * b > nz) break;
+        std::vector<int> ch;
+        int rest = nz - tail * b;
+        while (rest >= a) { ch.push_back(a); rest -= a; }
+        if (rest > 0) ch.push_back(rest);
+        for (int t = 0; t < tail; ++t) ch.push_back(b);
+        if ((int)ch.size() <= kMaxLayers) cands.push_back(ch);
+      }
+    }
+  }
+  // Cheap pre-filter by a wave model, then simulate the best few.
+  std::vector<std::pair<double, size_t>> score;
+  for (size_t i = 0; i < cands.size(); ++i) {
+    double w = 0;
+    for (int c : cands[i]) w += c + 4.0;
+    const double waves = (double)ntiles * cands[i].size() / (double)slots;
+    score.push_back({w * ntiles / (double)slots + waves, i});
+  }
+  std::sort(score.begin(), score.end());
+  size_t best = score[0].second;
+  double best_m = 1e300;
+  const size_t nsim = std::min<size_t>(score.size(), 48);
+  for (size_t r = 0; r < nsim; ++r) {
+    const size_t i = score[r].second;
+    const double m = layer_makespan(cands[i], ntiles, slots);
+    if (m < best_m - 1e-9) {
+      best_m = m;
+      best = i;
+    }
+  }
+  return cands[best];
+}
+
+void set_layers(SweepArgs &a, const std::vector<int> &ch) {
+  a.nlayers = (int)ch.size();
+  a.zl[0] = 0;
+  for (size_t l = 0; l < ch.size(); ++l) a.zl[l + 1] = a.zl[l] + ch[l];
 }
 
 void set_coeffs(wave_ctx *c) {
@@ -252,7 +315,6 @@ void set_coeffs(wave_ctx *c) {
   a.ny = c->ny;
   a.nz = c->nz;
   a.px = c->px;
-  a.zchunk = c->zchunk;
   a.ntx = (int)c->grid.x;
   const double ix = 1.0 / (c->dx * c->dx), iy = 1.0 / (c->dy * c->dy),
                iz = 1.0 / (c->dz * c->dz);
@@ -445,11 +507,13 @@ static int create_impl(wave_ctx *c, const float *velocity) {
   const int ntx = (c->nx + c->var.tx - 1) / c->var.tx;
   const int nty = (c->ny + c->var.ty - 1) / c->var.ty;
   c->ntiles = ntx * nty;
-  c->zchunk = choose_zchunk(c->nz, (long long)c->ntiles,
-                            (long long)sms * c->ctas_per_sm);
-  c->grid = dim3(ntx, nty, (c->nz + c->zchunk - 1) / c->zchunk);
-  if (c->grid.y > 65535 || c->grid.z > 65535) return WAVE_EINVAL;
+  const std::vector<int> layers = plan_layers(
+      c->nz, (long long)c->ntiles, (long long)sms * c->ctas_per_sm);
+  c->zchunk = *std::max_element(layers.begin(), layers.end());
+  c->grid = dim3(ntx, nty, (unsigned)layers.size());
+  if (c->grid.y > 65535) return WAVE_EINVAL;
   set_coeffs(c);
+  set_layers(c->args, layers);
   int stt = build_maps(c);
   if (stt) return stt;
   const char *gs = std::getenv("GBWAVE_GRAPH_STEPS");
@@ -896,16 +960,16 @@ extern "C" int wave_propagate_noalloc(const wave_grid *g, const wave_spacing *h,
       return st;
   }
   if ((st = noalloc_map(&vmap, velocity, nx, ny, nz, C::TX, C::TY))) return st;
-  const int zchunk = choose_zchunk(nz, (long long)ntiles,
-                                   (long long)nd->sms * nd->ctas_per_sm);
-  const dim3 grid(ntx, nty, (nz + zchunk - 1) / zchunk);
-  if (grid.y > 65535 || grid.z > 65535) return WAVE_EINVAL;
+  const std::vector<int> layers =
+      plan_layers(nz, (long long)ntiles, (long long)nd->sms * nd->ctas_per_sm);
+  const dim3 grid(ntx, nty, (unsigned)layers.size());
+  if (grid.y > 65535) return WAVE_EINVAL;
   SweepArgs a{};
+  set_layers(a, layers);
   a.nx = nx;
   a.ny = ny;
   a.nz = nz;
   a.px = nx;
-  a.zchunk = zchunk;
   a.ntx = ntx;
   const double ix = 1.0 / (h->dx * h->dx), iy = 1.0 / (h->dy * h->dy),
                iz = 1.0 / (h->dz * h->dz);
