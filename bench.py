@@ -34,6 +34,8 @@ import workloads as wl  # noqa: E402
 METRIC = ("Gpts/s & % HBM roofline (r=4 3D wave, FP32 vs BF16 store); "
           "serve p50/p99 latency")
 BYTES_PER_POINT = 16  # FP32: read u, u_prev, v^2dt^2, write u_next
+BYTES_PER_POINT_16 = 10  # 16-bit u, u_prev, u_next; FP32 v^2dt^2
+STORAGE = {"f32": 0, "bf16": 1, "f16": 2}
 WORKLOADS = {"1024x1024x512": wl.CFG_1024, "512cube": wl.CFG_512, "64cube": wl.CFG_SMALL}
 KERNEL_SOURCES = ["paper_2404_04441_gb300/csrc/sweep.cuh", "paper_2404_04441_gb300/csrc/ptx.cuh"]
 TRAFFIC_FILE = "profiles/sweep_f32_traffic.txt"
@@ -177,6 +179,34 @@ def oracle_sample(vel, cfg, dt, budget_s, nsteps_cap=None):
     return pts / el / 1e9, oracle.threads_used(), sample, el
 
 
+def precision_errors(gw, torch):
+    """Relative L2 of fields and traces against the FP64 oracle for each storage
+    mode on the random 8-layer 128^3 model, Ricker at (64, 64, 10), receivers
+    on z = 8 every 4th point, 500 steps."""
+    import oracle
+    n, nsteps = 128, 500
+    vel = wl.random_layered(n, n, n, seed=0)
+    sp = (10.0, 10.0, 10.0)
+    dt = 0.5 * gw.wave_cfl_dt(sp, float(vel.max()))
+    rec = wl.receiver_plane(n, n, 8, 4)
+    shot = (64, 64, 10, 15.0, -1.0, 1.0)
+    ou, _, otr = oracle.propagate(vel, sp, dt, nsteps, source=shot, receivers=rec)
+    out = {}
+    for name, st in STORAGE.items():
+        s = gw.WaveSolver((n, n, n), sp, dt, torch.from_numpy(vel).cuda(), storage=st)
+        tr = torch.zeros((nsteps, rec.shape[0]), device="cuda")
+        s.propagate(shot, nsteps, torch.from_numpy(rec).cuda(), tr)
+        u = np.empty((n, n, n), np.float32)
+        s.get_field(0, u)
+        s.close()
+        trh = tr.cpu().numpy().astype(np.float64)
+        out[name] = {
+            "rel_l2_field": float(np.linalg.norm(u - ou) / np.linalg.norm(ou)),
+            "rel_l2_traces": float(np.linalg.norm(trh - otr) / np.linalg.norm(otr)),
+            "workload": "random8layer_128cube, 500 steps"}
+    return out
+
+
 def run_reference(args, cfg):
     """The reference arm: the FP64 CPU oracle on this machine's host cores."""
     rank, world, _ = dist_env()
@@ -237,6 +267,8 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--variant", type=int, default=None, help="sweep kernel variant (tuning)")
+    ap.add_argument("--no-precision", action="store_true",
+                    help="skip the BF16/FP16 storage measurements")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
     cfg = WORKLOADS[args.workload]
@@ -345,6 +377,46 @@ def main():
                 "algorithmic_bytes_per_launch": BYTES_PER_POINT * npts,
                 "kernel": "wave_sweep_kernel"}
 
+    # ---- 16-bit storage forms: same workload and K; error on 128^3 x 500 ---
+    precision = None
+    if not args.no_precision:
+        precision = {}
+        for name in ("bf16", "f16"):
+            s16 = gw.WaveSolver((nx, ny, nz), sp, dt, vel_d, storage=STORAGE[name],
+                                stream=stream.cuda_stream)
+            tr16 = torch.empty((max(K, W), nrec), dtype=torch.float32, device="cuda")
+            s16.propagate(shot, W, rec_d, tr16)
+            s16.reset()
+            barrier()
+            torch.cuda.synchronize()
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            s16.propagate(shot, K, rec_d, tr16)
+            e1.record(stream)
+            e1.synchronize()
+            s16.synchronize()
+            ms16 = e0.elapsed_time(e1)
+            if world > 1:
+                t = torch.tensor([ms16], device="cuda")
+                torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+                ms16 = float(t.item())
+            s16.close()
+            del tr16
+            v16 = world * npts * K / (ms16 * 1e-3) / 1e9
+            ach = BYTES_PER_POINT_16 * npts / (ms16 * 1e-3 / K) / 1e9
+            precision[name] = {"value": v16, "unit": "Gpts/s", "ms_per_step": ms16 / K,
+                               "vs_f32": v16 / value,
+                               "roofline": {"bound": "hbm", "achieved": ach,
+                                            "peak": peaks["hbm_gbs"], "unit": "GB/s",
+                                            "frac": ach / peaks["hbm_gbs"],
+                                            "algorithmic_bytes_per_point": BYTES_PER_POINT_16}}
+        if rank == 0:
+            err = precision_errors(gw, torch)
+            for name in ("bf16", "f16"):
+                precision[name]["error_vs_fp64_oracle"] = err[name]
+            precision["f32_error_vs_fp64_oracle"] = err["f32"]
+
     cpu = None
     if rank == 0 and not args.no_cpu_baseline:
         g, cores, sample, el = oracle_sample(vel, cfg, dt, budget_s=15.0)
@@ -367,6 +439,7 @@ def main():
                        "launch": info},
             "e2e": e2e, "gpu_launches": launches, "roofline": roofline,
             "cpu_baseline": cpu, "clocks": clocks, "traces_finite": tr_ok,
+            "precision_forms": precision,
         }
         print(json.dumps(line), flush=True)
     if world > 1:

@@ -10,14 +10,24 @@
 //     the register queue and, four planes later, as the xy plane of Eq. 1;
 //   * u_prev and v^2 dt^2 at plane j, the tile only.
 // TMA's out-of-bounds zero fill supplies the zero Dirichlet halo, so the
-// fields are stored without padding planes (rows are padded to 4 floats).
-// Each thread computes 4 consecutive x points (float4) on VY rows, reads the
-// x and y neighbours from the xy plane in shared memory and the z neighbours
-// from its queue, and writes u_next over u_prev with 128-bit streaming
-// stores. The Ricker source and the receivers are applied in the same pass.
+// fields are stored without padding planes (rows are padded to 16 bytes).
+// Each thread computes 4 consecutive x points on VY rows, reads the x and y
+// neighbours from the xy plane in shared memory and the z neighbours from its
+// queue, and writes u_next over u_prev with streaming stores. The Ricker
+// source and the receivers are applied in the same pass.
+//
+// Storage: the wavefields are FP32, BF16 or FP16 (template type T); the
+// arithmetic is FP32 in every case and v^2 dt^2 is always FP32. A 16-bit
+// field holding time step k carries a power-of-two scale 2^e_k: value =
+// stored * 2^e_k. The scale of each newly written field is chosen from the
+// largest magnitudes of the two fields it is computed from, with headroom for
+// the largest possible growth in one step, so FP16 never overflows; the
+// scale factors are exact powers of two, so scaling adds no rounding.
 #pragma once
 
 #include <cuda.h>
+#include <cuda_bf16.h>
+#include <cuda_fp16.h>
 #include <cstdint>
 
 #include "ptx.cuh"
@@ -28,9 +38,11 @@ constexpr int kR = 4;                // stencil radius (Sec. 4.1: R = 4)
 constexpr int kErrTimeout = 1;       // device error word values
 constexpr uint64_t kWaitLimitNs = 2000000000ull;
 
-// Per-call state read by every sweep launch (device memory, one per context).
+// Per-context state read by every sweep launch (device memory). The fields
+// up to `error` are rewritten at each call; the rest persist.
 struct StepDesc {
   long long n;            // index of the next step within the current call
+  long long step0;        // absolute step number of the call's first step
   const float *wavelet;   // source value per step of the call (or null)
   float *traces;          // nsteps x nrec, row n written by step n (or null)
   const int4 *rec;        // receivers sorted by (tile, z): {z, local, id, 0}
@@ -39,12 +51,16 @@ struct StepDesc {
   int src_active;
   int sx, sy, sz;
   int error;              // first error recorded by a kernel (0 = none)
+  // 16-bit storage only: the field holding absolute step k has scale
+  // 2^exps[k & 3] and largest magnitude maxbits[k & 3] (bits of a float).
+  int exps[4];
+  unsigned maxbits[4];
 };
 
 constexpr int kMaxLayers = 16;
 
 struct SweepArgs {
-  int nx, ny, nz, px;  // interior sizes; px = row pitch in floats (mult. of 4)
+  int nx, ny, nz, px;  // interior sizes; px = row pitch in elements (16 B rows)
   // z layers: CTAs with blockIdx.z == l stream planes [zl[l], zl[l+1]).
   // Layers are launched in order, so large layers first and small ones last
   // shorten the partial last wave of CTAs.
@@ -53,34 +69,146 @@ struct SweepArgs {
   int ntx;             // tiles along x (tile id = by * ntx + bx)
   float c0;            // w0 * (1/dx^2 + 1/dy^2 + 1/dz^2)
   float cx[4], cy[4], cz[4];  // w_m / h_a^2 for m = 1..4
-  float *unext;        // output: the u_prev buffer, overwritten in place
+  void *unext;         // output: the u_prev buffer, overwritten in place
   StepDesc *desc;
   int koff;            // step offset of this launch within a graph chunk
   float dt2;           // dt^2, used only when the c field holds velocities
+  float cmax;          // largest v^2 dt^2 (16-bit storage: growth bound)
 };
 
-template <int TX_, int TY_, int VY_, int PF_, int MINB_>
+// Element access per storage type: 4 consecutive elements to/from float4.
+template <class T>
+struct Elem;
+
+template <>
+struct Elem<float> {
+  static constexpr int kHaloX = 4;  // box starts 4 elements left (16 B)
+  __device__ static __forceinline__ float4 load4(const float *p) {
+    return *reinterpret_cast<const float4 *>(p);
+  }
+  __device__ static __forceinline__ void store4_cs(float *p, float4 v) {
+    __stcs(reinterpret_cast<float4 *>(p), v);
+  }
+};
+
+template <>
+struct Elem<__nv_bfloat16> {
+  static constexpr int kHaloX = 8;  // 16-byte aligned box start: 8 elements
+  __device__ static __forceinline__ float4 load4(const __nv_bfloat16 *p) {
+    const uint2 w = *reinterpret_cast<const uint2 *>(p);
+    // A bf16 is the upper half of the float with the same bits.
+    return make_float4(__uint_as_float(w.x << 16),
+                       __uint_as_float(w.x & 0xffff0000u),
+                       __uint_as_float(w.y << 16),
+                       __uint_as_float(w.y & 0xffff0000u));
+  }
+  __device__ static __forceinline__ uint2 load_raw(const __nv_bfloat16 *p) {
+    return *reinterpret_cast<const uint2 *>(p);
+  }
+  // Element k (0..3) of a raw 4-element load, as FP32 (exact).
+  __device__ static __forceinline__ float unpack(uint2 w, int k) {
+    const unsigned x = (k < 2) ? w.x : w.y;
+    return (k & 1) ? __uint_as_float(x & 0xffff0000u) : __uint_as_float(x << 16);
+  }
+  // Element k of a raw load plus an FP32 value, rounded once (the same result
+  // as unpack(w, k) + c) in one mixed-precision add.
+  __device__ static __forceinline__ float add_to(uint2 w, int k, float c) {
+    const unsigned x = (k < 2) ? w.x : w.y;
+    float d;
+    if (k & 1)
+      asm("{\n\t.reg .b16 l, h;\n\tmov.b32 {l, h}, %1;\n\t"
+          "add.rn.f32.bf16 %0, h, %2;\n\t}"
+          : "=f"(d) : "r"(x), "f"(c));
+    else
+      asm("{\n\t.reg .b16 l, h;\n\tmov.b32 {l, h}, %1;\n\t"
+          "add.rn.f32.bf16 %0, l, %2;\n\t}"
+          : "=f"(d) : "r"(x), "f"(c));
+    return d;
+  }
+  __device__ static __forceinline__ void store4_cs(__nv_bfloat16 *p, float4 v) {
+    const __nv_bfloat162 a = __floats2bfloat162_rn(v.x, v.y);
+    const __nv_bfloat162 b = __floats2bfloat162_rn(v.z, v.w);
+    uint2 w;
+    w.x = *reinterpret_cast<const unsigned *>(&a);
+    w.y = *reinterpret_cast<const unsigned *>(&b);
+    __stcs(reinterpret_cast<uint2 *>(p), w);
+  }
+};
+
+template <>
+struct Elem<__half> {
+  static constexpr int kHaloX = 8;
+  __device__ static __forceinline__ float4 load4(const __half *p) {
+    const uint2 w = *reinterpret_cast<const uint2 *>(p);
+    const float2 a = __half22float2(*reinterpret_cast<const __half2 *>(&w.x));
+    const float2 b = __half22float2(*reinterpret_cast<const __half2 *>(&w.y));
+    return make_float4(a.x, a.y, b.x, b.y);
+  }
+  __device__ static __forceinline__ uint2 load_raw(const __half *p) {
+    return *reinterpret_cast<const uint2 *>(p);
+  }
+  __device__ static __forceinline__ float unpack(uint2 w, int k) {
+    const unsigned x = (k < 2) ? w.x : w.y;
+    const __half2 h = *reinterpret_cast<const __half2 *>(&x);
+    return (k & 1) ? __high2float(h) : __low2float(h);
+  }
+  __device__ static __forceinline__ float add_to(uint2 w, int k, float c) {
+    const unsigned x = (k < 2) ? w.x : w.y;
+    float d;
+    if (k & 1)
+      asm("{\n\t.reg .b16 l, h;\n\tmov.b32 {l, h}, %1;\n\t"
+          "add.rn.f32.f16 %0, h, %2;\n\t}"
+          : "=f"(d) : "r"(x), "f"(c));
+    else
+      asm("{\n\t.reg .b16 l, h;\n\tmov.b32 {l, h}, %1;\n\t"
+          "add.rn.f32.f16 %0, l, %2;\n\t}"
+          : "=f"(d) : "r"(x), "f"(c));
+    return d;
+  }
+  __device__ static __forceinline__ void store4_cs(__half *p, float4 v) {
+    const __half2 a = __floats2half2_rn(v.x, v.y);
+    const __half2 b = __floats2half2_rn(v.z, v.w);
+    uint2 w;
+    w.x = *reinterpret_cast<const unsigned *>(&a);
+    w.y = *reinterpret_cast<const unsigned *>(&b);
+    __stcs(reinterpret_cast<uint2 *>(p), w);
+  }
+};
+
+template <int TX_, int TY_, int VY_, int PF_, int MINB_, class T_ = float>
 struct SweepCfg {
+  using T = T_;
   static constexpr int TX = TX_, TY = TY_, VY = VY_, PF = PF_, MINB = MINB_;
-  static constexpr int NTX = TX / 4;       // threads along x (4 points each)
-  static constexpr int NTY = TY / VY;      // threads along y (VY rows each)
+  static constexpr bool kScaled = sizeof(T) == 2;
+  static constexpr int HX = Elem<T>::kHaloX;  // box columns left of the tile
+  static constexpr int NTX = TX / 4;          // threads along x (4 points each)
+  static constexpr int NTY = TY / VY;         // threads along y (VY rows each)
   static constexpr int THREADS = NTX * NTY;
-  static constexpr int SU = PF + 5;        // u ring: 5 live planes + prefetch
-  static constexpr int SP = PF + 1;        // u_prev / c ring
-  static constexpr int NB = PF + 1;        // one barrier per in-flight stage
-  static constexpr int UW = TX + 2 * kR;   // u slot row length (floats)
+  static constexpr int SU = PF + 5;           // u ring: 5 live planes + prefetch
+  static constexpr int SP = PF + 1;           // u_prev / c ring
+  static constexpr int NB = PF + 1;           // one barrier per in-flight stage
+  static constexpr int UW = TX + 2 * HX;      // u slot row length (elements)
   static constexpr int UH = TY + 2 * kR;
-  static constexpr int U_SLOT = UW * UH;   // floats
-  static constexpr int P_SLOT = TX * TY;
-  static constexpr uint32_t U_BYTES = U_SLOT * 4;
-  static constexpr uint32_t P_BYTES = P_SLOT * 4;
-  static constexpr size_t SMEM_BYTES =
-      128 + (size_t)(SU * U_SLOT + 2 * SP * P_SLOT + P_SLOT) * 4 + NB * 8;
+  static constexpr int U_SLOT = UW * UH;      // elements
+  static constexpr int P_SLOT = TX * TY;      // elements
+  static constexpr uint32_t U_BYTES = U_SLOT * sizeof(T);
+  static constexpr uint32_t UP_BYTES = P_SLOT * sizeof(T);
+  static constexpr uint32_t C_BYTES = P_SLOT * 4;
+  static constexpr size_t SMEM_BYTES = 128 + (size_t)SU * U_BYTES +
+                                       (size_t)SP * (UP_BYTES + C_BYTES) +
+                                       C_BYTES + NB * 8;
   static_assert(TX % 4 == 0 && TY % VY == 0, "tile shape");
-  static_assert((UW * 4) % 16 == 0, "TMA box row must be a multiple of 16 B");
-  static_assert(U_BYTES % 128 == 0 && P_BYTES % 128 == 0, "slot alignment");
+  static_assert((UW * sizeof(T)) % 16 == 0, "TMA box row: multiple of 16 B");
+  static_assert((TX * sizeof(T)) % 16 == 0, "TMA box row: multiple of 16 B");
+  static_assert(U_BYTES % 128 == 0 && UP_BYTES % 128 == 0 &&
+                    C_BYTES % 128 == 0,
+                "slot alignment");
   static_assert(UW <= 256 && UH <= 256, "TMA box limit");
 };
+
+__device__ __forceinline__ float exp2_int(int k) {
+  return ldexpf(1.0f, max(-126, min(127, k)));
+}
 
 // kVelocityField = false: tm_c maps v^2 dt^2. true: tm_c maps the velocity
 // itself and the kernel forms v^2 dt^2 from it (the allocation-free entry
@@ -91,11 +219,15 @@ __global__ void __launch_bounds__(C::THREADS, C::MINB)
                       const __grid_constant__ CUtensorMap tm_up,
                       const __grid_constant__ CUtensorMap tm_c,
                       const SweepArgs a) {
+  using T = typename C::T;
+  using E = Elem<T>;
   extern __shared__ unsigned char smem_raw[];
-  float *su = reinterpret_cast<float *>(
+  unsigned char *base = reinterpret_cast<unsigned char *>(
       (reinterpret_cast<uintptr_t>(smem_raw) + 127) & ~uintptr_t(127));
-  float *sp = su + C::SU * C::U_SLOT;
-  float *sc = sp + C::SP * C::P_SLOT;
+  T *su = reinterpret_cast<T *>(base);
+  T *sp = reinterpret_cast<T *>(base + C::SU * C::U_BYTES);
+  float *sc = reinterpret_cast<float *>(base + C::SU * C::U_BYTES +
+                                        C::SP * C::UP_BYTES);
   float *sr = sc + C::SP * C::P_SLOT;  // receiver staging (one plane)
   uint64_t *bars = reinterpret_cast<uint64_t *>(sr + C::P_SLOT);
 
@@ -109,13 +241,13 @@ __global__ void __launch_bounds__(C::THREADS, C::MINB)
   const int NS = (ze - zb) + 2 * kR;  // stages: 8 to fill the queue, then one per plane
 
   // Per-call state.
-  const StepDesc *d = a.desc;
+  StepDesc *d = a.desc;
   const long long n = d->n + a.koff;
   const int nrec = d->nrec;
   const int sx = d->sx - x0, sy = d->sy - y0, sz = d->sz;
   const bool src_here = d->src_active && sx >= 0 && sx < C::TX && sy >= 0 &&
                         sy < C::TY && sz >= zb && sz < ze;
-  const float wsrc = src_here ? d->wavelet[n] : 0.f;
+  float wsrc = src_here ? d->wavelet[n] : 0.f;
   int rcur = 0, rend = 0;
   const int4 *rec = d->rec;
   if (nrec > 0) {
@@ -126,6 +258,37 @@ __global__ void __launch_bounds__(C::THREADS, C::MINB)
   }
   int rz = (rcur < rend) ? rec[rcur].x : 0x7fffffff;  // z of the next receiver
   float *trow = (nrec > 0) ? d->traces + (size_t)n * nrec : nullptr;
+
+  // 16-bit storage: scales of the input fields (absolute steps ab and ab-1)
+  // and of the output field (step ab+1). The output scale bounds the new
+  // field: |u_next| <= 2|u| + |u_prev| + c |L u| <= 7 max(|u|, |u_prev|) for
+  // dt within the stability limit (c |L u| <= 4 max|u|), plus the source;
+  // 8 x that bound maps to at most 2^15 in the stored format.
+  float s1 = 1.f, s2 = 1.f, so = 1.f;
+  long long ab = 0;
+  if constexpr (C::kScaled) {
+    ab = d->step0 + n;
+    const int eu = d->exps[ab & 3], eup = d->exps[(ab + 3) & 3];
+    const float mu = __uint_as_float(d->maxbits[ab & 3]);
+    const float mup = __uint_as_float(d->maxbits[(ab + 3) & 3]);
+    float bound = 8.f * fmaxf(mu, mup);
+    if (d->src_active) bound += a.cmax * fabsf(d->wavelet[n]);
+    int eo = 0;
+    if (bound > 0.f) {
+      int e2;
+      frexpf(bound, &e2);  // bound <= 2^e2
+      eo = e2 - 15;
+    }
+    s1 = exp2_int(eu - eo);
+    s2 = exp2_int(eup - eo);
+    so = exp2_int(eo);
+    wsrc *= exp2_int(-eo);
+    if (blockIdx.x == 0 && blockIdx.y == 0 && blockIdx.z == 0 && tid == 0) {
+      d->exps[(ab + 1) & 3] = eo;     // read by the next step only
+      d->maxbits[(ab + 2) & 3] = 0u;  // accumulated by the next step
+    }
+  }
+  float vmax_out = 0.f;  // largest |output| of this thread (stored units)
 
   if (tid == 0) {
     prefetch_tensormap(&tm_u);
@@ -142,8 +305,9 @@ __global__ void __launch_bounds__(C::THREADS, C::MINB)
     uint64_t *bar = &bars[s % C::NB];
     const int j = zb - 2 * kR + s;
     const bool full = j >= zb;
-    mbar_arrive_expect_tx(bar, C::U_BYTES + (full ? 2 * C::P_BYTES : 0));
-    tma_load_3d(su + (s % C::SU) * C::U_SLOT, &tm_u, bar, x0 - kR, y0 - kR,
+    mbar_arrive_expect_tx(bar,
+                          C::U_BYTES + (full ? C::UP_BYTES + C::C_BYTES : 0));
+    tma_load_3d(su + (s % C::SU) * C::U_SLOT, &tm_u, bar, x0 - C::HX, y0 - kR,
                 j + kR);
     if (full) {
       tma_load_3d(sp + (s % C::SP) * C::P_SLOT, &tm_up, bar, x0, y0, j);
@@ -164,7 +328,7 @@ __global__ void __launch_bounds__(C::THREADS, C::MINB)
 #pragma unroll
     for (int k = 0; k < 9; ++k) q[v][k] = make_float4(0.f, 0.f, 0.f, 0.f);
 
-  const int col = 4 * tx + kR;  // smem column of this thread's first point
+  const int col = 4 * tx + C::HX;  // smem column of this thread's first point
   int s = 0;
   for (int s0 = 0; s0 < NS; s0 += 9) {
 #pragma unroll
@@ -181,63 +345,131 @@ __global__ void __launch_bounds__(C::THREADS, C::MINB)
       if (tid == 0 && s + C::PF < NS) issue(s + C::PF);
       // Front plane (j+4) into the queue.
       const int fslot = (C::SU == 9) ? p : (s % C::SU);
-      const float *uf = su + fslot * C::U_SLOT;
+      const T *uf = su + fslot * C::U_SLOT;
 #pragma unroll
       for (int v = 0; v < C::VY; ++v)
-        q[v][p] = lds4(uf + (ty * C::VY + v + kR) * C::UW + col);
+        q[v][p] = E::load4(uf + (ty * C::VY + v + kR) * C::UW + col);
       const int j = zb - 2 * kR + s;
       if (j < zb) continue;
 
       const int cslot = (C::SU == 9) ? (p + 5) % 9 : ((s + C::SU - kR) % C::SU);
-      const float *uc = su + cslot * C::U_SLOT;  // plane j
-      const float *pp = sp + (s % C::SP) * C::P_SLOT;
+      const T *uc = su + cslot * C::U_SLOT;  // plane j
+      const T *pp = sp + (s % C::SP) * C::P_SLOT;
       const float *pc = sc + (s % C::SP) * C::P_SLOT;
       float4 res[C::VY];
 #pragma unroll
       for (int v = 0; v < C::VY; ++v) {
         const int r = ty * C::VY + v + kR;  // smem row of this point row
-        const float4 a0 = lds4(uc + r * C::UW + col - 4);
-        const float4 a1 = lds4(uc + r * C::UW + col);
-        const float4 a2 = lds4(uc + r * C::UW + col + 4);
-        const float xs[12] = {a0.x, a0.y, a0.z, a0.w, a1.x, a1.y,
-                              a1.z, a1.w, a2.x, a2.y, a2.z, a2.w};
-        float acc[4];
+        // The centre plane j of this thread's points is already in the queue.
+        const float4 a1 = q[v][(p + 5) % 9];
+        // Packed FP32x2 arithmetic: points (0,1) in `lo`, (2,3) in `hi`.
+        // Lane-wise it is the same sequence of IEEE round-to-nearest
+        // additions and fused multiply-adds as the scalar form.
+        float2 lo = __fmul2_rn(make_float2(a.c0, a.c0), make_float2(a1.x, a1.y));
+        float2 hi = __fmul2_rn(make_float2(a.c0, a.c0), make_float2(a1.z, a1.w));
+        if constexpr (!C::kScaled) {
+          const float4 a0 = E::load4(uc + r * C::UW + col - 4);
+          const float4 a2 = E::load4(uc + r * C::UW + col + 4);
+          const float xs[12] = {a0.x, a0.y, a0.z, a0.w, a1.x, a1.y,
+                                a1.z, a1.w, a2.x, a2.y, a2.z, a2.w};
 #pragma unroll
-        for (int e = 0; e < 4; ++e) acc[e] = a.c0 * xs[4 + e];
+          for (int m = 1; m <= kR; ++m) {
+            const float4 ym = E::load4(uc + (r - m) * C::UW + col);
+            const float4 yp = E::load4(uc + (r + m) * C::UW + col);
+            const float4 zm = q[v][(p + 5 - m + 9) % 9];
+            const float4 zp = q[v][(p + 5 + m) % 9];
+            const float2 cx2 = make_float2(a.cx[m - 1], a.cx[m - 1]);
+            const float2 cy2 = make_float2(a.cy[m - 1], a.cy[m - 1]);
+            const float2 cz2 = make_float2(a.cz[m - 1], a.cz[m - 1]);
+            float2 xl, xh;
+            if (m % 2 == 0) {  // operands are aligned register pairs
+              xl = __fadd2_rn(make_float2(xs[4 - m], xs[5 - m]),
+                              make_float2(xs[4 + m], xs[5 + m]));
+              xh = __fadd2_rn(make_float2(xs[6 - m], xs[7 - m]),
+                              make_float2(xs[6 + m], xs[7 + m]));
+            } else {
+              xl = make_float2(xs[4 - m] + xs[4 + m], xs[5 - m] + xs[5 + m]);
+              xh = make_float2(xs[6 - m] + xs[6 + m], xs[7 - m] + xs[7 + m]);
+            }
+            lo = __ffma2_rn(cx2, xl, lo);
+            hi = __ffma2_rn(cx2, xh, hi);
+            lo = __ffma2_rn(cy2, __fadd2_rn(make_float2(ym.x, ym.y),
+                                            make_float2(yp.x, yp.y)), lo);
+            hi = __ffma2_rn(cy2, __fadd2_rn(make_float2(ym.z, ym.w),
+                                            make_float2(yp.z, yp.w)), hi);
+            lo = __ffma2_rn(cz2, __fadd2_rn(make_float2(zm.x, zm.y),
+                                            make_float2(zp.x, zp.y)), lo);
+            hi = __ffma2_rn(cz2, __fadd2_rn(make_float2(zm.z, zm.w),
+                                            make_float2(zp.z, zp.w)), hi);
+          }
+        } else {
+          // 16-bit planes: each neighbour pair sum is one mixed-precision add
+          // of a stored element to an FP32 value (the other element, taken
+          // from the queue or converted once), never a second conversion.
+          const uint2 r0 = E::load_raw(uc + r * C::UW + col - 4);
+          const uint2 r2 = E::load_raw(uc + r * C::UW + col + 4);
+          const float c1[4] = {a1.x, a1.y, a1.z, a1.w};
+          // x slot i of this row: 0..3 in r0, 4..7 = centre (FP32), 8..11 in r2
+          auto xpair = [&](int i, int j) -> float {
+            const bool i32 = i >= 4 && i < 8, j32 = j >= 4 && j < 8;
+            const uint2 ri = (i < 4) ? r0 : r2, rj = (j < 4) ? r0 : r2;
+            if (i32 && j32) return c1[i - 4] + c1[j - 4];
+            if (i32) return E::add_to(rj, j & 3, c1[i - 4]);
+            if (j32) return E::add_to(ri, i & 3, c1[j - 4]);
+            return E::add_to(ri, i & 3, E::unpack(rj, j & 3));
+          };
 #pragma unroll
-        for (int m = 1; m <= kR; ++m) {
-          const float4 ym = lds4(uc + (r - m) * C::UW + col);
-          const float4 yp = lds4(uc + (r + m) * C::UW + col);
-          const float4 zm = q[v][(p + 5 - m + 9) % 9];
-          const float4 zp = q[v][(p + 5 + m) % 9];
-          const float cxm = a.cx[m - 1], cym = a.cy[m - 1], czm = a.cz[m - 1];
-          acc[0] = fmaf(cxm, xs[4 - m] + xs[4 + m], acc[0]);
-          acc[1] = fmaf(cxm, xs[5 - m] + xs[5 + m], acc[1]);
-          acc[2] = fmaf(cxm, xs[6 - m] + xs[6 + m], acc[2]);
-          acc[3] = fmaf(cxm, xs[7 - m] + xs[7 + m], acc[3]);
-          acc[0] = fmaf(cym, ym.x + yp.x, acc[0]);
-          acc[1] = fmaf(cym, ym.y + yp.y, acc[1]);
-          acc[2] = fmaf(cym, ym.z + yp.z, acc[2]);
-          acc[3] = fmaf(cym, ym.w + yp.w, acc[3]);
-          acc[0] = fmaf(czm, zm.x + zp.x, acc[0]);
-          acc[1] = fmaf(czm, zm.y + zp.y, acc[1]);
-          acc[2] = fmaf(czm, zm.z + zp.z, acc[2]);
-          acc[3] = fmaf(czm, zm.w + zp.w, acc[3]);
+          for (int m = 1; m <= kR; ++m) {
+            const uint2 ym = E::load_raw(uc + (r - m) * C::UW + col);
+            const uint2 yp = E::load_raw(uc + (r + m) * C::UW + col);
+            const float4 zm = q[v][(p + 5 - m + 9) % 9];
+            const float4 zp = q[v][(p + 5 + m) % 9];
+            const float2 cx2 = make_float2(a.cx[m - 1], a.cx[m - 1]);
+            const float2 cy2 = make_float2(a.cy[m - 1], a.cy[m - 1]);
+            const float2 cz2 = make_float2(a.cz[m - 1], a.cz[m - 1]);
+            const float2 xl = make_float2(xpair(4 - m, 4 + m), xpair(5 - m, 5 + m));
+            const float2 xh = make_float2(xpair(6 - m, 6 + m), xpair(7 - m, 7 + m));
+            const float2 yl = make_float2(E::add_to(ym, 0, E::unpack(yp, 0)),
+                                          E::add_to(ym, 1, E::unpack(yp, 1)));
+            const float2 yh = make_float2(E::add_to(ym, 2, E::unpack(yp, 2)),
+                                          E::add_to(ym, 3, E::unpack(yp, 3)));
+            lo = __ffma2_rn(cx2, xl, lo);
+            hi = __ffma2_rn(cx2, xh, hi);
+            lo = __ffma2_rn(cy2, yl, lo);
+            hi = __ffma2_rn(cy2, yh, hi);
+            lo = __ffma2_rn(cz2, __fadd2_rn(make_float2(zm.x, zm.y),
+                                            make_float2(zp.x, zp.y)), lo);
+            hi = __ffma2_rn(cz2, __fadd2_rn(make_float2(zm.z, zm.w),
+                                            make_float2(zp.z, zp.w)), hi);
+          }
         }
         const int pofs = (ty * C::VY + v) * C::TX + 4 * tx;
-        const float4 upv = lds4(pp + pofs);
-        float4 cv = lds4(pc + pofs);
+        const float4 upv = E::load4(pp + pofs);
+        float4 cv = *reinterpret_cast<const float4 *>(pc + pofs);
         if (kVelocityField) {
           cv.x = cv.x * cv.x * a.dt2;
           cv.y = cv.y * cv.y * a.dt2;
           cv.z = cv.z * cv.z * a.dt2;
           cv.w = cv.w * cv.w * a.dt2;
         }
-        float4 o;
-        o.x = fmaf(cv.x, acc[0], fmaf(2.f, xs[4], -upv.x));
-        o.y = fmaf(cv.y, acc[1], fmaf(2.f, xs[5], -upv.y));
-        o.z = fmaf(cv.z, acc[2], fmaf(2.f, xs[6], -upv.z));
-        o.w = fmaf(cv.w, acc[3], fmaf(2.f, xs[7], -upv.w));
+        const float2 cvl = make_float2(cv.x, cv.y), cvh = make_float2(cv.z, cv.w);
+        const float2 ul = make_float2(a1.x, a1.y), uh = make_float2(a1.z, a1.w);
+        const float2 pl = make_float2(-upv.x, -upv.y);
+        const float2 ph = make_float2(-upv.z, -upv.w);
+        float2 ol, oh;
+        if constexpr (C::kScaled) {
+          // Stored units: u = 2^eu U, u_prev = 2^eup UP, output 2^eo O.
+          const float2 s1v = make_float2(s1, s1), s2v = make_float2(s2, s2);
+          ol = __ffma2_rn(s1v, __ffma2_rn(cvl, lo, __fadd2_rn(ul, ul)),
+                          __fmul2_rn(s2v, pl));
+          oh = __ffma2_rn(s1v, __ffma2_rn(cvh, hi, __fadd2_rn(uh, uh)),
+                          __fmul2_rn(s2v, ph));
+        } else {
+          const float2 two = make_float2(2.f, 2.f);
+          ol = __ffma2_rn(cvl, lo, __ffma2_rn(two, ul, pl));
+          oh = __ffma2_rn(cvh, hi, __ffma2_rn(two, uh, ph));
+        }
+        float4 o = make_float4(ol.x, ol.y, oh.x, oh.y);
         if (src_here && j == sz && sy == ty * C::VY + v) {
           const int e = sx - 4 * tx;
           if (e == 0) o.x = fmaf(cv.x, wsrc, o.x);
@@ -245,21 +477,33 @@ __global__ void __launch_bounds__(C::THREADS, C::MINB)
           if (e == 2) o.z = fmaf(cv.z, wsrc, o.z);
           if (e == 3) o.w = fmaf(cv.w, wsrc, o.w);
         }
+        if constexpr (C::kScaled) {
+          vmax_out = fmaxf(vmax_out, fmaxf(fmaxf(fabsf(o.x), fabsf(o.y)),
+                                           fmaxf(fabsf(o.z), fabsf(o.w))));
+        }
         res[v] = o;
         const int y = y0 + ty * C::VY + v;
         const int x = x0 + 4 * tx;
         if (y < a.ny && x < a.px)
-          __stcs(reinterpret_cast<float4 *>(a.unext + ((size_t)j * a.ny + y) *
-                                                          a.px + x),
-                 o);
+          E::store4_cs(reinterpret_cast<T *>(a.unext) +
+                           ((size_t)j * a.ny + y) * a.px + x,
+                       o);
       }
 
       // Receivers on this plane: stage the plane, then one thread per entry.
       if (j == rz) {
 #pragma unroll
-        for (int v = 0; v < C::VY; ++v)
+        for (int v = 0; v < C::VY; ++v) {
+          float4 t = res[v];
+          if constexpr (C::kScaled) {
+            t.x *= so;
+            t.y *= so;
+            t.z *= so;
+            t.w *= so;
+          }
           *reinterpret_cast<float4 *>(sr + (ty * C::VY + v) * C::TX + 4 * tx) =
-              res[v];
+              t;
+        }
         __syncthreads();
         int last = rcur;
         while (last < rend && rec[last].x == j) ++last;
@@ -271,6 +515,14 @@ __global__ void __launch_bounds__(C::THREADS, C::MINB)
         rz = (rcur < rend) ? rec[rcur].x : 0x7fffffff;
       }
     }
+  }
+  if constexpr (C::kScaled) {
+    // Largest |u_next| of the step, for the scale of the step after it.
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1)
+      vmax_out = fmaxf(vmax_out, __shfl_xor_sync(0xffffffffu, vmax_out, o));
+    if ((tid & 31) == 0 && vmax_out > 0.f)
+      atomicMax(&d->maxbits[(ab + 1) & 3], __float_as_uint(vmax_out * so));
   }
   return;
 

@@ -27,21 +27,29 @@ namespace {
 constexpr double kW[5] = {-205.0 / 72.0, 8.0 / 5.0, -1.0 / 5.0, 8.0 / 315.0,
                           -1.0 / 560.0};
 
-// Kernel variants (tile x, tile y, rows per thread, prefetch depth, CTAs/SM).
-// Variant 0 is the default: measured fastest on GB300 at 512^3 and
-// 1024 x 1024 x 512 (4 CTAs of 4 warps per SM).
+// Kernel variants (tile x, tile y, rows per thread, prefetch depth, CTAs/SM,
+// storage type). Variant 0 of each storage is the default, measured fastest
+// on GB300 at 1024 x 1024 x 512 and 512^3; the others stay selectable
+// (GBWAVE_VARIANT) for tuning runs.
+//  FP32: 32 x 16 tiles, 4 CTAs of 4 warps per SM.
 using Cfg0 = SweepCfg<32, 16, 1, 4, 4>;
 using CfgA = SweepCfg<64, 16, 1, 4, 2>;
-using Cfg2 = SweepCfg<32, 8, 1, 4, 6>;
-using Cfg3 = SweepCfg<32, 32, 1, 4, 2>;
-using Cfg4 = SweepCfg<64, 8, 1, 4, 3>;
-using Cfg5 = SweepCfg<16, 16, 1, 4, 6>;
-using Cfg6 = SweepCfg<32, 16, 1, 3, 4>;
+using Cfg2 = SweepCfg<64, 8, 1, 4, 4>;
+using Cfg3 = SweepCfg<32, 16, 1, 3, 4>;
+//  16-bit: 64-wide tiles, so a half-warp reads one contiguous 128-byte row of
+//  16-bit elements (no shared-memory bank conflicts).
+using CfgB0 = SweepCfg<64, 8, 1, 4, 4, __nv_bfloat16>;
+using CfgB1 = SweepCfg<32, 16, 1, 4, 4, __nv_bfloat16>;
+using CfgB2 = SweepCfg<64, 16, 2, 4, 3, __nv_bfloat16>;
+using CfgH0 = SweepCfg<64, 8, 1, 4, 4, __half>;
+using CfgH1 = SweepCfg<32, 16, 1, 4, 4, __half>;
+using CfgH2 = SweepCfg<64, 16, 2, 4, 3, __half>;
 
 struct Variant {
   const void *func;
   int tx, ty, threads;
   size_t smem;
+  int esize, halo_x;  // bytes per wavefield element; box columns left of a tile
   void (*launch)(dim3, cudaStream_t, const CUtensorMap &, const CUtensorMap &,
                  const CUtensorMap &, const SweepArgs &);
 };
@@ -55,18 +63,35 @@ void launch_sweep(dim3 grid, cudaStream_t st, const CUtensorMap &tu,
 
 template <class C>
 Variant make_variant() {
-  return Variant{reinterpret_cast<const void *>(&wave_sweep_kernel<C>), C::TX,
-                 C::TY, C::THREADS, C::SMEM_BYTES, &launch_sweep<C>};
+  return Variant{reinterpret_cast<const void *>(&wave_sweep_kernel<C>),
+                 C::TX,
+                 C::TY,
+                 C::THREADS,
+                 C::SMEM_BYTES,
+                 (int)sizeof(typename C::T),
+                 C::HX,
+                 &launch_sweep<C>};
 }
 
-Variant pick_variant(int which) {
+Variant pick_variant(int storage, int which) {
+  if (storage == WAVE_STORAGE_BF16) {
+    switch (which) {
+      case 1: return make_variant<CfgB1>();
+      case 2: return make_variant<CfgB2>();
+      default: return make_variant<CfgB0>();
+    }
+  }
+  if (storage == WAVE_STORAGE_F16) {
+    switch (which) {
+      case 1: return make_variant<CfgH1>();
+      case 2: return make_variant<CfgH2>();
+      default: return make_variant<CfgH0>();
+    }
+  }
   switch (which) {
     case 1: return make_variant<CfgA>();
     case 2: return make_variant<Cfg2>();
     case 3: return make_variant<Cfg3>();
-    case 4: return make_variant<Cfg4>();
-    case 5: return make_variant<Cfg5>();
-    case 6: return make_variant<Cfg6>();
     default: return make_variant<Cfg0>();
   }
 }
@@ -120,6 +145,60 @@ __global__ void velocity_to_c_kernel(float *c, long long n, double dt2) {
   }
 }
 
+template <class T>
+__device__ __forceinline__ T from_f32(float v);
+template <>
+__device__ __forceinline__ __nv_bfloat16 from_f32(float v) {
+  return __float2bfloat16_rn(v);
+}
+template <>
+__device__ __forceinline__ __half from_f32(float v) {
+  return __float2half_rn(v);
+}
+__device__ __forceinline__ float to_f32(__nv_bfloat16 v) {
+  return __bfloat162float(v);
+}
+__device__ __forceinline__ float to_f32(__half v) { return __half2float(v); }
+
+// Dense FP32 (x fastest) -> pitched 16-bit field with scale 2^exps[slot].
+template <class T>
+__global__ void to_stored_kernel(T *dst, int pxu, const float *src, int nx,
+                                 long long rows, const StepDesc *d, int slot) {
+  const float inv = ldexpf(1.0f, -d->exps[slot]);
+  const long long total = rows * (long long)nx;
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+       i < total; i += (long long)gridDim.x * blockDim.x) {
+    const long long r = i / nx;
+    const int x = (int)(i - r * nx);
+    dst[r * pxu + x] = from_f32<T>(src[i] * inv);
+  }
+}
+
+// Pitched 16-bit field with scale 2^exps[slot] -> dense FP32.
+template <class T>
+__global__ void from_stored_kernel(float *dst, const T *src, int pxu, int nx,
+                                   long long rows, const StepDesc *d,
+                                   int slot) {
+  const float sc = ldexpf(1.0f, d->exps[slot]);
+  const long long total = rows * (long long)nx;
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+       i < total; i += (long long)gridDim.x * blockDim.x) {
+    const long long r = i / nx;
+    const int x = (int)(i - r * nx);
+    dst[i] = to_f32(src[r * pxu + x]) * sc;
+  }
+}
+
+// Largest |v| (as float bits) of a dense FP32 array.
+__global__ void absmax_kernel(const float *v, long long n, unsigned *out) {
+  unsigned m = 0;
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
+       i += (long long)gridDim.x * blockDim.x)
+    m = max(m, __float_as_uint(fabsf(v[i])));
+  for (int o = 16; o > 0; o >>= 1) m = max(m, __shfl_xor_sync(0xffffffffu, m, o));
+  if ((threadIdx.x & 31) == 0) atomicMax(out, m);
+}
+
 struct DeviceBuf {
   void *p = nullptr;
   size_t cap = 0;
@@ -128,12 +207,17 @@ struct DeviceBuf {
 }  // namespace
 
 struct wave_ctx {
-  int nx = 0, ny = 0, nz = 0, px = 0;
+  int nx = 0, ny = 0, nz = 0;
+  int px = 0;       // row pitch of the v^2 dt^2 field (floats, multiple of 4)
+  int pxu = 0;      // row pitch of the wavefields (elements, 16-byte rows)
+  int storage = WAVE_STORAGE_F32;
+  int sms = 0;
+  double vmax = 0;
   double dx = 0, dy = 0, dz = 0, dt = 0;
   cudaStream_t stream = nullptr;
   cudaStream_t capture_stream = nullptr;
   int device = 0;
-  float *buf[2] = {nullptr, nullptr};  // buf[cur] = u, buf[cur ^ 1] = u_prev
+  void *buf[2] = {nullptr, nullptr};  // buf[cur] = u, buf[cur ^ 1] = u_prev
   float *c = nullptr;
   int cur = 0;
   int64_t step = 0;
@@ -151,6 +235,7 @@ struct wave_ctx {
   std::vector<int4> h_rec;
   std::vector<int> h_rec_start;
   std::vector<float> h_wavelet;
+  unsigned char scale_image[32];  // host staging of the 16-bit scale state
 };
 
 namespace {
@@ -204,35 +289,44 @@ PFN_cuTensorMapEncodeTiled_v12000 get_encode() {
   return fn;
 }
 
-// 3D FP32 tensor map over a (nz, ny, px)-pitched field with logical x extent
+// 3D tensor map over a (nz, ny, pitch)-pitched field with logical x extent
 // nx; elements outside [0,nx) x [0,ny) x [0,nz) read as zero.
-int make_map(CUtensorMap *m, const float *base, const wave_ctx *c, int box_x,
-             int box_y) {
+int make_map(CUtensorMap *m, const void *base, const wave_ctx *c, int box_x,
+             int box_y, CUtensorMapDataType dtype, int pitch, int esize) {
   auto enc = get_encode();
   if (!enc) return WAVE_ECUDA;
   cuuint64_t dims[3] = {(cuuint64_t)c->nx, (cuuint64_t)c->ny,
                         (cuuint64_t)c->nz};
-  cuuint64_t strides[2] = {(cuuint64_t)c->px * 4,
-                           (cuuint64_t)c->px * 4 * (cuuint64_t)c->ny};
+  cuuint64_t strides[2] = {(cuuint64_t)pitch * esize,
+                           (cuuint64_t)pitch * esize * (cuuint64_t)c->ny};
   cuuint32_t box[3] = {(cuuint32_t)box_x, (cuuint32_t)box_y, 1};
   cuuint32_t estr[3] = {1, 1, 1};
-  CUresult r = enc(m, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 3,
-                   const_cast<float *>(base), dims, strides, box, estr,
-                   CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
-                   CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+  CUresult r = enc(m, dtype, 3, const_cast<void *>(base), dims, strides, box,
+                   estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
+                   CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
                    CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
   return r == CUDA_SUCCESS ? WAVE_OK : WAVE_ECUDA;
 }
 
+CUtensorMapDataType field_dtype(int storage) {
+  if (storage == WAVE_STORAGE_BF16) return CU_TENSOR_MAP_DATA_TYPE_BFLOAT16;
+  if (storage == WAVE_STORAGE_F16) return CU_TENSOR_MAP_DATA_TYPE_FLOAT16;
+  return CU_TENSOR_MAP_DATA_TYPE_FLOAT32;
+}
+
 int build_maps(wave_ctx *c) {
-  const int tx = c->var.tx, ty = c->var.ty;
+  const int tx = c->var.tx, ty = c->var.ty, hx = c->var.halo_x;
+  const CUtensorMapDataType dt = field_dtype(c->storage);
   for (int b = 0; b < 2; ++b) {
-    int st = make_map(&c->tm_halo[b], c->buf[b], c, tx + 2 * kR, ty + 2 * kR);
+    int st = make_map(&c->tm_halo[b], c->buf[b], c, tx + 2 * hx, ty + 2 * kR,
+                      dt, c->pxu, c->var.esize);
     if (st) return st;
-    st = make_map(&c->tm_tile[b], c->buf[b], c, tx, ty);
+    st = make_map(&c->tm_tile[b], c->buf[b], c, tx, ty, dt, c->pxu,
+                  c->var.esize);
     if (st) return st;
   }
-  return make_map(&c->tm_c, c->c, c, tx, ty);
+  return make_map(&c->tm_c, c->c, c, tx, ty, CU_TENSOR_MAP_DATA_TYPE_FLOAT32,
+                  c->px, 4);
 }
 
 // Makespan of one launch in plane units: CTAs start in launch order (layer
@@ -314,8 +408,9 @@ void set_coeffs(wave_ctx *c) {
   a.nx = c->nx;
   a.ny = c->ny;
   a.nz = c->nz;
-  a.px = c->px;
+  a.px = c->pxu;
   a.ntx = (int)c->grid.x;
+  a.cmax = (float)(c->vmax * c->vmax * c->dt * c->dt);
   const double ix = 1.0 / (c->dx * c->dx), iy = 1.0 / (c->dy * c->dy),
                iz = 1.0 / (c->dz * c->dz);
   a.c0 = (float)(kW[0] * (ix + iy + iz));
@@ -382,7 +477,9 @@ int read_device_error(const wave_ctx *c) {
 }
 
 int upload_desc(wave_ctx *c) {
-  // Everything but the error word (which persists until read).
+  c->host_desc.step0 = c->step;
+  // Everything before the error word (which persists until read, followed
+  // by the scale state of 16-bit storage).
   WAVE_TRY_CUDA(cudaMemcpyAsync(c->d_desc, &c->host_desc,
                                 offsetof(StepDesc, error),
                                 cudaMemcpyHostToDevice, c->stream));
@@ -446,21 +543,28 @@ void wave_destroy(wave_ctx *c) {
   delete c;
 }
 
+size_t field_bytes(const wave_ctx *c) {
+  return (size_t)c->pxu * c->ny * c->nz * (size_t)c->var.esize;
+}
+
 static int create_impl(wave_ctx *c, const float *velocity) {
   const size_t plane = (size_t)c->px * c->ny;
   const size_t nfield = plane * c->nz;
   const size_t bytes = nfield * sizeof(float);
   cudaStream_t st = c->stream;
+  const char *ev = std::getenv("GBWAVE_VARIANT");
+  c->var = pick_variant(c->storage, ev ? std::atoi(ev) : 0);
   WAVE_TRY_CUDA(cudaGetDevice(&c->device));
   WAVE_TRY_CUDA(cudaStreamCreateWithFlags(&c->capture_stream,
                                           cudaStreamNonBlocking));
-  WAVE_TRY_CUDA(cudaMalloc((void **)&c->buf[0], bytes));
-  WAVE_TRY_CUDA(cudaMalloc((void **)&c->buf[1], bytes));
+  const size_t fbytes = field_bytes(c);
+  WAVE_TRY_CUDA(cudaMalloc(&c->buf[0], fbytes));
+  WAVE_TRY_CUDA(cudaMalloc(&c->buf[1], fbytes));
   WAVE_TRY_CUDA(cudaMalloc((void **)&c->c, bytes));
   WAVE_TRY_CUDA(cudaMalloc((void **)&c->d_desc, sizeof(StepDesc)));
   WAVE_TRY_CUDA(cudaMalloc(&c->d_scratch, 16));
-  WAVE_TRY_CUDA(cudaMemsetAsync(c->buf[0], 0, bytes, st));
-  WAVE_TRY_CUDA(cudaMemsetAsync(c->buf[1], 0, bytes, st));
+  WAVE_TRY_CUDA(cudaMemsetAsync(c->buf[0], 0, fbytes, st));
+  WAVE_TRY_CUDA(cudaMemsetAsync(c->buf[1], 0, fbytes, st));
   WAVE_TRY_CUDA(cudaMemsetAsync(c->c, 0, bytes, st));
   WAVE_TRY_CUDA(cudaMemsetAsync(c->d_desc, 0, sizeof(StepDesc), st));
   WAVE_TRY_CUDA(cudaMemsetAsync(c->d_scratch, 0, 16, st));
@@ -475,6 +579,7 @@ static int create_impl(wave_ctx *c, const float *velocity) {
   int sms = 0;
   WAVE_TRY_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount,
                                        c->device));
+  c->sms = sms;
   scan_velocity_kernel<<<sms * 4, 256, 0, st>>>(
       c->c, c->nx, c->px, (long long)c->ny * c->nz, vmax_bits, nbad);
   WAVE_TRY_CUDA(cudaGetLastError());
@@ -491,13 +596,12 @@ static int create_impl(wave_ctx *c, const float *velocity) {
   wave_spacing h{c->dx, c->dy, c->dz};
   const double lim = wave_cfl_dt(&h, (double)vmax);
   if (!(c->dt <= lim * (1.0 + 1e-12))) return WAVE_EUNSTABLE;
+  c->vmax = vmax;
   velocity_to_c_kernel<<<sms * 4, 256, 0, st>>>(c->c, (long long)nfield,
                                                 c->dt * c->dt);
   WAVE_TRY_CUDA(cudaGetLastError());
 
   // Launch geometry.
-  const char *ev = std::getenv("GBWAVE_VARIANT");
-  c->var = pick_variant(ev ? std::atoi(ev) : 0);
   WAVE_TRY_CUDA(cudaFuncSetAttribute(c->var.func,
                                      cudaFuncAttributeMaxDynamicSharedMemorySize,
                                      (int)c->var.smem));
@@ -533,9 +637,13 @@ int wave_create(const wave_grid *g, const wave_spacing *h, double dt,
   if (!finite_pos(h->dx) || !finite_pos(h->dy) || !finite_pos(h->dz) ||
       !finite_pos(dt))
     return WAVE_EINVAL;
-  if (storage != WAVE_STORAGE_F32) return WAVE_ENOTSUP;
-  // Row pitch in floats: a multiple of 4 so rows are 16-byte aligned (TMA).
+  if (storage != WAVE_STORAGE_F32 && storage != WAVE_STORAGE_BF16 &&
+      storage != WAVE_STORAGE_F16)
+    return WAVE_ENOTSUP;
+  // Row pitches: 16-byte rows (TMA): 4 floats, or 8 16-bit elements.
   const long long px = ((long long)g->nx + 3) / 4 * 4;
+  const long long pxu =
+      storage == WAVE_STORAGE_F32 ? px : ((long long)g->nx + 7) / 8 * 8;
   if (px * (long long)g->ny * (long long)g->nz > (1ll << 36)) return WAVE_EINVAL;
   wave_ctx *c = new (std::nothrow) wave_ctx();
   if (!c) return WAVE_ENOMEM;
@@ -543,6 +651,8 @@ int wave_create(const wave_grid *g, const wave_spacing *h, double dt,
   c->ny = g->ny;
   c->nz = g->nz;
   c->px = (int)px;
+  c->pxu = (int)pxu;
+  c->storage = storage;
   c->dx = h->dx;
   c->dy = h->dy;
   c->dz = h->dz;
@@ -666,20 +776,144 @@ int wave_propagate(wave_ctx *c, const wave_shot *shot, int nsteps,
   return WAVE_OK;
 }
 
+}  // extern "C"
+
+// Index of the scale slot of the field holding u (which = 0) or u_prev (1).
+static int field_slot(const wave_ctx *c, int which) {
+  return (int)((c->step + (which ? 3 : 0)) & 3);
+}
+
+template <class T>
+static void launch_from_stored(const wave_ctx *c, float *dst, const void *src,
+                               int slot) {
+  from_stored_kernel<T><<<c->sms * 4, 256, 0, c->stream>>>(
+      dst, reinterpret_cast<const T *>(src), c->pxu, c->nx,
+      (long long)c->ny * c->nz, c->d_desc, slot);
+}
+
+template <class T>
+static void launch_to_stored(const wave_ctx *c, void *dst, const float *src,
+                             int slot) {
+  to_stored_kernel<T><<<c->sms * 4, 256, 0, c->stream>>>(
+      reinterpret_cast<T *>(dst), c->pxu, src, c->nx,
+      (long long)c->ny * c->nz, c->d_desc, slot);
+}
+
+extern "C" {
+
 int wave_get_field(const wave_ctx *c, int which, float *out) {
   if (!c || !out || (which != 0 && which != 1)) return WAVE_EINVAL;
-  const float *src = c->buf[which == 0 ? c->cur : (c->cur ^ 1)];
-  WAVE_TRY_CUDA(cudaMemcpy2DAsync(out, (size_t)c->nx * 4, src,
-                                  (size_t)c->px * 4, (size_t)c->nx * 4,
-                                  (size_t)c->ny * c->nz, cudaMemcpyDefault,
-                                  c->stream));
-  if (!is_device_ptr(out)) return read_device_error(c);
-  return WAVE_OK;
+  const void *src = c->buf[which == 0 ? c->cur : (c->cur ^ 1)];
+  const bool host_out = !is_device_ptr(out);
+  if (c->storage == WAVE_STORAGE_F32) {
+    WAVE_TRY_CUDA(cudaMemcpy2DAsync(out, (size_t)c->nx * 4, src,
+                                    (size_t)c->px * 4, (size_t)c->nx * 4,
+                                    (size_t)c->ny * c->nz, cudaMemcpyDefault,
+                                    c->stream));
+    if (host_out) return read_device_error(c);
+    return WAVE_OK;
+  }
+  // 16-bit storage: expand to FP32 with the field's scale.
+  const size_t n = (size_t)c->nx * c->ny * c->nz;
+  float *dst = out;
+  if (host_out) WAVE_TRY_CUDA(cudaMalloc((void **)&dst, n * 4));
+  if (c->storage == WAVE_STORAGE_BF16)
+    launch_from_stored<__nv_bfloat16>(c, dst, src, field_slot(c, which));
+  else
+    launch_from_stored<__half>(c, dst, src, field_slot(c, which));
+  cudaError_t e = cudaGetLastError();
+  if (host_out) {
+    if (e == cudaSuccess)
+      e = cudaMemcpyAsync(out, dst, n * 4, cudaMemcpyDeviceToHost, c->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+    cudaFree(dst);
+  }
+  if (e != cudaSuccess) return cuda_status(e);
+  return host_out ? read_device_error(c) : WAVE_OK;
 }
+
+}  // extern "C"
+
+// Scale exponent for a field whose largest magnitude is m: stored values
+// are at most 2^14 in magnitude.
+static int scale_exponent(float m) {
+  if (!(m > 0.f) || !std::isfinite(m)) return 0;
+  int e;
+  std::frexp(m, &e);
+  return e - 14;
+}
+
+static int set_state_16(wave_ctx *c, const float *u, const float *u_prev,
+                        int64_t step) {
+  const size_t n = (size_t)c->nx * c->ny * c->nz;
+  cudaStream_t st = c->stream;
+  const float *src[2] = {u, u_prev};
+  float *tmp[2] = {nullptr, nullptr};
+  int status = WAVE_OK;
+  for (int b = 0; b < 2 && status == WAVE_OK; ++b) {
+    if (!is_device_ptr(src[b])) {
+      cudaError_t e = cudaMalloc((void **)&tmp[b], n * 4);
+      if (e == cudaSuccess)
+        e = cudaMemcpyAsync(tmp[b], src[b], n * 4, cudaMemcpyHostToDevice, st);
+      if (e != cudaSuccess) status = cuda_status(e);
+      src[b] = tmp[b];
+    }
+  }
+  unsigned mb[2] = {0, 0};
+  if (status == WAVE_OK) {
+    unsigned *dm = reinterpret_cast<unsigned *>(c->d_scratch);
+    cudaError_t e = cudaMemsetAsync(dm, 0, 8, st);
+    for (int b = 0; b < 2 && e == cudaSuccess; ++b) {
+      absmax_kernel<<<c->sms * 4, 256, 0, st>>>(src[b], (long long)n, dm + b);
+      e = cudaGetLastError();
+    }
+    if (e == cudaSuccess)
+      e = cudaMemcpyAsync(mb, dm, 8, cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    if (e != cudaSuccess) status = cuda_status(e);
+  }
+  if (status == WAVE_OK) {
+    float m[2];
+    std::memcpy(m, mb, 8);
+    if (!std::isfinite(m[0]) || !std::isfinite(m[1])) status = WAVE_EINVAL;
+    // Scale state: u at absolute step `step`, u_prev at step - 1.
+    int exps[4] = {0, 0, 0, 0};
+    unsigned maxb[4] = {0, 0, 0, 0};
+    exps[step & 3] = scale_exponent(m[0]);
+    exps[(step + 3) & 3] = scale_exponent(m[1]);
+    maxb[step & 3] = mb[0];
+    maxb[(step + 3) & 3] = mb[1];
+    std::memcpy(c->scale_image, exps, 16);
+    std::memcpy(c->scale_image + 16, maxb, 16);
+    cudaError_t e = cudaSuccess;
+    if (status == WAVE_OK)
+      e = cudaMemcpyAsync(reinterpret_cast<char *>(c->d_desc) +
+                              offsetof(StepDesc, exps),
+                          c->scale_image, 32, cudaMemcpyHostToDevice, st);
+    c->cur = 0;
+    c->step = step;
+    for (int b = 0; b < 2 && e == cudaSuccess && status == WAVE_OK; ++b) {
+      const int slot = b == 0 ? (int)(step & 3) : (int)((step + 3) & 3);
+      if (c->storage == WAVE_STORAGE_BF16)
+        launch_to_stored<__nv_bfloat16>(c, c->buf[b], src[b], slot);
+      else
+        launch_to_stored<__half>(c, c->buf[b], src[b], slot);
+      e = cudaGetLastError();
+    }
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    if (e != cudaSuccess && status == WAVE_OK) status = cuda_status(e);
+  }
+  cudaFree(tmp[0]);
+  cudaFree(tmp[1]);
+  return status;
+}
+
+extern "C" {
 
 int wave_set_state(wave_ctx *c, const float *u, const float *u_prev,
                    int64_t step) {
   if (!c || !u || !u_prev || step < 0) return WAVE_EINVAL;
+  if (c->storage != WAVE_STORAGE_F32) return set_state_16(c, u, u_prev, step);
   c->cur = 0;
   const float *src[2] = {u, u_prev};
   for (int b = 0; b < 2; ++b)
@@ -701,9 +935,12 @@ int wave_get_step(const wave_ctx *c, int64_t *step) {
 
 int wave_reset(wave_ctx *c) {
   if (!c) return WAVE_EINVAL;
-  const size_t bytes = (size_t)c->px * c->ny * c->nz * 4;
+  const size_t bytes = field_bytes(c);
   WAVE_TRY_CUDA(cudaMemsetAsync(c->buf[0], 0, bytes, c->stream));
   WAVE_TRY_CUDA(cudaMemsetAsync(c->buf[1], 0, bytes, c->stream));
+  WAVE_TRY_CUDA(cudaMemsetAsync(
+      reinterpret_cast<char *>(c->d_desc) + offsetof(StepDesc, exps), 0,
+      sizeof(int) * 4 + sizeof(unsigned) * 4, c->stream));
   c->cur = 0;
   c->step = 0;
   return WAVE_OK;

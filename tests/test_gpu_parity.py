@@ -213,7 +213,7 @@ def test_invalid_inputs_are_rejected(wave_lib):
     with pytest.raises(E):
         wave_lib.WaveSolver((nx, ny, nz), sp, 0.5 * lim, bad)
     with pytest.raises(E) as ei:
-        wave_lib.WaveSolver((nx, ny, nz), sp, 0.5 * lim, vel, storage=1)
+        wave_lib.WaveSolver((nx, ny, nz), sp, 0.5 * lim, vel, storage=7)
     assert ei.value.code == -8
     with pytest.raises(E):
         wave_lib.WaveSolver((0, ny, nz), sp, 0.5 * lim, vel)

@@ -1,0 +1,136 @@
+"""16-bit wavefield storage (BF16 / FP16 with power-of-two field scales,
+FP32 arithmetic, FP32 v^2 dt^2) against the FP64 oracle, through the C ABI.
+
+Tolerances follow from the storage format: every step rounds u_next to the
+format (relative 2^-9 for BF16, 2^-12 for FP16), and the leapfrog carries the
+rounding errors forward undamped. Short runs from the same (rounded) state
+bound what indexing or scaling mistakes would break (those give O(1)
+errors); the 128^3 x 500-step workload measures the accumulated error the
+format costs, reported per mode.
+"""
+import numpy as np
+import pytest
+
+import workloads as wl
+
+pytestmark = pytest.mark.gpu
+
+STORAGE = {"bf16": 1, "f16": 2}
+# largest relative rounding error of one conversion (half an ulp at the
+# bottom of a binade): 7 fraction bits for BF16, 10 for FP16
+EPS = {"bf16": 2.0 ** -8, "f16": 2.0 ** -11}
+
+
+def rel_l2(a, b):
+    a = np.asarray(a, dtype=np.float64)
+    b = np.asarray(b, dtype=np.float64)
+    return float(np.linalg.norm(a - b) / np.linalg.norm(b))
+
+
+def _run(pkg, vel, sp, dt, storage, nsteps, u0=None, up0=None, step0=0, shot=None, rec=None):
+    import torch
+    nz, ny, nx = vel.shape
+    s = pkg.WaveSolver((nx, ny, nz), sp, dt, torch.from_numpy(vel).cuda(), storage=storage)
+    try:
+        if u0 is not None:
+            s.set_state(u0, up0, step0)
+        start_u = np.empty((nz, ny, nx), np.float32)
+        start_up = np.empty((nz, ny, nx), np.float32)
+        s.get_field(0, start_u)
+        s.get_field(1, start_up)
+        nrec = 0 if rec is None else rec.shape[0]
+        tr = torch.zeros((nsteps, nrec), device="cuda") if nrec else None
+        s.propagate(shot, nsteps, torch.from_numpy(rec).cuda() if nrec else None, tr)
+        u = np.empty((nz, ny, nx), np.float32)
+        up = np.empty((nz, ny, nx), np.float32)
+        s.get_field(0, u)
+        s.get_field(1, up)
+        s.synchronize()
+        return start_u, start_up, u, up, (tr.cpu().numpy() if nrec else None)
+    finally:
+        s.close()
+
+
+@pytest.mark.parametrize("mode", ["bf16", "f16"])
+def test_state_round_trip(wave_lib, mode):
+    nx, ny, nz = 37, 21, 13
+    vel = wl.layered3(nx, ny, nz)
+    sp = (10.0, 10.0, 10.0)
+    dt = 0.5 * wave_lib.wave_cfl_dt(sp, 3500.0)
+    u0, up0 = wl.random_state((nz, ny, nx), seed=4, scale=3e-3)
+    up0 *= 1e3
+    su, sup, _, _, _ = _run(wave_lib, vel, sp, dt, STORAGE[mode], 0, u0, up0, 7)
+    for got, want in ((su, u0), (sup, up0)):
+        err = np.abs(got.astype(np.float64) - want) / np.maximum(np.abs(want), 1e-30)
+        assert np.max(err) <= EPS[mode] * 1.0001
+
+
+@pytest.mark.parametrize("mode", ["bf16", "f16"])
+@pytest.mark.parametrize("shape,nsteps", [((70, 37, 23), 7), ((33, 65, 17), 33), ((8, 9, 10), 4)])
+def test_short_runs_match_oracle(wave_lib, oracle_mod, mode, shape, nsteps):
+    nx, ny, nz = shape
+    rng = np.random.default_rng(nx + 3 * ny + 7 * nz)
+    vel = rng.uniform(1500.0, 4500.0, size=(nz, ny, nx)).astype(np.float32)
+    sp = (10.0, 12.0, 9.0)
+    dt = 0.45 * wave_lib.wave_cfl_dt(sp, float(vel.max()))
+    u0, up0 = wl.random_state((nz, ny, nx), seed=5)
+    rec = wl.random_receivers(nx, ny, nz, 23, seed=6)
+    shot = (nx // 3, ny // 2, nz // 2, 15.0, 0.01, 1e2)
+    su, sup, u, up, tr = _run(wave_lib, vel, sp, dt, STORAGE[mode], nsteps, u0, up0, 3, shot, rec)
+    # the oracle starts from the state as stored (already rounded)
+    ou, oup, otr = oracle_mod.propagate(vel, sp, dt, nsteps, u=su, u_prev=sup, step0=3,
+                                        source=shot, receivers=rec)
+    tol = 6 * EPS[mode] * np.sqrt(nsteps)
+    assert rel_l2(u, ou) <= tol
+    assert rel_l2(up, oup) <= tol
+    assert rel_l2(tr, otr) <= tol
+
+
+def test_fp16_scale_prevents_overflow(wave_lib):
+    # A source 1e8 times larger than FP16's largest value: the field scale
+    # must follow it without producing infinities.
+    nx = ny = nz = 32
+    vel = wl.layered3(nx, ny, nz)
+    sp = (10.0, 10.0, 10.0)
+    dt = 0.5 * wave_lib.wave_cfl_dt(sp, 3500.0)
+    shot = (16, 16, 16, 15.0, -1.0, 1e12)
+    rec = np.array([[16, 16, 16], [20, 16, 16]], dtype=np.int32)
+    _, _, u, up, tr = _run(wave_lib, vel, sp, dt, 2, 120, shot=shot, rec=rec)
+    assert np.all(np.isfinite(u)) and np.all(np.isfinite(tr))
+    assert np.max(np.abs(u)) > 1e6
+    _, _, u32, _, tr32 = _run(wave_lib, vel, sp, dt, 0, 120, shot=shot, rec=rec)
+    assert rel_l2(u, u32) < 2e-2
+    assert rel_l2(tr, tr32) < 2e-2
+
+
+@pytest.mark.parametrize("mode", ["f32", "bf16", "f16"])
+def test_precision_workload_128cube_500_steps(wave_lib, oracle_mod, mode, record_property):
+    """Random 8-layer model at 128^3, Ricker near the top, receiver plane at
+    z = 8, 500 steps: relative L2 against the FP64 oracle per storage mode."""
+    n = 128
+    cfg = dict(wl.CFG_512, shape=(n, n, n), source=(64, 64, 10))
+    vel = wl.random_layered(n, n, n, seed=0)
+    sp = cfg["spacing"]
+    dt = 0.5 * wave_lib.wave_cfl_dt(sp, float(vel.max()))
+    rec = wl.receiver_plane(n, n, 8, 4)
+    shot = (64, 64, 10, 15.0, -1.0, 1.0)
+    nsteps = 500
+    storage = {"f32": 0, "bf16": 1, "f16": 2}[mode]
+    _, _, u, _, tr = _run(wave_lib, vel, sp, dt, storage, nsteps, shot=shot, rec=rec)
+    ou, _, otr = _precision_oracle(oracle_mod, vel, sp, dt, nsteps, shot, rec)
+    e_u, e_t = rel_l2(u, ou), rel_l2(tr, otr)
+    record_property("rel_l2_field", e_u)
+    record_property("rel_l2_traces", e_t)
+    print("\nstorage %s: 128^3 x 500 steps rel-L2 field %.3e traces %.3e" % (mode, e_u, e_t))
+    bound = {"f32": 1e-4, "bf16": 1.0, "f16": 2e-2}[mode]
+    assert e_u <= bound and e_t <= bound
+
+
+_ORACLE_CACHE = {}
+
+
+def _precision_oracle(oracle_mod, vel, sp, dt, nsteps, shot, rec):
+    key = (vel.shape, dt, nsteps)
+    if key not in _ORACLE_CACHE:
+        _ORACLE_CACHE[key] = oracle_mod.propagate(vel, sp, dt, nsteps, source=shot, receivers=rec)
+    return _ORACLE_CACHE[key]
