@@ -207,6 +207,54 @@ def precision_errors(gw, torch):
     return out
 
 
+def serve_stream(gw, torch, storage, n_requests, max_slots=32):
+    """The shot-serving stream: Poisson arrivals (mean 20/s) of shots with
+    grids drawn from {128..512 step 32}^3, 300-800 steps, a random layered
+    model each, source at z = 10, receivers every 4th point on z = 8,
+    150 GB admission budget. Returns latency percentiles and throughput."""
+    spec = dict(wl.SERVE_STREAM, n=n_requests)
+    reqs = wl.serving_requests(**spec)
+    srv = gw.ShotServer(spec["budget_bytes"], max_slots)
+    pending = []
+    t0 = time.perf_counter()
+    for r in reqs:
+        delay = t0 + r["arrival_s"] - time.perf_counter()
+        if delay > 0:
+            time.sleep(delay)
+        nx, ny, nz = r["grid"]
+        vz = torch.from_numpy(wl.layered_profile(nz, r["vel_seed"])).cuda()
+        vel = vz[:, None, None].expand(nz, ny, nx).contiguous()
+        rec = torch.from_numpy(wl.receiver_plane(nx, ny, min(spec["rec_z"], nz - 1),
+                                                 spec["rec_stride"])).cuda()
+        tr = torch.empty((r["nsteps"], rec.shape[0]), device="cuda")
+        t = srv.submit(r["grid"], (10.0, 10.0, 10.0), vel, (*r["source"], 15.0, -1.0, 1.0),
+                       r["nsteps"], rec, tr, storage=storage)
+        pending.append((t, nx * ny * nz * r["nsteps"]))
+    lat, work, first, last, failed = [], 0.0, None, 0.0, 0
+    for t, pts in pending:
+        st, res = srv.wait(t)
+        if st != 0:
+            failed += 1
+            continue
+        lat.append(res["done_s"] - res["submit_s"])
+        work += pts
+        first = res["submit_s"] if first is None else min(first, res["submit_s"])
+        last = max(last, res["done_s"])
+    stats = srv.stats()
+    srv.close()
+    lat = np.array(lat)
+    return {"requests": len(reqs), "failed": failed,
+            "p50_latency_s": float(np.percentile(lat, 50)) if lat.size else None,
+            "p99_latency_s": float(np.percentile(lat, 99)) if lat.size else None,
+            "mean_latency_s": float(lat.mean()) if lat.size else None,
+            "gpts": work / max(last - first, 1e-9) / 1e9 if lat.size else None,
+            "gpts_busy": stats["point_steps"] / max(stats["busy_s"], 1e-9) / 1e9,
+            "makespan_s": last - first if lat.size else None,
+            "resident_peak": stats["resident_peak"], "max_slots": max_slots,
+            "bytes_peak": stats["bytes_peak"], "budget_bytes": spec["budget_bytes"],
+            "arrival_rate_per_s": spec["rate_per_s"]}
+
+
 def run_reference(args, cfg):
     """The reference arm: the FP64 CPU oracle on this machine's host cores."""
     rank, world, _ = dist_env()
@@ -269,6 +317,9 @@ def main():
     ap.add_argument("--variant", type=int, default=None, help="sweep kernel variant (tuning)")
     ap.add_argument("--no-precision", action="store_true",
                     help="skip the BF16/FP16 storage measurements")
+    ap.add_argument("--no-serve", action="store_true",
+                    help="skip the shot-serving stream")
+    ap.add_argument("--serve-requests", type=int, default=wl.SERVE_STREAM["n"])
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
     cfg = WORKLOADS[args.workload]
@@ -417,6 +468,12 @@ def main():
                 precision[name]["error_vs_fp64_oracle"] = err[name]
             precision["f32_error_vs_fp64_oracle"] = err["f32"]
 
+    # ---- shot serving: continuous batching of a Poisson request stream -------
+    serving = None
+    if not args.no_serve:
+        serving = {name: serve_stream(gw, torch, STORAGE[name], args.serve_requests)
+                   for name in ("f32", "f16")}
+
     cpu = None
     if rank == 0 and not args.no_cpu_baseline:
         g, cores, sample, el = oracle_sample(vel, cfg, dt, budget_s=15.0)
@@ -439,7 +496,7 @@ def main():
                        "launch": info},
             "e2e": e2e, "gpu_launches": launches, "roofline": roofline,
             "cpu_baseline": cpu, "clocks": clocks, "traces_finite": tr_ok,
-            "precision_forms": precision,
+            "precision_forms": precision, "serving": serving,
         }
         print(json.dumps(line), flush=True)
     if world > 1:

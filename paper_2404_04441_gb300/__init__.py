@@ -17,6 +17,7 @@ __all__ = [
     "wave_get_field", "wave_set_state", "wave_get_step", "wave_reset",
     "wave_synchronize", "wave_destroy", "wave_strerror", "wave_get_launch_info",
     "wave_selftest_wait", "wave_propagate_noalloc", "WaveSolver", "library_path",
+    "ShotServer",
 ]
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
@@ -47,6 +48,29 @@ class _Spacing(ctypes.Structure):
 class _Shot(ctypes.Structure):
     _fields_ = [("sx", ctypes.c_int32), ("sy", ctypes.c_int32), ("sz", ctypes.c_int32),
                 ("f_peak", ctypes.c_double), ("t0", ctypes.c_double), ("amp", ctypes.c_double)]
+
+
+class _Request(ctypes.Structure):
+    _fields_ = [("grid", _Grid), ("spacing", _Spacing), ("dt", ctypes.c_double),
+                ("velocity", ctypes.c_void_p), ("storage", ctypes.c_int), ("shot", _Shot),
+                ("nsteps", ctypes.c_int), ("rec_xyz", ctypes.c_void_p), ("nrec", ctypes.c_int),
+                ("traces", ctypes.c_void_p)]
+
+
+class _Result(ctypes.Structure):
+    _fields_ = [("status", ctypes.c_int), ("ticket", ctypes.c_int64),
+                ("submit_s", ctypes.c_double), ("start_s", ctypes.c_double),
+                ("done_s", ctypes.c_double), ("dt", ctypes.c_double),
+                ("steps_done", ctypes.c_int64)]
+
+
+class _Stats(ctypes.Structure):
+    _fields_ = [("submitted", ctypes.c_int64), ("completed", ctypes.c_int64),
+                ("failed", ctypes.c_int64), ("queued", ctypes.c_int64),
+                ("resident", ctypes.c_int64), ("bytes_resident", ctypes.c_size_t),
+                ("bytes_peak", ctypes.c_size_t), ("resident_peak", ctypes.c_int),
+                ("batch_steps", ctypes.c_int64), ("point_steps", ctypes.c_double),
+                ("busy_s", ctypes.c_double)]
 
 
 def library_path():
@@ -82,6 +106,15 @@ def load(path=None):
     lib.wave_strerror.restype = ctypes.c_char_p
     lib.wave_get_launch_info.argtypes = [vp] + [ctypes.POINTER(ctypes.c_int)] * 5
     lib.wave_selftest_wait.argtypes = [ctypes.c_int64, vp]
+    lib.serve_create.argtypes = [ctypes.c_size_t, ip, vp, ctypes.POINTER(vp)]
+    lib.serve_submit.argtypes = [vp, ctypes.POINTER(_Request), ctypes.POINTER(ctypes.c_int64)]
+    lib.serve_poll.argtypes = [vp, ctypes.c_int64, ctypes.POINTER(_Result)]
+    lib.serve_wait.argtypes = [vp, ctypes.c_int64, ctypes.c_double, ctypes.POINTER(_Result)]
+    lib.serve_get_stats.argtypes = [vp, ctypes.POINTER(_Stats)]
+    lib.serve_destroy.argtypes = [vp]
+    lib.serve_destroy.restype = None
+    for name in ("serve_create", "serve_submit", "serve_poll", "serve_wait", "serve_get_stats"):
+        getattr(lib, name).restype = ctypes.c_int
     lib.wave_propagate_noalloc.argtypes = [
         ctypes.POINTER(_Grid), ctypes.POINTER(_Spacing), ctypes.c_double, vp, vp, vp,
         ctypes.POINTER(_Shot), ctypes.c_int64, ip, vp, ip, vp, vp, ctypes.POINTER(ip)]
@@ -295,6 +328,85 @@ class WaveSolver:
         if getattr(self, "ctx", None):
             wave_destroy(self.ctx)
             self.ctx = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def _result_dict(r):
+    return {"status": r.status, "ticket": r.ticket, "submit_s": r.submit_s,
+            "start_s": r.start_s, "done_s": r.done_s, "dt": r.dt,
+            "steps_done": r.steps_done}
+
+
+class ShotServer:
+    """Continuous-batching shot server (include/wave_serve.h).
+
+    ``submit`` keeps references to the request's arrays until the request is
+    reported complete by ``poll``/``wait``, since the engine reads velocity and
+    receivers when it admits the request and writes the traces while it runs.
+    CUDA tensors are made visible to the server's stream by synchronizing
+    torch's current stream before each submit.
+    """
+
+    def __init__(self, hbm_budget_bytes, max_slots=64, stream=None):
+        lib = load()
+        out = ctypes.c_void_p()
+        _check(lib.serve_create(int(hbm_budget_bytes), int(max_slots),
+                                None if stream is None else int(stream), ctypes.byref(out)),
+               "serve_create")
+        self.handle = out
+        self._keep = {}
+
+    def submit(self, grid, spacing, velocity, shot, nsteps, rec=None, traces=None,
+               storage=0, dt=0.0):
+        nx, ny, nz = map(int, grid)
+        nrec = 0 if rec is None else int(rec.shape[0])
+        if any(type(a).__module__.startswith("torch") and a.is_cuda
+               for a in (velocity, rec, traces) if a is not None):
+            import torch
+            torch.cuda.current_stream().synchronize()
+        sx, sy, sz, f, t0, amp = shot
+        req = _Request(
+            _Grid(nx, ny, nz), _Spacing(*map(float, spacing)), float(dt),
+            _ptr(velocity, "float32", nx * ny * nz, "velocity"), int(storage),
+            _Shot(int(sx), int(sy), int(sz), float(f), -1.0 if t0 is None else float(t0),
+                  float(amp)),
+            int(nsteps), _ptr(rec, "int32", 3 * nrec, "rec") if nrec else None, nrec,
+            _ptr(traces, "float32", int(nsteps) * nrec, "traces") if nrec else None)
+        ticket = ctypes.c_int64()
+        _check(load().serve_submit(self.handle, ctypes.byref(req), ctypes.byref(ticket)),
+               "serve_submit")
+        self._keep[ticket.value] = (velocity, rec, traces)
+        return ticket.value
+
+    def poll(self, ticket):
+        r = _Result()
+        st = load().serve_poll(self.handle, int(ticket), ctypes.byref(r))
+        if st != -6:
+            self._keep.pop(int(ticket), None)
+        return st, _result_dict(r)
+
+    def wait(self, ticket, timeout_s=-1.0):
+        r = _Result()
+        st = load().serve_wait(self.handle, int(ticket), float(timeout_s), ctypes.byref(r))
+        if st != -6:
+            self._keep.pop(int(ticket), None)
+        return st, _result_dict(r)
+
+    def stats(self):
+        s = _Stats()
+        _check(load().serve_get_stats(self.handle, ctypes.byref(s)), "serve_get_stats")
+        return {k: getattr(s, k) for k, _ in _Stats._fields_}
+
+    def close(self):
+        if getattr(self, "handle", None):
+            load().serve_destroy(self.handle)
+            self.handle = None
+            self._keep.clear()
 
     def __del__(self):
         try:

@@ -13,14 +13,14 @@ ROOT = os.path.dirname(HERE)
 CSRC = os.path.join(HERE, "csrc")
 OUT_DIR = os.path.join(HERE, "_build")
 LIB = os.path.join(OUT_DIR, "libgbwave.so")
-SOURCES = [os.path.join(CSRC, "wave.cu")]
-DEPS = SOURCES + [os.path.join(CSRC, f) for f in ("sweep.cuh", "ptx.cuh")] + [
-    os.path.join(ROOT, "include", "wave.h")]
+SOURCES = [os.path.join(CSRC, f) for f in ("wave.cu", "serve.cu")]
+DEPS = SOURCES + [os.path.join(CSRC, f) for f in ("sweep.cuh", "ptx.cuh", "common.cuh")] + [
+    os.path.join(ROOT, "include", f) for f in ("wave.h", "wave_serve.h")]
 
 NVCC_FLAGS = [
     "-gencode", "arch=compute_103a,code=sm_103a",
     "-O3", "-lineinfo", "-std=c++17",
-    "-Xcompiler", "-fPIC", "-shared",
+    "-Xcompiler", "-fPIC",
     "-Xptxas", "-v",
 ]
 
@@ -43,13 +43,29 @@ def build(force=False, verbose=False):
         return LIB
     os.makedirs(OUT_DIR, exist_ok=True)
     tmp = LIB + ".tmp%d" % os.getpid()
-    cmd = [nvcc_path()] + NVCC_FLAGS + SOURCES + ["-o", tmp]
-    proc = subprocess.run(cmd, capture_output=True, text=True)
+    # Compile the translation units in parallel, then link the shared library.
+    objs, procs = [], []
+    for src in SOURCES:
+        obj = os.path.join(OUT_DIR, os.path.basename(src) + ".o")
+        objs.append(obj)
+        cmd = [nvcc_path()] + NVCC_FLAGS + ["-c", src, "-o", obj]
+        procs.append(subprocess.Popen(cmd, stdout=subprocess.PIPE, stderr=subprocess.PIPE,
+                                      text=True))
+    logs = []
+    for p in procs:
+        out, err = p.communicate()
+        logs.append(err)
+        if p.returncode != 0:
+            sys.stderr.write(out + err)
+            raise RuntimeError("nvcc failed building %s" % LIB)
+    link = [nvcc_path(), "-gencode", "arch=compute_103a,code=sm_103a", "-shared",
+            "-Xcompiler", "-fPIC"] + objs + ["-o", tmp]
+    proc = subprocess.run(link, capture_output=True, text=True)
     if proc.returncode != 0:
         sys.stderr.write(proc.stdout + proc.stderr)
-        raise RuntimeError("nvcc failed building %s" % LIB)
+        raise RuntimeError("nvcc failed linking %s" % LIB)
     with open(os.path.join(OUT_DIR, "ptxas.log"), "w") as f:
-        f.write(proc.stderr)
+        f.write("".join(logs))
     if verbose:
         sys.stderr.write(proc.stderr)
     os.replace(tmp, LIB)

@@ -1,0 +1,307 @@
+// Host and setup-kernel helpers shared by the translation units of the
+// library (context API, allocation-free entry point, shot server). Internal:
+// every definition has internal linkage, so each .cu file gets its own copy.
+#pragma once
+
+#include <cuda.h>
+#include <cuda_runtime.h>
+#include <cudaTypedefs.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstdint>
+#include <cstring>
+#include <functional>
+#include <vector>
+
+#include "../../include/wave.h"
+#include "sweep.cuh"
+
+namespace {
+using namespace gbw;
+
+// 8th-order central second-derivative weights w_0..w_4 (Eq. 1's
+// discretization parameters, c_am = w_m / h_a^2).
+constexpr double kW[5] = {-205.0 / 72.0, 8.0 / 5.0, -1.0 / 5.0, 8.0 / 315.0,
+                          -1.0 / 560.0};
+
+// Velocity scan over the dense-in-x pitched buffer: max, and count of values
+// that are not finite and positive.
+__global__ void scan_velocity_kernel(const float *v, int nx, int px,
+                                     long long rows, unsigned *vmax_bits,
+                                     unsigned long long *nbad) {
+  unsigned local_max = 0;
+  unsigned long long local_bad = 0;
+  const long long total = rows * (long long)nx;
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+       i < total; i += (long long)gridDim.x * blockDim.x) {
+    const long long r = i / nx;
+    const int x = (int)(i - r * nx);
+    const float val = v[r * px + x];
+    if (!(val > 0.f) || !isfinite(val)) {
+      ++local_bad;
+    } else {
+      local_max = max(local_max, __float_as_uint(val));
+    }
+  }
+  for (int o = 16; o > 0; o >>= 1) {
+    local_max = max(local_max, __shfl_xor_sync(0xffffffffu, local_max, o));
+    local_bad += __shfl_xor_sync(0xffffffffu, local_bad, o);
+  }
+  if ((threadIdx.x & 31) == 0) {
+    atomicMax(vmax_bits, local_max);
+    if (local_bad) atomicAdd(nbad, local_bad);
+  }
+}
+
+// c = v^2 dt^2 in place (FP64 product, rounded once to FP32).
+__global__ void velocity_to_c_kernel(float *c, long long n, double dt2) {
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
+       i += (long long)gridDim.x * blockDim.x) {
+    const double v = c[i];
+    c[i] = (float)(v * v * dt2);
+  }
+}
+
+template <class T>
+__device__ __forceinline__ T from_f32(float v);
+template <>
+__device__ __forceinline__ __nv_bfloat16 from_f32(float v) {
+  return __float2bfloat16_rn(v);
+}
+template <>
+__device__ __forceinline__ __half from_f32(float v) {
+  return __float2half_rn(v);
+}
+__device__ __forceinline__ float to_f32(__nv_bfloat16 v) {
+  return __bfloat162float(v);
+}
+__device__ __forceinline__ float to_f32(__half v) { return __half2float(v); }
+
+// Dense FP32 (x fastest) -> pitched 16-bit field with scale 2^exps[slot].
+template <class T>
+__global__ void to_stored_kernel(T *dst, int pxu, const float *src, int nx,
+                                 long long rows, const StepDesc *d, int slot) {
+  const float inv = ldexpf(1.0f, -d->exps[slot]);
+  const long long total = rows * (long long)nx;
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+       i < total; i += (long long)gridDim.x * blockDim.x) {
+    const long long r = i / nx;
+    const int x = (int)(i - r * nx);
+    dst[r * pxu + x] = from_f32<T>(src[i] * inv);
+  }
+}
+
+// Pitched 16-bit field with scale 2^exps[slot] -> dense FP32.
+template <class T>
+__global__ void from_stored_kernel(float *dst, const T *src, int pxu, int nx,
+                                   long long rows, const StepDesc *d,
+                                   int slot) {
+  const float sc = ldexpf(1.0f, d->exps[slot]);
+  const long long total = rows * (long long)nx;
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+       i < total; i += (long long)gridDim.x * blockDim.x) {
+    const long long r = i / nx;
+    const int x = (int)(i - r * nx);
+    dst[i] = to_f32(src[r * pxu + x]) * sc;
+  }
+}
+
+// Largest |v| (as float bits) of a dense FP32 array.
+__global__ void absmax_kernel(const float *v, long long n, unsigned *out) {
+  unsigned m = 0;
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
+       i += (long long)gridDim.x * blockDim.x)
+    m = max(m, __float_as_uint(fabsf(v[i])));
+  for (int o = 16; o > 0; o >>= 1) m = max(m, __shfl_xor_sync(0xffffffffu, m, o));
+  if ((threadIdx.x & 31) == 0) atomicMax(out, m);
+}
+
+struct DeviceBuf {
+  void *p = nullptr;
+  size_t cap = 0;
+};
+
+int cuda_status(cudaError_t e) {
+  if (e == cudaSuccess) return WAVE_OK;
+  if (e == cudaErrorMemoryAllocation) return WAVE_ENOMEM;
+  return WAVE_ECUDA;
+}
+
+#define WAVE_TRY_CUDA(expr)                         \
+  do {                                              \
+    cudaError_t e_ = (expr);                        \
+    if (e_ != cudaSuccess) return cuda_status(e_);  \
+  } while (0)
+
+bool is_device_ptr(const void *p) {
+  cudaPointerAttributes at;
+  if (cudaPointerGetAttributes(&at, p) != cudaSuccess) {
+    cudaGetLastError();
+    return false;
+  }
+  return at.type == cudaMemoryTypeDevice || at.type == cudaMemoryTypeManaged;
+}
+
+int ensure(DeviceBuf &b, size_t bytes, cudaStream_t st) {
+  if (b.cap >= bytes) return WAVE_OK;
+  if (b.p) {
+    // Work queued earlier may still read the old buffer.
+    WAVE_TRY_CUDA(cudaStreamSynchronize(st));
+    cudaFree(b.p);
+    b.p = nullptr;
+    b.cap = 0;
+  }
+  size_t cap = std::max<size_t>(bytes, 256);
+  WAVE_TRY_CUDA(cudaMalloc(&b.p, cap));
+  b.cap = cap;
+  return WAVE_OK;
+}
+
+PFN_cuTensorMapEncodeTiled_v12000 get_encode() {
+  static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
+  if (!fn) {
+    void *p = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000,
+                                         cudaEnableDefault, &q) == cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      fn = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(p);
+  }
+  return fn;
+}
+
+CUtensorMapDataType field_dtype(int storage) {
+  if (storage == WAVE_STORAGE_BF16) return CU_TENSOR_MAP_DATA_TYPE_BFLOAT16;
+  if (storage == WAVE_STORAGE_F16) return CU_TENSOR_MAP_DATA_TYPE_FLOAT16;
+  return CU_TENSOR_MAP_DATA_TYPE_FLOAT32;
+}
+
+// Makespan of one launch in plane units: CTAs start in launch order (layer
+// by layer, tiles within a layer) on the earliest free of `slots` resident
+// slots and take (planes + kPreRoll) each; kPreRoll prices the 8 u-only
+// stages that refill the register queue at the start of every CTA.
+double layer_makespan(const std::vector<int> &chunks, long long ntiles,
+                      long long slots) {
+  constexpr double kPreRoll = 4.0;
+  std::vector<double> heap((size_t)std::min<long long>(slots, 1 << 20), 0.0);
+  double end = 0.0;
+  for (int c : chunks) {
+    for (long long t = 0; t < ntiles; ++t) {
+      std::pop_heap(heap.begin(), heap.end(), std::greater<double>());
+      const double e = heap.back() + c + kPreRoll;
+      heap.back() = e;
+      std::push_heap(heap.begin(), heap.end(), std::greater<double>());
+      end = std::max(end, e);
+    }
+  }
+  return end;
+}
+
+// Split nz into at most kMaxLayers z layers: uniform splits and "k equal
+// chunks then a tail of small chunks", scored by layer_makespan.
+std::vector<int> plan_layers(int nz, long long ntiles, long long slots) {
+  std::vector<std::vector<int>> cands;
+  for (int k = 1; k <= std::min(nz, kMaxLayers); ++k) {
+    const int zc = (nz + k - 1) / k;
+    std::vector<int> ch;
+    for (int z = 0; z < nz; z += zc) ch.push_back(std::min(zc, nz - z));
+    cands.push_back(ch);
+  }
+  for (int a = 16; a < nz; a += 8) {
+    for (int b : {8, 16, 24, 32, 48, 64}) {
+      if (b >= a) continue;
+      for (int tail = 1; tail <= 4; ++tail) {
+        if (a + tail * b > nz) break;
+        std::vector<int> ch;
+        int rest = nz - tail * b;
+        while (rest >= a) { ch.push_back(a); rest -= a; }
+        if (rest > 0) ch.push_back(rest);
+        for (int t = 0; t < tail; ++t) ch.push_back(b);
+        if ((int)ch.size() <= kMaxLayers) cands.push_back(ch);
+      }
+    }
+  }
+  // Cheap pre-filter by a wave model, then simulate the best few.
+  std::vector<std::pair<double, size_t>> score;
+  for (size_t i = 0; i < cands.size(); ++i) {
+    double w = 0;
+    for (int c : cands[i]) w += c + 4.0;
+    const double waves = (double)ntiles * cands[i].size() / (double)slots;
+    score.push_back({w * ntiles / (double)slots + waves, i});
+  }
+  std::sort(score.begin(), score.end());
+  size_t best = score[0].second;
+  double best_m = 1e300;
+  const size_t nsim = std::min<size_t>(score.size(), 48);
+  for (size_t r = 0; r < nsim; ++r) {
+    const size_t i = score[r].second;
+    const double m = layer_makespan(cands[i], ntiles, slots);
+    if (m < best_m - 1e-9) {
+      best_m = m;
+      best = i;
+    }
+  }
+  return cands[best];
+}
+
+void set_layers(SweepArgs &a, const std::vector<int> &ch) {
+  a.nlayers = (int)ch.size();
+  a.zl[0] = 0;
+  for (size_t l = 0; l < ch.size(); ++l) a.zl[l + 1] = a.zl[l] + ch[l];
+}
+
+double ricker(double t, double f, double t0, double amp) {
+  const double pi = 3.14159265358979323846;
+  const double a = pi * pi * f * f * (t - t0) * (t - t0);
+  return amp * (1.0 - 2.0 * a) * std::exp(-a);
+}
+
+bool finite_pos(double v) { return std::isfinite(v) && v > 0.0; }
+
+
+// 3D tensor map over a (nz, ny, pitch)-pitched field with logical extent
+// (nx, ny, nz); elements outside it read as zero (the zero halo).
+int encode_map(CUtensorMap *m, const void *base, int nx, int ny, int nz,
+               int pitch, int esize, CUtensorMapDataType dtype, int box_x,
+               int box_y) {
+  auto enc = get_encode();
+  if (!enc) return WAVE_ECUDA;
+  cuuint64_t dims[3] = {(cuuint64_t)nx, (cuuint64_t)ny, (cuuint64_t)nz};
+  cuuint64_t strides[2] = {(cuuint64_t)pitch * esize,
+                           (cuuint64_t)pitch * esize * (cuuint64_t)ny};
+  cuuint32_t box[3] = {(cuuint32_t)box_x, (cuuint32_t)box_y, 1};
+  cuuint32_t estr[3] = {1, 1, 1};
+  CUresult r = enc(m, dtype, 3, const_cast<void *>(base), dims, strides, box,
+                   estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
+                   CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                   CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  return r == CUDA_SUCCESS ? WAVE_OK : WAVE_ECUDA;
+}
+
+// Receivers (x, y, z) on the host -> entries {z, local index in tile, id,
+// tile} sorted by (tile, z, id) and per-tile start offsets (ntiles + 1).
+// Returns WAVE_EINVAL for a receiver outside the nx*ny*nz interior.
+int build_receiver_table(const int32_t *xyz, int nrec, int nx, int ny, int nz,
+                         int tx, int ty, int ntx, int ntiles,
+                         std::vector<int4> &entries, std::vector<int> &start) {
+  entries.resize(nrec);
+  start.assign((size_t)ntiles + 1, 0);
+  for (int r = 0; r < nrec; ++r) {
+    const int x = xyz[3 * r], y = xyz[3 * r + 1], z = xyz[3 * r + 2];
+    if (x < 0 || x >= nx || y < 0 || y >= ny || z < 0 || z >= nz)
+      return WAVE_EINVAL;
+    const int t = (y / ty) * ntx + (x / tx);
+    entries[r] = make_int4(z, (y % ty) * tx + (x % tx), r, t);
+    start[t + 1]++;
+  }
+  std::sort(entries.begin(), entries.end(), [](const int4 &a, const int4 &b) {
+    if (a.w != b.w) return a.w < b.w;
+    if (a.x != b.x) return a.x < b.x;
+    return a.z < b.z;
+  });
+  for (int t = 0; t < ntiles; ++t) start[t + 1] += start[t];
+  return WAVE_OK;
+}
+
+}  // namespace

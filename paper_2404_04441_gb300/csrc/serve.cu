@@ -1,0 +1,590 @@
+// Shot server (declared in include/wave_serve.h): requests queue on the
+// host, an engine thread admits them by device-memory budget and free slots,
+// advances every resident shot by one step per batched launch, and completes
+// shots as they reach their step counts.
+#include <chrono>
+#include <condition_variable>
+#include <cstdlib>
+#include <deque>
+#include <memory>
+#include <mutex>
+#include <thread>
+#include <unordered_map>
+
+#include "../../include/wave_serve.h"
+#include "common.cuh"
+#include "sweep.cuh"
+
+using namespace gbw;
+
+namespace {
+
+// One kernel configuration per storage type (index = WAVE_STORAGE_*), the
+// same tiles as the single-grid defaults.
+using ServeF32 = SweepCfg<32, 16, 1, 4, 4>;
+using ServeB16 = SweepCfg<64, 8, 1, 4, 4, __nv_bfloat16>;
+using ServeH16 = SweepCfg<64, 8, 1, 4, 4, __half>;
+constexpr int kKinds = 3;
+constexpr int kMaxGroup = 16;     // batch steps between two engine checks
+constexpr int kLayerPlanes = 128; // target z planes per CTA for batched shots
+
+struct Kind {
+  int tx, ty, hx, esize, threads;
+  size_t smem;
+  const void *func;
+  void (*launch)(int, cudaStream_t, const BatchShot *, int, long long);
+};
+
+template <class C>
+void launch_batch(int ctas, cudaStream_t st, const BatchShot *table, int n,
+                  long long k) {
+  wave_sweep_batched_kernel<C><<<ctas, C::THREADS, C::SMEM_BYTES, st>>>(
+      table, n, k);
+}
+
+template <class C>
+Kind make_kind() {
+  return Kind{C::TX,
+              C::TY,
+              C::HX,
+              (int)sizeof(typename C::T),
+              C::THREADS,
+              C::SMEM_BYTES,
+              reinterpret_cast<const void *>(&wave_sweep_batched_kernel<C>),
+              &launch_batch<C>};
+}
+
+const Kind &kind_of(int storage) {
+  static const Kind kinds[kKinds] = {make_kind<ServeF32>(), make_kind<ServeB16>(),
+                                     make_kind<ServeH16>()};
+  return kinds[storage];
+}
+
+size_t round_up(size_t x, size_t a) { return (x + a - 1) / a * a; }
+
+struct Request {
+  int64_t ticket = 0;
+  wave_request r{};
+  int status = WAVE_EBUSY;
+  double t_submit = 0, t_start = -1, t_done = -1, dt = 0;
+  int64_t steps_done = 0;
+  size_t bytes = 0;
+  // Resident state (engine thread only).
+  void *buf[2] = {nullptr, nullptr};
+  float *c = nullptr;
+  StepDesc *desc = nullptr;
+  float *wavelet = nullptr;
+  int4 *rec = nullptr;
+  int *rec_start = nullptr;
+  float *stage = nullptr;  // device trace staging when traces are host memory
+  bool host_traces = false;
+  BatchShot shot{};
+  int ctas = 0;
+  double points = 0;
+};
+
+// Device bytes of a request once resident (the budget unit).
+size_t request_bytes(const wave_request &r) {
+  const Kind &k = kind_of(r.storage);
+  const size_t nx = r.grid.nx, ny = r.grid.ny, nz = r.grid.nz;
+  const size_t pxu = r.storage == WAVE_STORAGE_F32 ? round_up(nx, 4)
+                                                   : round_up(nx, 8);
+  const size_t ntiles = ((nx + k.tx - 1) / k.tx) * ((ny + k.ty - 1) / k.ty);
+  size_t b = 2 * pxu * ny * nz * k.esize;          // wavefields
+  b += round_up(nx, 4) * ny * nz * 4;               // v^2 dt^2
+  b += sizeof(StepDesc) + (size_t)r.nsteps * 4;     // descriptor, wavelet
+  b += (size_t)r.nrec * sizeof(int4) + (ntiles + 1) * 4;
+  return b;  // plus a staging buffer for host traces (added at submit)
+}
+
+}  // namespace
+
+struct serve_ctx {
+  size_t budget = 0;
+  int max_slots = 0;
+  cudaStream_t stream = nullptr;
+  bool own_stream = false;
+  int device = 0;
+  std::chrono::steady_clock::time_point t0;
+  std::mutex mu;
+  std::condition_variable cv_engine, cv_done;
+  std::deque<Request *> queue;
+  std::unordered_map<int64_t, std::unique_ptr<Request>> all;
+  int64_t next_ticket = 1;
+  bool stopping = false;
+  serve_stats_t st{};
+  std::thread engine;
+  // Engine thread only.
+  std::vector<Request *> resident;
+  size_t bytes = 0;
+  long long k = 0;  // batch steps taken
+  BatchShot *d_table[kKinds] = {nullptr, nullptr, nullptr};
+  std::vector<BatchShot> h_table[kKinds];
+  int table_ctas[kKinds] = {0, 0, 0};
+  bool dirty = true;
+  void *d_scan = nullptr;     // 16 bytes: velocity max, invalid count
+  long long fault_alloc = -1; // host fault injection: fail this allocation
+  long long allocs = 0;
+
+  double now() const {
+    return std::chrono::duration<double>(std::chrono::steady_clock::now() - t0)
+        .count();
+  }
+};
+
+namespace {
+
+int serve_alloc(serve_ctx *s, void **p, size_t bytes) {
+  *p = nullptr;
+  if (s->fault_alloc >= 0 && s->allocs++ == s->fault_alloc) return WAVE_ENOMEM;
+  WAVE_TRY_CUDA(cudaMallocAsync(p, std::max<size_t>(bytes, 256), s->stream));
+  return WAVE_OK;
+}
+
+void release(serve_ctx *s, Request *q) {
+  void *ps[] = {q->buf[0], q->buf[1], q->c,        q->desc,
+                q->wavelet, q->rec,   q->rec_start, q->stage};
+  for (void *p : ps)
+    if (p) cudaFreeAsync(p, s->stream);
+  q->buf[0] = q->buf[1] = nullptr;
+  q->c = nullptr;
+  q->desc = nullptr;
+  q->wavelet = nullptr;
+  q->rec = nullptr;
+  q->rec_start = nullptr;
+  q->stage = nullptr;
+}
+
+void finish(serve_ctx *s, Request *q, int status) {
+  std::lock_guard<std::mutex> lk(s->mu);
+  q->status = status;
+  q->t_done = s->now();
+  if (status == WAVE_OK)
+    s->st.completed++;
+  else
+    s->st.failed++;
+  s->cv_done.notify_all();
+}
+
+// Make a queued request resident: buffers, v^2 dt^2, tables, tensor maps.
+int admit(serve_ctx *s, Request *q) {
+  const wave_request &r = q->r;
+  const Kind &kd = kind_of(r.storage);
+  cudaStream_t st = s->stream;
+  const int nx = r.grid.nx, ny = r.grid.ny, nz = r.grid.nz;
+  const int px = (int)round_up(nx, 4);
+  const int pxu = r.storage == WAVE_STORAGE_F32 ? px : (int)round_up(nx, 8);
+  const int ntx = (nx + kd.tx - 1) / kd.tx, nty = (ny + kd.ty - 1) / kd.ty;
+  const int ntiles = ntx * nty;
+  const size_t fbytes = (size_t)pxu * ny * nz * kd.esize;
+  const size_t cbytes = (size_t)px * ny * nz * 4;
+  int e;
+  if ((e = serve_alloc(s, &q->buf[0], fbytes)) ||
+      (e = serve_alloc(s, &q->buf[1], fbytes)) ||
+      (e = serve_alloc(s, (void **)&q->c, cbytes)) ||
+      (e = serve_alloc(s, (void **)&q->desc, sizeof(StepDesc))) ||
+      (e = serve_alloc(s, (void **)&q->wavelet, (size_t)r.nsteps * 4)) ||
+      (e = serve_alloc(s, (void **)&q->rec, (size_t)r.nrec * sizeof(int4))) ||
+      (e = serve_alloc(s, (void **)&q->rec_start, (size_t)(ntiles + 1) * 4)))
+    return e;
+  q->host_traces = r.nrec > 0 && !is_device_ptr(r.traces);
+  if (q->host_traces &&
+      (e = serve_alloc(s, (void **)&q->stage, (size_t)r.nsteps * r.nrec * 4)))
+    return e;
+  WAVE_TRY_CUDA(cudaMemsetAsync(q->buf[0], 0, fbytes, st));
+  WAVE_TRY_CUDA(cudaMemsetAsync(q->buf[1], 0, fbytes, st));
+  WAVE_TRY_CUDA(cudaMemsetAsync(q->c, 0, cbytes, st));
+
+  // Velocity: validate, then v^2 dt^2.
+  WAVE_TRY_CUDA(cudaMemcpy2DAsync(q->c, (size_t)px * 4, r.velocity,
+                                  (size_t)nx * 4, (size_t)nx * 4,
+                                  (size_t)ny * nz, cudaMemcpyDefault, st));
+  WAVE_TRY_CUDA(cudaMemsetAsync(s->d_scan, 0, 16, st));
+  int sms = 0;
+  WAVE_TRY_CUDA(
+      cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, s->device));
+  scan_velocity_kernel<<<sms * 4, 256, 0, st>>>(
+      q->c, nx, px, (long long)ny * nz, reinterpret_cast<unsigned *>(s->d_scan),
+      reinterpret_cast<unsigned long long *>((char *)s->d_scan + 8));
+  WAVE_TRY_CUDA(cudaGetLastError());
+  unsigned char res[16];
+  WAVE_TRY_CUDA(cudaMemcpyAsync(res, s->d_scan, 16, cudaMemcpyDeviceToHost, st));
+  WAVE_TRY_CUDA(cudaStreamSynchronize(st));
+  unsigned vb;
+  unsigned long long bad;
+  std::memcpy(&vb, res, 4);
+  std::memcpy(&bad, res + 8, 8);
+  if (bad) return WAVE_EINVAL;
+  float vmax;
+  std::memcpy(&vmax, &vb, 4);
+  const double lim = wave_cfl_dt(&r.spacing, (double)vmax);
+  const double dt = r.dt > 0 ? r.dt : 0.5 * lim;
+  if (!(dt <= lim * (1.0 + 1e-12))) return WAVE_EUNSTABLE;
+  q->dt = dt;
+  velocity_to_c_kernel<<<sms * 4, 256, 0, st>>>(q->c, (long long)px * ny * nz,
+                                                dt * dt);
+  WAVE_TRY_CUDA(cudaGetLastError());
+
+  // Receivers and source wavelet.
+  std::vector<int32_t> xyz((size_t)r.nrec * 3);
+  if (r.nrec > 0) {
+    WAVE_TRY_CUDA(cudaMemcpy(xyz.data(), r.rec_xyz, xyz.size() * 4,
+                             cudaMemcpyDefault));
+  }
+  std::vector<int4> entries;
+  std::vector<int> starts;
+  if ((e = build_receiver_table(xyz.data(), r.nrec, nx, ny, nz, kd.tx, kd.ty,
+                                ntx, ntiles, entries, starts)))
+    return e;
+  std::vector<float> wl(r.nsteps);
+  const double t0 = r.shot.t0 < 0 ? 1.0 / r.shot.f_peak : r.shot.t0;
+  for (int n = 0; n < r.nsteps; ++n)
+    wl[n] = (float)ricker(n * dt, r.shot.f_peak, t0, r.shot.amp);
+  if (r.nrec > 0)
+    WAVE_TRY_CUDA(cudaMemcpyAsync(q->rec, entries.data(),
+                                  entries.size() * sizeof(int4),
+                                  cudaMemcpyHostToDevice, st));
+  WAVE_TRY_CUDA(cudaMemcpyAsync(q->rec_start, starts.data(), starts.size() * 4,
+                                cudaMemcpyHostToDevice, st));
+  WAVE_TRY_CUDA(cudaMemcpyAsync(q->wavelet, wl.data(), wl.size() * 4,
+                                cudaMemcpyHostToDevice, st));
+  StepDesc d{};
+  d.wavelet = q->wavelet;
+  d.traces = q->host_traces ? q->stage : r.traces;
+  d.rec = q->rec;
+  d.rec_start = q->rec_start;
+  d.nrec = r.nrec;
+  d.src_active = 1;
+  d.sx = r.shot.sx;
+  d.sy = r.shot.sy;
+  d.sz = r.shot.sz;
+  WAVE_TRY_CUDA(
+      cudaMemcpyAsync(q->desc, &d, sizeof(d), cudaMemcpyHostToDevice, st));
+
+  // Batch entry: tensor maps for both buffer parities, arguments.
+  BatchShot &b = q->shot;
+  std::memset(&b, 0, sizeof(b));
+  const CUtensorMapDataType dtf = field_dtype(r.storage);
+  for (int i = 0; i < 2; ++i) {
+    if ((e = encode_map(&b.halo[i], q->buf[i], nx, ny, nz, pxu, kd.esize, dtf,
+                        kd.tx + 2 * kd.hx, kd.ty + 2 * kR)))
+      return e;
+    if ((e = encode_map(&b.tile[i], q->buf[i], nx, ny, nz, pxu, kd.esize, dtf,
+                        kd.tx, kd.ty)))
+      return e;
+  }
+  if ((e = encode_map(&b.cmap, q->c, nx, ny, nz, px, 4,
+                      CU_TENSOR_MAP_DATA_TYPE_FLOAT32, kd.tx, kd.ty)))
+    return e;
+  SweepArgs &a = b.args;
+  a.nx = nx;
+  a.ny = ny;
+  a.nz = nz;
+  a.px = pxu;
+  const int nl =
+      std::min(kMaxLayers, std::max(1, (nz + kLayerPlanes - 1) / kLayerPlanes));
+  const int zc = (nz + nl - 1) / nl;
+  std::vector<int> layers;
+  for (int z = 0; z < nz; z += zc) layers.push_back(std::min(zc, nz - z));
+  set_layers(a, layers);
+  a.ntx = ntx;
+  const double ix = 1.0 / (r.spacing.dx * r.spacing.dx),
+               iy = 1.0 / (r.spacing.dy * r.spacing.dy),
+               iz = 1.0 / (r.spacing.dz * r.spacing.dz);
+  a.c0 = (float)(kW[0] * (ix + iy + iz));
+  for (int m = 1; m <= 4; ++m) {
+    a.cx[m - 1] = (float)(kW[m] * ix);
+    a.cy[m - 1] = (float)(kW[m] * iy);
+    a.cz[m - 1] = (float)(kW[m] * iz);
+  }
+  a.desc = q->desc;
+  a.cmax = (float)((double)vmax * vmax * dt * dt);
+  b.buf[0] = q->buf[0];
+  b.buf[1] = q->buf[1];
+  b.b0 = s->k;
+  b.ntx = ntx;
+  b.nty = nty;
+  q->ctas = ntiles * (int)layers.size();
+  q->points = (double)nx * ny * nz;
+  return WAVE_OK;
+}
+
+int upload_tables(serve_ctx *s) {
+  for (int kd = 0; kd < kKinds; ++kd) {
+    auto &t = s->h_table[kd];
+    t.clear();
+    int ctas = 0;
+    for (Request *q : s->resident) {
+      if (q->r.storage != kd) continue;
+      q->shot.cta_begin = ctas;
+      ctas += q->ctas;
+      t.push_back(q->shot);
+    }
+    s->table_ctas[kd] = ctas;
+    if (!t.empty())
+      WAVE_TRY_CUDA(cudaMemcpyAsync(s->d_table[kd], t.data(),
+                                    t.size() * sizeof(BatchShot),
+                                    cudaMemcpyHostToDevice, s->stream));
+  }
+  s->dirty = false;
+  return WAVE_OK;
+}
+
+// Complete a resident shot whose steps are all done (stream synchronized).
+void complete(serve_ctx *s, Request *q) {
+  int status = WAVE_OK;
+  int err = 0;
+  cudaError_t e = cudaMemcpyAsync(&err, &q->desc->error, sizeof(int),
+                                  cudaMemcpyDeviceToHost, s->stream);
+  if (e == cudaSuccess && q->host_traces)
+    e = cudaMemcpyAsync(q->r.traces, q->stage,
+                        (size_t)q->r.nsteps * q->r.nrec * 4,
+                        cudaMemcpyDeviceToHost, s->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s->stream);
+  if (e != cudaSuccess)
+    status = cuda_status(e);
+  else if (err)
+    status = err == kErrTimeout ? WAVE_ETIMEOUT : WAVE_ECUDA;
+  release(s, q);
+  finish(s, q, status);
+}
+
+void engine_main(serve_ctx *s) {
+  cudaSetDevice(s->device);
+  for (;;) {
+    // Admission: first in, first out, while budget and slots allow.
+    for (;;) {
+      Request *q = nullptr;
+      {
+        std::lock_guard<std::mutex> lk(s->mu);
+        if (!s->queue.empty() && (int)s->resident.size() < s->max_slots &&
+            s->bytes + s->queue.front()->bytes <= s->budget) {
+          q = s->queue.front();
+          s->queue.pop_front();
+          s->st.queued--;
+        }
+      }
+      if (!q) break;
+      const int e = admit(s, q);
+      if (e != WAVE_OK) {
+        cudaGetLastError();
+        release(s, q);
+        cudaStreamSynchronize(s->stream);
+        finish(s, q, e);
+        continue;
+      }
+      {
+        std::lock_guard<std::mutex> lk(s->mu);
+        q->t_start = s->now();
+        s->resident.push_back(q);
+        s->bytes += q->bytes;
+        s->st.resident = (int64_t)s->resident.size();
+        s->st.bytes_resident = s->bytes;
+        s->st.bytes_peak = std::max(s->st.bytes_peak, s->bytes);
+        s->st.resident_peak =
+            std::max(s->st.resident_peak, (int)s->resident.size());
+      }
+      s->dirty = true;
+    }
+    if (s->resident.empty()) {
+      std::unique_lock<std::mutex> lk(s->mu);
+      if (s->stopping && s->queue.empty()) break;
+      s->cv_engine.wait(lk, [&] { return s->stopping || !s->queue.empty(); });
+      continue;
+    }
+
+    const double tb = s->now();
+    int status = WAVE_OK;
+    if (s->dirty) status = upload_tables(s);
+    int K = kMaxGroup;
+    for (Request *q : s->resident)
+      K = (int)std::min<int64_t>(K, q->r.nsteps - q->steps_done);
+    for (int kk = 0; kk < K && status == WAVE_OK; ++kk)
+      for (int kd = 0; kd < kKinds; ++kd)
+        if (s->table_ctas[kd] > 0)
+          kind_of(kd).launch(s->table_ctas[kd], s->stream, s->d_table[kd],
+                             (int)s->h_table[kd].size(), s->k + kk);
+    cudaError_t e = cudaGetLastError();
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s->stream);
+    if (status == WAVE_OK && e != cudaSuccess) status = cuda_status(e);
+    s->k += K;
+    {
+      std::lock_guard<std::mutex> lk(s->mu);
+      s->st.batch_steps += K;
+      s->st.busy_s += s->now() - tb;
+      for (Request *q : s->resident) {
+        q->steps_done += K;
+        s->st.point_steps += q->points * K;
+      }
+    }
+    // Completion (or failure of everything resident if the launch failed).
+    std::vector<Request *> keep;
+    for (Request *q : s->resident) {
+      if (status != WAVE_OK) {
+        release(s, q);
+        finish(s, q, status);
+      } else if (q->steps_done >= q->r.nsteps) {
+        complete(s, q);
+      } else {
+        keep.push_back(q);
+        continue;
+      }
+      s->bytes -= q->bytes;
+      s->dirty = true;
+    }
+    std::lock_guard<std::mutex> lk(s->mu);
+    s->resident.swap(keep);
+    s->st.resident = (int64_t)s->resident.size();
+    s->st.bytes_resident = s->bytes;
+  }
+}
+
+int validate_request(const wave_request *r) {
+  if (!r || !r->velocity) return WAVE_EINVAL;
+  if (r->grid.nx < 1 || r->grid.ny < 1 || r->grid.nz < 1) return WAVE_EINVAL;
+  if ((long long)r->grid.nx * r->grid.ny * r->grid.nz > (1ll << 36))
+    return WAVE_EINVAL;
+  if (!finite_pos(r->spacing.dx) || !finite_pos(r->spacing.dy) ||
+      !finite_pos(r->spacing.dz) || !std::isfinite(r->dt))
+    return WAVE_EINVAL;
+  if (r->storage < 0 || r->storage >= kKinds) return WAVE_ENOTSUP;
+  if (r->nsteps < 1 || r->nrec < 0) return WAVE_EINVAL;
+  if (r->nrec > 0 && (!r->rec_xyz || !r->traces)) return WAVE_EINVAL;
+  const wave_shot &sh = r->shot;
+  if (sh.sx < 0 || sh.sx >= r->grid.nx || sh.sy < 0 || sh.sy >= r->grid.ny ||
+      sh.sz < 0 || sh.sz >= r->grid.nz || !finite_pos(sh.f_peak) ||
+      !std::isfinite(sh.t0) || !std::isfinite(sh.amp))
+    return WAVE_EINVAL;
+  return WAVE_OK;
+}
+
+void fill_result(const Request *q, wave_result *out) {
+  if (!out) return;
+  out->status = q->status;
+  out->ticket = q->ticket;
+  out->submit_s = q->t_submit;
+  out->start_s = q->t_start;
+  out->done_s = q->t_done;
+  out->dt = q->dt;
+  out->steps_done = std::min<int64_t>(q->steps_done, q->r.nsteps);
+}
+
+}  // namespace
+
+extern "C" {
+
+int serve_create(size_t hbm_budget_bytes, int max_slots, void *stream,
+                 serve_ctx **out) {
+  if (!out) return WAVE_EINVAL;
+  *out = nullptr;
+  if (hbm_budget_bytes == 0 || max_slots < 1 || max_slots > 4096)
+    return WAVE_EINVAL;
+  std::unique_ptr<serve_ctx> s(new (std::nothrow) serve_ctx());
+  if (!s) return WAVE_ENOMEM;
+  s->budget = hbm_budget_bytes;
+  s->max_slots = max_slots;
+  s->t0 = std::chrono::steady_clock::now();
+  WAVE_TRY_CUDA(cudaGetDevice(&s->device));
+  if (stream) {
+    s->stream = reinterpret_cast<cudaStream_t>(stream);
+  } else {
+    WAVE_TRY_CUDA(cudaStreamCreateWithFlags(&s->stream, cudaStreamNonBlocking));
+    s->own_stream = true;
+  }
+  int e = WAVE_OK;
+  for (int kd = 0; kd < kKinds && e == WAVE_OK; ++kd) {
+    const Kind &k = kind_of(kd);
+    e = cuda_status(cudaFuncSetAttribute(
+        k.func, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)k.smem));
+    if (e == WAVE_OK)
+      e = cuda_status(cudaMalloc((void **)&s->d_table[kd],
+                                 sizeof(BatchShot) * (size_t)max_slots));
+  }
+  if (e == WAVE_OK) e = cuda_status(cudaMalloc(&s->d_scan, 16));
+  if (const char *f = std::getenv("GBWAVE_SERVE_FAULT_ALLOC"))
+    s->fault_alloc = std::atoll(f);
+  if (e != WAVE_OK) {
+    for (int kd = 0; kd < kKinds; ++kd) cudaFree(s->d_table[kd]);
+    cudaFree(s->d_scan);
+    if (s->own_stream) cudaStreamDestroy(s->stream);
+    return e;
+  }
+  serve_ctx *raw = s.release();
+  raw->engine = std::thread(engine_main, raw);
+  *out = raw;
+  return WAVE_OK;
+}
+
+int serve_submit(serve_ctx *s, const wave_request *req, int64_t *ticket) {
+  if (!s || !ticket) return WAVE_EINVAL;
+  *ticket = 0;
+  const int v = validate_request(req);
+  if (v != WAVE_OK) return v;
+  std::unique_ptr<Request> q(new (std::nothrow) Request());
+  if (!q) return WAVE_ENOMEM;
+  q->r = *req;
+  q->bytes = request_bytes(*req);
+  if (req->nrec > 0 && !is_device_ptr(req->traces))
+    q->bytes += (size_t)req->nsteps * req->nrec * 4;
+  if (q->bytes > s->budget) return WAVE_ETOOBIG;
+  std::lock_guard<std::mutex> lk(s->mu);
+  if (s->stopping) return WAVE_EBUSY;
+  q->ticket = s->next_ticket++;
+  q->t_submit = s->now();
+  *ticket = q->ticket;
+  s->queue.push_back(q.get());
+  s->all.emplace(q->ticket, std::move(q));
+  s->st.submitted++;
+  s->st.queued++;
+  s->cv_engine.notify_one();
+  return WAVE_OK;
+}
+
+int serve_poll(serve_ctx *s, int64_t ticket, wave_result *out) {
+  if (!s) return WAVE_EINVAL;
+  std::lock_guard<std::mutex> lk(s->mu);
+  auto it = s->all.find(ticket);
+  if (it == s->all.end()) return WAVE_EINVAL;
+  fill_result(it->second.get(), out);
+  return it->second->status;
+}
+
+int serve_wait(serve_ctx *s, int64_t ticket, double timeout_s,
+               wave_result *out) {
+  if (!s) return WAVE_EINVAL;
+  std::unique_lock<std::mutex> lk(s->mu);
+  auto it = s->all.find(ticket);
+  if (it == s->all.end()) return WAVE_EINVAL;
+  Request *q = it->second.get();
+  auto done = [&] { return q->status != WAVE_EBUSY; };
+  if (timeout_s < 0)
+    s->cv_done.wait(lk, done);
+  else
+    s->cv_done.wait_for(lk, std::chrono::duration<double>(timeout_s), done);
+  fill_result(q, out);
+  return q->status;
+}
+
+int serve_get_stats(serve_ctx *s, serve_stats_t *out) {
+  if (!s || !out) return WAVE_EINVAL;
+  std::lock_guard<std::mutex> lk(s->mu);
+  *out = s->st;
+  return WAVE_OK;
+}
+
+void serve_destroy(serve_ctx *s) {
+  if (!s) return;
+  {
+    std::lock_guard<std::mutex> lk(s->mu);
+    s->stopping = true;
+    s->cv_engine.notify_all();
+  }
+  if (s->engine.joinable()) s->engine.join();
+  cudaStreamSynchronize(s->stream);
+  for (int kd = 0; kd < kKinds; ++kd) cudaFree(s->d_table[kd]);
+  cudaFree(s->d_scan);
+  if (s->own_stream) cudaStreamDestroy(s->stream);
+  delete s;
+}
+
+}  // extern "C"

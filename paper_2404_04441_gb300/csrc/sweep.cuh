@@ -213,15 +213,18 @@ __device__ __forceinline__ float exp2_int(int k) {
 // kVelocityField = false: tm_c maps v^2 dt^2. true: tm_c maps the velocity
 // itself and the kernel forms v^2 dt^2 from it (the allocation-free entry
 // point, which has no buffer of its own to hold v^2 dt^2).
-template <class C, bool kVelocityField = false>
-__global__ void __launch_bounds__(C::THREADS, C::MINB)
-    wave_sweep_kernel(const __grid_constant__ CUtensorMap tm_u,
-                      const __grid_constant__ CUtensorMap tm_up,
-                      const __grid_constant__ CUtensorMap tm_c,
-                      const SweepArgs a) {
+//
+// sweep_cta is the work of one CTA: tile (bx, by) of the grid, z layer bz.
+// tm_u / tm_up / tm_c point to the tensor maps (kernel parameters or global
+// memory), smem_raw to the dynamic shared memory.
+template <class C, bool kVelocityField>
+__device__ __forceinline__ void sweep_cta(const CUtensorMap *tm_u,
+                                          const CUtensorMap *tm_up,
+                                          const CUtensorMap *tm_c,
+                                          const SweepArgs &a, int bx, int by,
+                                          int bz, unsigned char *smem_raw) {
   using T = typename C::T;
   using E = Elem<T>;
-  extern __shared__ unsigned char smem_raw[];
   unsigned char *base = reinterpret_cast<unsigned char *>(
       (reinterpret_cast<uintptr_t>(smem_raw) + 127) & ~uintptr_t(127));
   T *su = reinterpret_cast<T *>(base);
@@ -234,10 +237,10 @@ __global__ void __launch_bounds__(C::THREADS, C::MINB)
   const int tid = threadIdx.x;
   const int tx = tid % C::NTX;
   const int ty = tid / C::NTX;
-  const int x0 = blockIdx.x * C::TX;
-  const int y0 = blockIdx.y * C::TY;
-  const int zb = a.zl[blockIdx.z];
-  const int ze = a.zl[blockIdx.z + 1];
+  const int x0 = bx * C::TX;
+  const int y0 = by * C::TY;
+  const int zb = a.zl[bz];
+  const int ze = a.zl[bz + 1];
   const int NS = (ze - zb) + 2 * kR;  // stages: 8 to fill the queue, then one per plane
 
   // Per-call state.
@@ -251,7 +254,7 @@ __global__ void __launch_bounds__(C::THREADS, C::MINB)
   int rcur = 0, rend = 0;
   const int4 *rec = d->rec;
   if (nrec > 0) {
-    const int tile = blockIdx.y * a.ntx + blockIdx.x;
+    const int tile = by * a.ntx + bx;
     rcur = d->rec_start[tile];
     rend = d->rec_start[tile + 1];
     while (rcur < rend && rec[rcur].x < zb) ++rcur;
@@ -283,7 +286,7 @@ __global__ void __launch_bounds__(C::THREADS, C::MINB)
     s2 = exp2_int(eup - eo);
     so = exp2_int(eo);
     wsrc *= exp2_int(-eo);
-    if (blockIdx.x == 0 && blockIdx.y == 0 && blockIdx.z == 0 && tid == 0) {
+    if (bx == 0 && by == 0 && bz == 0 && tid == 0) {
       d->exps[(ab + 1) & 3] = eo;     // read by the next step only
       d->maxbits[(ab + 2) & 3] = 0u;  // accumulated by the next step
     }
@@ -291,9 +294,9 @@ __global__ void __launch_bounds__(C::THREADS, C::MINB)
   float vmax_out = 0.f;  // largest |output| of this thread (stored units)
 
   if (tid == 0) {
-    prefetch_tensormap(&tm_u);
-    prefetch_tensormap(&tm_up);
-    prefetch_tensormap(&tm_c);
+    prefetch_tensormap(tm_u);
+    prefetch_tensormap(tm_up);
+    prefetch_tensormap(tm_c);
     for (int b = 0; b < C::NB; ++b) mbar_init(&bars[b], 1);
     fence_barrier_init();
   }
@@ -307,11 +310,11 @@ __global__ void __launch_bounds__(C::THREADS, C::MINB)
     const bool full = j >= zb;
     mbar_arrive_expect_tx(bar,
                           C::U_BYTES + (full ? C::UP_BYTES + C::C_BYTES : 0));
-    tma_load_3d(su + (s % C::SU) * C::U_SLOT, &tm_u, bar, x0 - C::HX, y0 - kR,
+    tma_load_3d(su + (s % C::SU) * C::U_SLOT, tm_u, bar, x0 - C::HX, y0 - kR,
                 j + kR);
     if (full) {
-      tma_load_3d(sp + (s % C::SP) * C::P_SLOT, &tm_up, bar, x0, y0, j);
-      tma_load_3d(sc + (s % C::SP) * C::P_SLOT, &tm_c, bar, x0, y0, j);
+      tma_load_3d(sp + (s % C::SP) * C::P_SLOT, tm_up, bar, x0, y0, j);
+      tma_load_3d(sc + (s % C::SP) * C::P_SLOT, tm_c, bar, x0, y0, j);
     }
   };
   if (tid == 0)
@@ -540,6 +543,76 @@ wait_failed:
     }
     __syncthreads();
   }
+}
+
+// One step of one grid: CTA (blockIdx.x, .y) is a tile, blockIdx.z a z layer.
+template <class C, bool kVelocityField = false>
+__global__ void __launch_bounds__(C::THREADS, C::MINB)
+    wave_sweep_kernel(const __grid_constant__ CUtensorMap tm_u,
+                      const __grid_constant__ CUtensorMap tm_up,
+                      const __grid_constant__ CUtensorMap tm_c,
+                      const SweepArgs a) {
+  extern __shared__ unsigned char smem_raw[];
+  sweep_cta<C, kVelocityField>(&tm_u, &tm_up, &tm_c, a, blockIdx.x, blockIdx.y,
+                               blockIdx.z, smem_raw);
+}
+
+// One shot of a batch (device memory, 128-byte aligned): its tensor maps for
+// both buffer parities, its arguments, and where its CTAs start.
+struct alignas(128) BatchShot {
+  CUtensorMap halo[2];  // u halo box over buf[0] / buf[1]
+  CUtensorMap tile[2];  // u_prev tile box over buf[0] / buf[1]
+  CUtensorMap cmap;     // v^2 dt^2 tile box
+  SweepArgs args;       // unext and koff are set per launch
+  void *buf[2];         // buf[0] holds the shot's step 0
+  long long b0;         // batch step at which the shot takes its step 0
+  int cta_begin;        // first linear CTA index of this shot
+  int ntx, nty;         // tiles; args.nlayers layers
+};
+
+__device__ __forceinline__ void tensormap_acquire(const CUtensorMap *m) {
+  asm volatile(
+      "fence.proxy.tensormap::generic.acquire.gpu [%0], 128;" ::"l"(
+          reinterpret_cast<uint64_t>(m))
+      : "memory");
+}
+
+// One step of every shot of a batch: the 1D grid is the concatenation of the
+// shots' CTA grids (shot i owns [cta_begin_i, cta_begin_{i+1})). Batch step k
+// is step k - b0 of each shot; each shot's buffers alternate from its own
+// step 0, so a shot computes exactly what the single-grid kernel computes.
+template <class C>
+__global__ void __launch_bounds__(C::THREADS, C::MINB)
+    wave_sweep_batched_kernel(const BatchShot *__restrict__ shots, int nshots,
+                              long long k) {
+  extern __shared__ unsigned char smem_raw[];
+  const int lin = blockIdx.x;
+  int lo = 0, hi = nshots - 1;
+  while (lo < hi) {
+    const int mid = (lo + hi + 1) >> 1;
+    if (shots[mid].cta_begin <= lin) lo = mid; else hi = mid - 1;
+  }
+  const BatchShot &sh = shots[lo];
+  const int local = lin - sh.cta_begin;
+  const int per_layer = sh.ntx * sh.nty;
+  const int bz = local / per_layer;
+  const int rem = local - bz * per_layer;
+  const int by = rem / sh.ntx;
+  const int bx = rem - by * sh.ntx;
+  const long long n = k - sh.b0;  // the shot's own step
+  const int cur = (int)(n & 1);   // buffer holding the shot's u
+  __shared__ SweepArgs a;         // uniform per CTA: read with broadcast loads
+  if (threadIdx.x == 0) {
+    a = sh.args;
+    a.unext = sh.buf[cur ^ 1];
+    a.koff = (int)n;
+    tensormap_acquire(&sh.halo[cur]);
+    tensormap_acquire(&sh.tile[cur ^ 1]);
+    tensormap_acquire(&sh.cmap);
+  }
+  __syncthreads();
+  sweep_cta<C, false>(&sh.halo[cur], &sh.tile[cur ^ 1], &sh.cmap, a, bx, by, bz,
+                      smem_raw);
 }
 
 }  // namespace gbw

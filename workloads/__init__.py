@@ -138,6 +138,44 @@ def random_receivers(nx, ny, nz, n, seed):
     return np.ascontiguousarray(rec, dtype=np.int32)
 
 
+def layered_profile(nz, seed, nlayers=8, vmin=1500.0, vmax=4500.0):
+    """float32 (nz,) velocities of a random horizontally layered model."""
+    rng = np.random.default_rng(seed)
+    depths = np.sort(rng.integers(1, max(2, nz), size=nlayers - 1))
+    vels = np.sort(rng.uniform(vmin, vmax, size=nlayers))
+    return vels[np.searchsorted(depths, np.arange(nz), side="right")].astype(np.float32)
+
+
+def layered_volume(nx, ny, nz, seed):
+    """float32 (nz, ny, nx) random layered model (no lateral variation)."""
+    vz = layered_profile(nz, seed)
+    return np.ascontiguousarray(np.broadcast_to(vz[:, None, None], (nz, ny, nx)))
+
+
+# Shot-serving stream: Poisson arrivals of independent shots of uneven sizes.
+SERVE_STREAM = dict(n=256, rate_per_s=20.0, seed=0, sizes=tuple(range(128, 513, 32)),
+                    steps=(300, 800), src_z=10, rec_z=8, rec_stride=4,
+                    budget_bytes=150 * 10 ** 9)
+
+
+def serving_requests(n=256, rate_per_s=20.0, seed=0, sizes=tuple(range(128, 513, 32)),
+                     steps=(300, 800), src_z=10, **_):
+    """Seeded request list: arrival time (s), grid (nx, ny, nz), nsteps,
+    source (x, y, z) and the seed of its layered velocity model."""
+    rng = np.random.default_rng(seed)
+    t = 0.0
+    out = []
+    for i in range(n):
+        t += rng.exponential(1.0 / rate_per_s)
+        nx, ny, nz = (int(rng.choice(sizes)) for _ in range(3))
+        out.append(dict(arrival_s=t, grid=(nx, ny, nz),
+                        nsteps=int(rng.integers(steps[0], steps[1] + 1)),
+                        source=(int(rng.integers(0, nx)), int(rng.integers(0, ny)),
+                                min(src_z, nz - 1)),
+                        vel_seed=int(rng.integers(0, 2 ** 31))))
+    return out
+
+
 def velocity_for(cfg):
     """The velocity model a workload description names."""
     nx, ny, nz = cfg["shape"]
