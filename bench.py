@@ -255,6 +255,49 @@ def serve_stream(gw, torch, storage, n_requests, max_slots=32):
             "arrival_rate_per_s": spec["rate_per_s"]}
 
 
+def serve_saturated(gw, torch, n_requests=48):
+    """Capacity on the stream's shot mix: the first n requests submitted at
+    once to the server (FP32 and FP16 storage) against the same shots run one
+    after another through the plain FP32 single-grid path."""
+    reqs = wl.serving_requests(**dict(wl.SERVE_STREAM, n=n_requests))
+    made = []
+    for r in reqs:
+        nx, ny, nz = r["grid"]
+        vz = torch.from_numpy(wl.layered_profile(nz, r["vel_seed"])).cuda()
+        vel = vz[:, None, None].expand(nz, ny, nx).contiguous()
+        rec = torch.from_numpy(wl.receiver_plane(nx, ny, min(8, nz - 1), 4)).cuda()
+        made.append((r, vel, rec))
+    work = sum(r["grid"][0] * r["grid"][1] * r["grid"][2] * r["nsteps"] for r in reqs)
+    out = {"requests": n_requests, "point_steps": work}
+    torch.cuda.synchronize()
+    # plain FP32, one shot after another
+    t0 = time.perf_counter()
+    for r, vel, rec in made:
+        s = gw.WaveSolver(r["grid"], (10.0, 10.0, 10.0),
+                          0.5 * gw.wave_cfl_dt((10.0, 10.0, 10.0), float(vel.max())), vel)
+        tr = torch.empty((r["nsteps"], rec.shape[0]), device="cuda")
+        s.propagate((*r["source"], 15.0, -1.0, 1.0), r["nsteps"], rec, tr)
+        s.synchronize()
+        s.close()
+    out["plain_f32_sequential_gpts"] = work / (time.perf_counter() - t0) / 1e9
+    for name in ("f32", "f16"):
+        srv = gw.ShotServer(wl.SERVE_STREAM["budget_bytes"], 64)
+        trs = []
+        t0 = time.perf_counter()
+        for r, vel, rec in made:
+            tr = torch.empty((r["nsteps"], rec.shape[0]), device="cuda")
+            trs.append((srv.submit(r["grid"], (10.0, 10.0, 10.0), vel,
+                                   (*r["source"], 15.0, -1.0, 1.0), r["nsteps"], rec, tr,
+                                   storage=STORAGE[name]), tr))
+        ok = all(srv.wait(t)[0] == 0 for t, _ in trs)
+        el = time.perf_counter() - t0
+        srv.close()
+        out["served_%s_gpts" % name] = work / el / 1e9 if ok else None
+    out["served_f32_vs_plain_f32"] = out["served_f32_gpts"] / out["plain_f32_sequential_gpts"]
+    out["served_f16_vs_plain_f32"] = out["served_f16_gpts"] / out["plain_f32_sequential_gpts"]
+    return out
+
+
 def run_reference(args, cfg):
     """The reference arm: the FP64 CPU oracle on this machine's host cores."""
     rank, world, _ = dist_env()
@@ -473,6 +516,7 @@ def main():
     if not args.no_serve:
         serving = {name: serve_stream(gw, torch, STORAGE[name], args.serve_requests)
                    for name in ("f32", "f16")}
+        serving["saturated_mix"] = serve_saturated(gw, torch)
 
     cpu = None
     if rank == 0 and not args.no_cpu_baseline:

@@ -26,21 +26,28 @@ using ServeB16 = SweepCfg<64, 8, 1, 4, 4, __nv_bfloat16>;
 using ServeH16 = SweepCfg<64, 8, 1, 4, 4, __half>;
 constexpr int kKinds = 3;
 constexpr int kMaxGroup = 16;     // batch steps between two engine checks
-constexpr int kLayerPlanes = 128; // target z planes per CTA for batched shots
+constexpr int kLayerPlanes = 256; // target z planes per CTA for batched shots
 
 struct Kind {
   int tx, ty, hx, esize, threads;
   size_t smem;
   const void *func;
-  void (*launch)(int, cudaStream_t, const BatchShot *, int, long long);
+  void (*launch)(int, cudaStream_t, const BatchShot *, int, long long,
+                 const StencilCoefs &);
 };
 
 template <class C>
 void launch_batch(int ctas, cudaStream_t st, const BatchShot *table, int n,
-                  long long k) {
+                  long long k, const StencilCoefs &co) {
   wave_sweep_batched_kernel<C><<<ctas, C::THREADS, C::SMEM_BYTES, st>>>(
-      table, n, k);
+      table, n, k, co);
 }
+
+// Resident shots of one storage type and one grid spacing: one launch.
+struct Group {
+  int kind, first, count, ctas;
+  StencilCoefs co;
+};
 
 template <class C>
 Kind make_kind() {
@@ -120,7 +127,7 @@ struct serve_ctx {
   long long k = 0;  // batch steps taken
   BatchShot *d_table[kKinds] = {nullptr, nullptr, nullptr};
   std::vector<BatchShot> h_table[kKinds];
-  int table_ctas[kKinds] = {0, 0, 0};
+  std::vector<Group> groups;
   bool dirty = true;
   void *d_scan = nullptr;     // 16 bytes: velocity max, invalid count
   long long fault_alloc = -1; // host fault injection: fail this allocation
@@ -291,17 +298,18 @@ int admit(serve_ctx *s, Request *q) {
   const double ix = 1.0 / (r.spacing.dx * r.spacing.dx),
                iy = 1.0 / (r.spacing.dy * r.spacing.dy),
                iz = 1.0 / (r.spacing.dz * r.spacing.dz);
-  a.c0 = (float)(kW[0] * (ix + iy + iz));
+  a.k.c0 = (float)(kW[0] * (ix + iy + iz));
   for (int m = 1; m <= 4; ++m) {
-    a.cx[m - 1] = (float)(kW[m] * ix);
-    a.cy[m - 1] = (float)(kW[m] * iy);
-    a.cz[m - 1] = (float)(kW[m] * iz);
+    a.k.cx[m - 1] = (float)(kW[m] * ix);
+    a.k.cy[m - 1] = (float)(kW[m] * iy);
+    a.k.cz[m - 1] = (float)(kW[m] * iz);
   }
   a.desc = q->desc;
   a.cmax = (float)((double)vmax * vmax * dt * dt);
   b.buf[0] = q->buf[0];
   b.buf[1] = q->buf[1];
   b.b0 = s->k;
+  b.nsteps = r.nsteps;
   b.ntx = ntx;
   b.nty = nty;
   q->ctas = ntiles * (int)layers.size();
@@ -309,18 +317,31 @@ int admit(serve_ctx *s, Request *q) {
   return WAVE_OK;
 }
 
+// Order the resident shots by (storage, spacing), cut them into launch
+// groups and upload the batch tables.
 int upload_tables(serve_ctx *s) {
+  s->groups.clear();
   for (int kd = 0; kd < kKinds; ++kd) {
+    std::vector<Request *> shots;
+    for (Request *q : s->resident)
+      if (q->r.storage == kd) shots.push_back(q);
+    std::stable_sort(shots.begin(), shots.end(), [](Request *x, Request *y) {
+      return std::memcmp(&x->shot.args.k, &y->shot.args.k,
+                         sizeof(StencilCoefs)) < 0;
+    });
     auto &t = s->h_table[kd];
     t.clear();
-    int ctas = 0;
-    for (Request *q : s->resident) {
-      if (q->r.storage != kd) continue;
-      q->shot.cta_begin = ctas;
-      ctas += q->ctas;
+    for (Request *q : shots) {
+      const bool same = !s->groups.empty() && s->groups.back().kind == kd &&
+                        std::memcmp(&s->groups.back().co, &q->shot.args.k,
+                                    sizeof(StencilCoefs)) == 0;
+      if (!same) s->groups.push_back(Group{kd, (int)t.size(), 0, 0, q->shot.args.k});
+      Group &g = s->groups.back();
+      q->shot.cta_begin = g.ctas;
+      g.ctas += q->ctas;
+      g.count++;
       t.push_back(q->shot);
     }
-    s->table_ctas[kd] = ctas;
     if (!t.empty())
       WAVE_TRY_CUDA(cudaMemcpyAsync(s->d_table[kd], t.data(),
                                     t.size() * sizeof(BatchShot),
@@ -396,14 +417,17 @@ void engine_main(serve_ctx *s) {
     const double tb = s->now();
     int status = WAVE_OK;
     if (s->dirty) status = upload_tables(s);
-    int K = kMaxGroup;
+    // A fixed group of steps: a shot that finishes inside it is skipped by
+    // the remaining launches (its CTAs return at once) and completes at the
+    // group's end, so the engine synchronizes once per group.
+    int K = 1;
     for (Request *q : s->resident)
-      K = (int)std::min<int64_t>(K, q->r.nsteps - q->steps_done);
+      K = (int)std::max<int64_t>(K, std::min<int64_t>(kMaxGroup,
+                                                      q->r.nsteps - q->steps_done));
     for (int kk = 0; kk < K && status == WAVE_OK; ++kk)
-      for (int kd = 0; kd < kKinds; ++kd)
-        if (s->table_ctas[kd] > 0)
-          kind_of(kd).launch(s->table_ctas[kd], s->stream, s->d_table[kd],
-                             (int)s->h_table[kd].size(), s->k + kk);
+      for (const Group &g : s->groups)
+        kind_of(g.kind).launch(g.ctas, s->stream, s->d_table[g.kind] + g.first,
+                               g.count, s->k + kk, g.co);
     cudaError_t e = cudaGetLastError();
     if (e == cudaSuccess) e = cudaStreamSynchronize(s->stream);
     if (status == WAVE_OK && e != cudaSuccess) status = cuda_status(e);
@@ -413,8 +437,9 @@ void engine_main(serve_ctx *s) {
       s->st.batch_steps += K;
       s->st.busy_s += s->now() - tb;
       for (Request *q : s->resident) {
-        q->steps_done += K;
-        s->st.point_steps += q->points * K;
+        const int64_t did = std::min<int64_t>(K, q->r.nsteps - q->steps_done);
+        q->steps_done += did;
+        s->st.point_steps += q->points * did;
       }
     }
     // Completion (or failure of everything resident if the launch failed).

@@ -59,6 +59,12 @@ struct StepDesc {
 
 constexpr int kMaxLayers = 16;
 
+// Eq. 1 coefficients of one grid spacing.
+struct StencilCoefs {
+  float c0;                   // w0 * (1/dx^2 + 1/dy^2 + 1/dz^2)
+  float cx[4], cy[4], cz[4];  // w_m / h_a^2 for m = 1..4
+};
+
 struct SweepArgs {
   int nx, ny, nz, px;  // interior sizes; px = row pitch in elements (16 B rows)
   // z layers: CTAs with blockIdx.z == l stream planes [zl[l], zl[l+1]).
@@ -67,8 +73,7 @@ struct SweepArgs {
   int nlayers;
   int zl[kMaxLayers + 1];
   int ntx;             // tiles along x (tile id = by * ntx + bx)
-  float c0;            // w0 * (1/dx^2 + 1/dy^2 + 1/dz^2)
-  float cx[4], cy[4], cz[4];  // w_m / h_a^2 for m = 1..4
+  StencilCoefs k;      // coefficients (kernel parameters: constant operands)
   void *unext;         // output: the u_prev buffer, overwritten in place
   StepDesc *desc;
   int koff;            // step offset of this launch within a graph chunk
@@ -194,7 +199,9 @@ struct SweepCfg {
   static constexpr uint32_t U_BYTES = U_SLOT * sizeof(T);
   static constexpr uint32_t UP_BYTES = P_SLOT * sizeof(T);
   static constexpr uint32_t C_BYTES = P_SLOT * 4;
-  static constexpr size_t SMEM_BYTES = 128 + (size_t)SU * U_BYTES +
+  // Dynamic shared memory; 4 CTAs per SM fit while this stays within
+  // 228 KiB / 4 minus the 1 KiB the hardware reserves per CTA.
+  static constexpr size_t SMEM_BYTES = (size_t)SU * U_BYTES +
                                        (size_t)SP * (UP_BYTES + C_BYTES) +
                                        C_BYTES + NB * 8;
   static_assert(TX % 4 == 0 && TY % VY == 0, "tile shape");
@@ -216,17 +223,20 @@ __device__ __forceinline__ float exp2_int(int k) {
 //
 // sweep_cta is the work of one CTA: tile (bx, by) of the grid, z layer bz.
 // tm_u / tm_up / tm_c point to the tensor maps (kernel parameters or global
-// memory), smem_raw to the dynamic shared memory.
+// memory), co to the coefficients (kept in kernel parameter space, where the
+// arithmetic can use them as constant operands), smem_raw to the dynamic
+// shared memory.
 template <class C, bool kVelocityField>
 __device__ __forceinline__ void sweep_cta(const CUtensorMap *tm_u,
                                           const CUtensorMap *tm_up,
                                           const CUtensorMap *tm_c,
-                                          const SweepArgs &a, int bx, int by,
-                                          int bz, unsigned char *smem_raw) {
+                                          const SweepArgs &a,
+                                          const StencilCoefs &co, int bx,
+                                          int by, int bz,
+                                          unsigned char *smem_raw) {
   using T = typename C::T;
   using E = Elem<T>;
-  unsigned char *base = reinterpret_cast<unsigned char *>(
-      (reinterpret_cast<uintptr_t>(smem_raw) + 127) & ~uintptr_t(127));
+  unsigned char *base = smem_raw;  // 128-byte aligned (declaration below)
   T *su = reinterpret_cast<T *>(base);
   T *sp = reinterpret_cast<T *>(base + C::SU * C::U_BYTES);
   float *sc = reinterpret_cast<float *>(base + C::SU * C::U_BYTES +
@@ -368,8 +378,8 @@ __device__ __forceinline__ void sweep_cta(const CUtensorMap *tm_u,
         // Packed FP32x2 arithmetic: points (0,1) in `lo`, (2,3) in `hi`.
         // Lane-wise it is the same sequence of IEEE round-to-nearest
         // additions and fused multiply-adds as the scalar form.
-        float2 lo = __fmul2_rn(make_float2(a.c0, a.c0), make_float2(a1.x, a1.y));
-        float2 hi = __fmul2_rn(make_float2(a.c0, a.c0), make_float2(a1.z, a1.w));
+        float2 lo = __fmul2_rn(make_float2(co.c0, co.c0), make_float2(a1.x, a1.y));
+        float2 hi = __fmul2_rn(make_float2(co.c0, co.c0), make_float2(a1.z, a1.w));
         if constexpr (!C::kScaled) {
           const float4 a0 = E::load4(uc + r * C::UW + col - 4);
           const float4 a2 = E::load4(uc + r * C::UW + col + 4);
@@ -381,9 +391,9 @@ __device__ __forceinline__ void sweep_cta(const CUtensorMap *tm_u,
             const float4 yp = E::load4(uc + (r + m) * C::UW + col);
             const float4 zm = q[v][(p + 5 - m + 9) % 9];
             const float4 zp = q[v][(p + 5 + m) % 9];
-            const float2 cx2 = make_float2(a.cx[m - 1], a.cx[m - 1]);
-            const float2 cy2 = make_float2(a.cy[m - 1], a.cy[m - 1]);
-            const float2 cz2 = make_float2(a.cz[m - 1], a.cz[m - 1]);
+            const float2 cx2 = make_float2(co.cx[m - 1], co.cx[m - 1]);
+            const float2 cy2 = make_float2(co.cy[m - 1], co.cy[m - 1]);
+            const float2 cz2 = make_float2(co.cz[m - 1], co.cz[m - 1]);
             float2 xl, xh;
             if (m % 2 == 0) {  // operands are aligned register pairs
               xl = __fadd2_rn(make_float2(xs[4 - m], xs[5 - m]),
@@ -427,9 +437,9 @@ __device__ __forceinline__ void sweep_cta(const CUtensorMap *tm_u,
             const uint2 yp = E::load_raw(uc + (r + m) * C::UW + col);
             const float4 zm = q[v][(p + 5 - m + 9) % 9];
             const float4 zp = q[v][(p + 5 + m) % 9];
-            const float2 cx2 = make_float2(a.cx[m - 1], a.cx[m - 1]);
-            const float2 cy2 = make_float2(a.cy[m - 1], a.cy[m - 1]);
-            const float2 cz2 = make_float2(a.cz[m - 1], a.cz[m - 1]);
+            const float2 cx2 = make_float2(co.cx[m - 1], co.cx[m - 1]);
+            const float2 cy2 = make_float2(co.cy[m - 1], co.cy[m - 1]);
+            const float2 cz2 = make_float2(co.cz[m - 1], co.cz[m - 1]);
             const float2 xl = make_float2(xpair(4 - m, 4 + m), xpair(5 - m, 5 + m));
             const float2 xh = make_float2(xpair(6 - m, 6 + m), xpair(7 - m, 7 + m));
             const float2 yl = make_float2(E::add_to(ym, 0, E::unpack(yp, 0)),
@@ -552,9 +562,9 @@ __global__ void __launch_bounds__(C::THREADS, C::MINB)
                       const __grid_constant__ CUtensorMap tm_up,
                       const __grid_constant__ CUtensorMap tm_c,
                       const SweepArgs a) {
-  extern __shared__ unsigned char smem_raw[];
-  sweep_cta<C, kVelocityField>(&tm_u, &tm_up, &tm_c, a, blockIdx.x, blockIdx.y,
-                               blockIdx.z, smem_raw);
+  extern __shared__ __align__(128) unsigned char smem_raw[];
+  sweep_cta<C, kVelocityField>(&tm_u, &tm_up, &tm_c, a, a.k, blockIdx.x,
+                               blockIdx.y, blockIdx.z, smem_raw);
 }
 
 // One shot of a batch (device memory, 128-byte aligned): its tensor maps for
@@ -566,6 +576,7 @@ struct alignas(128) BatchShot {
   SweepArgs args;       // unext and koff are set per launch
   void *buf[2];         // buf[0] holds the shot's step 0
   long long b0;         // batch step at which the shot takes its step 0
+  int nsteps;           // the shot's step count: later batch steps skip it
   int cta_begin;        // first linear CTA index of this shot
   int ntx, nty;         // tiles; args.nlayers layers
 };
@@ -581,11 +592,13 @@ __device__ __forceinline__ void tensormap_acquire(const CUtensorMap *m) {
 // shots' CTA grids (shot i owns [cta_begin_i, cta_begin_{i+1})). Batch step k
 // is step k - b0 of each shot; each shot's buffers alternate from its own
 // step 0, so a shot computes exactly what the single-grid kernel computes.
+// All shots of one launch share the grid spacing, whose coefficients come as
+// a kernel parameter.
 template <class C>
 __global__ void __launch_bounds__(C::THREADS, C::MINB)
     wave_sweep_batched_kernel(const BatchShot *__restrict__ shots, int nshots,
-                              long long k) {
-  extern __shared__ unsigned char smem_raw[];
+                              long long k, const StencilCoefs co) {
+  extern __shared__ __align__(128) unsigned char smem_raw[];
   const int lin = blockIdx.x;
   int lo = 0, hi = nshots - 1;
   while (lo < hi) {
@@ -600,6 +613,7 @@ __global__ void __launch_bounds__(C::THREADS, C::MINB)
   const int by = rem / sh.ntx;
   const int bx = rem - by * sh.ntx;
   const long long n = k - sh.b0;  // the shot's own step
+  if (n >= sh.nsteps) return;     // finished inside this group of steps
   const int cur = (int)(n & 1);   // buffer holding the shot's u
   __shared__ SweepArgs a;         // uniform per CTA: read with broadcast loads
   if (threadIdx.x == 0) {
@@ -611,8 +625,8 @@ __global__ void __launch_bounds__(C::THREADS, C::MINB)
     tensormap_acquire(&sh.cmap);
   }
   __syncthreads();
-  sweep_cta<C, false>(&sh.halo[cur], &sh.tile[cur ^ 1], &sh.cmap, a, bx, by, bz,
-                      smem_raw);
+  sweep_cta<C, false>(&sh.halo[cur], &sh.tile[cur ^ 1], &sh.cmap, a, co, bx, by,
+                      bz, smem_raw);
 }
 
 }  // namespace gbw

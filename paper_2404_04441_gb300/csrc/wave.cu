@@ -170,11 +170,11 @@ void set_coeffs(wave_ctx *c) {
   a.cmax = (float)(c->vmax * c->vmax * c->dt * c->dt);
   const double ix = 1.0 / (c->dx * c->dx), iy = 1.0 / (c->dy * c->dy),
                iz = 1.0 / (c->dz * c->dz);
-  a.c0 = (float)(kW[0] * (ix + iy + iz));
+  a.k.c0 = (float)(kW[0] * (ix + iy + iz));
   for (int m = 1; m <= 4; ++m) {
-    a.cx[m - 1] = (float)(kW[m] * ix);
-    a.cy[m - 1] = (float)(kW[m] * iy);
-    a.cz[m - 1] = (float)(kW[m] * iz);
+    a.k.cx[m - 1] = (float)(kW[m] * ix);
+    a.k.cy[m - 1] = (float)(kW[m] * iy);
+    a.k.cz[m - 1] = (float)(kW[m] * iz);
   }
   a.desc = c->d_desc;
 }
@@ -959,11 +959,11 @@ extern "C" int wave_propagate_noalloc(const wave_grid *g, const wave_spacing *h,
   a.ntx = ntx;
   const double ix = 1.0 / (h->dx * h->dx), iy = 1.0 / (h->dy * h->dy),
                iz = 1.0 / (h->dz * h->dz);
-  a.c0 = (float)(kW[0] * (ix + iy + iz));
+  a.k.c0 = (float)(kW[0] * (ix + iy + iz));
   for (int m = 1; m <= 4; ++m) {
-    a.cx[m - 1] = (float)(kW[m] * ix);
-    a.cy[m - 1] = (float)(kW[m] * iy);
-    a.cz[m - 1] = (float)(kW[m] * iz);
+    a.k.cx[m - 1] = (float)(kW[m] * ix);
+    a.k.cy[m - 1] = (float)(kW[m] * iy);
+    a.k.cz[m - 1] = (float)(kW[m] * iz);
   }
   a.desc = reinterpret_cast<StepDesc *>(scr);
   a.dt2 = (float)(dt * dt);
