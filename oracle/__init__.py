@@ -41,6 +41,11 @@ def _load():
         lib.oracle_propagate.restype = ctypes.c_int
         lib.oracle_threads.argtypes = []
         lib.oracle_threads.restype = ctypes.c_int
+        lib.oracle_gradient.argtypes = (
+            [ctypes.c_int] * 3 + [ctypes.c_double] * 4 + [ctypes.c_void_p, ctypes.c_int]
+            + [ctypes.c_int] * 3 + [ctypes.c_double] * 3
+            + [ctypes.c_void_p, ctypes.c_int, ctypes.c_void_p, ctypes.c_void_p])
+        lib.oracle_gradient.restype = ctypes.c_int
         _lib = lib
     return _lib
 
@@ -123,6 +128,26 @@ def propagate(vel, spacing, dt, nsteps, u=None, u_prev=None, step0=0,
     if rc != 0:
         raise ValueError("oracle_propagate rejected its input (rc=%d)" % rc)
     return u, up, traces
+
+
+def gradient(vel, spacing, dt, nsteps, source, receivers, resid):
+    """Discrete adjoint gradient dJ/d(v^2) of a run from rest, given
+    resid[n, r] = dJ/d traces[n, r]. Returns (nz, ny, nx) FP64."""
+    vel = _f64(vel)
+    nz, ny, nx = vel.shape
+    rec = np.ascontiguousarray(receivers, dtype=np.int32).reshape(-1, 3)
+    res = _f64(resid).reshape(nsteps, rec.shape[0])
+    sx, sy, sz, f, t0, amp = source
+    if t0 is None or t0 < 0:
+        t0 = 1.0 / f
+    g = np.zeros_like(vel)
+    rc = _load().oracle_gradient(nx, ny, nz, *map(float, spacing), float(dt), vel.ctypes.data,
+                                 int(nsteps), int(sx), int(sy), int(sz), float(f), float(t0),
+                                 float(amp), rec.ctypes.data, rec.shape[0], res.ctypes.data,
+                                 g.ctypes.data)
+    if rc != 0:
+        raise ValueError("oracle_gradient rejected its input (rc=%d)" % rc)
+    return g
 
 
 def threads_used():

@@ -163,7 +163,13 @@ int oracle_propagate(int nx, int ny, int nz, double dx, double dy, double dz,
                      int sz, double f, double t0, double amp,
                      const double *wavelet, const int32_t *rec, int nrec,
                      double *traces, int periodic) {
-  if (nx < 1 || ny < 1 || nz < 1 || nsteps < 0) return -1;
+  if (nx < 1 || ny < 1 || nz < 1 || nsteps < 0 || nrec < 0) return -1;
+  if (has_source && (sx < 0 || sx >= nx || sy < 0 || sy >= ny || sz < 0 || sz >= nz))
+    return -1;
+  for (int r = 0; r < nrec; r++)
+    if (rec[3 * r] < 0 || rec[3 * r] >= nx || rec[3 * r + 1] < 0 ||
+        rec[3 * r + 1] >= ny || rec[3 * r + 2] < 0 || rec[3 * r + 2] >= nz)
+      return -1;
   size_t n = (size_t)nx * ny * nz;
   double *c = (double *)malloc(n * sizeof(double));
   double *unext = (double *)malloc(n * sizeof(double));
@@ -205,5 +211,80 @@ int oracle_propagate(int nx, int ny, int nz, double dx, double dy, double dz,
   }
   free(c);
   free(unext);
+  return 0;
+}
+
+/*
+ * Gradient of a receiver misfit with respect to the squared velocity m = v^2
+ * (the discrete adjoint of oracle_propagate from rest, zero halo).
+ *
+ * The forward recursion from u^0 = u^-1 = 0 is
+ *     u^{n+1} = 2 u^n - u^{n-1} + C (L u^n) + C_s w_n e_s,   C = m dt^2,
+ * the traces are d^n = R u^{n+1} (n = 0..N-1), and the caller passes
+ * resid[n][r] = dJ/dd^n_r (for J = 1/2 sum |d - d_obs|^2 this is d - d_obs).
+ * Setting the derivative of the Lagrangian with respect to each u^k to zero
+ * gives the adjoint recursion, run backwards from q^{N+1} = q^{N+2} = 0:
+ *     q^k = 2 q^{k+1} - q^{k+2} + L^T (C q^{k+1}) + R^T resid^{k-1},
+ * and the derivative with respect to m_i (through C and the source term)
+ *     g_i = (1/m_i) sum_{n=0}^{N-1} q^{n+1}_i (u^{n+1} - 2 u^n + u^{n-1})_i,
+ * the adjoint field correlated with the forward second time difference.
+ * L is symmetric with the zero halo (Eq. 1 is a symmetric star), so L^T = L.
+ * All forward fields are kept in memory: small grids only.
+ *
+ * Returns 0, or -1 on invalid input or allocation failure.
+ */
+int oracle_gradient(int nx, int ny, int nz, double dx, double dy, double dz,
+                    double dt, const double *vel, int nsteps, int sx, int sy,
+                    int sz, double f, double t0, double amp, const int32_t *rec,
+                    int nrec, const double *resid, double *grad) {
+  if (nx < 1 || ny < 1 || nz < 1 || nsteps < 1 || nrec < 0) return -1;
+  if (sx < 0 || sx >= nx || sy < 0 || sy >= ny || sz < 0 || sz >= nz) return -1;
+  for (int r = 0; r < nrec; r++)
+    if (rec[3 * r] < 0 || rec[3 * r] >= nx || rec[3 * r + 1] < 0 ||
+        rec[3 * r + 1] >= ny || rec[3 * r + 2] < 0 || rec[3 * r + 2] >= nz)
+      return -1;
+  const size_t n = (size_t)nx * ny * nz;
+  /* u[k] holds u^{k-1}, k = 0..nsteps+1 */
+  double *u = (double *)calloc(n * (size_t)(nsteps + 2), sizeof(double));
+  double *c = (double *)malloc(n * sizeof(double));
+  double *q0 = (double *)calloc(n, sizeof(double)); /* q^{k+2} */
+  double *q1 = (double *)calloc(n, sizeof(double)); /* q^{k+1} */
+  double *q2 = (double *)calloc(n, sizeof(double)); /* q^k */
+  double *cq = (double *)malloc(n * sizeof(double));
+  double *lap = (double *)malloc(n * sizeof(double));
+  if (!u || !c || !q0 || !q1 || !q2 || !cq || !lap) {
+    free(u); free(c); free(q0); free(q1); free(q2); free(cq); free(lap);
+    return -1;
+  }
+  for (size_t p = 0; p < n; p++) c[p] = vel[p] * vel[p] * dt * dt;
+  /* forward: u^{n+1} from u^n, u^{n-1}; keep every field */
+  for (int s = 0; s < nsteps; s++) {
+    const double *um = u + (size_t)s * n;       /* u^{s-1} */
+    const double *uc = u + (size_t)(s + 1) * n; /* u^s */
+    double *un = u + (size_t)(s + 2) * n;       /* u^{s+1} */
+    oracle_laplacian(nx, ny, nz, dx, dy, dz, uc, lap, 0);
+    for (size_t p = 0; p < n; p++) un[p] = 2.0 * uc[p] - um[p] + c[p] * lap[p];
+    size_t ps = ((size_t)sz * ny + sy) * nx + sx;
+    un[ps] += c[ps] * oracle_ricker(s * dt, f, t0, amp);
+  }
+  for (size_t p = 0; p < n; p++) grad[p] = 0.0;
+  /* adjoint: q^k for k = N .. 1 */
+  for (int k = nsteps; k >= 1; k--) {
+    for (size_t p = 0; p < n; p++) cq[p] = c[p] * q1[p];
+    oracle_laplacian(nx, ny, nz, dx, dy, dz, cq, lap, 0);
+    for (size_t p = 0; p < n; p++) q2[p] = 2.0 * q1[p] - q0[p] + lap[p];
+    for (int r = 0; r < nrec; r++) {
+      size_t pr = ((size_t)rec[3 * r + 2] * ny + rec[3 * r + 1]) * nx + rec[3 * r];
+      q2[pr] += resid[(size_t)(k - 1) * nrec + r];
+    }
+    /* term n = k - 1: q^k (u^k - 2 u^{k-1} + u^{k-2}) */
+    const double *a = u + (size_t)(k + 1) * n, *b = u + (size_t)k * n,
+                 *d = u + (size_t)(k - 1) * n;
+    for (size_t p = 0; p < n; p++)
+      grad[p] += q2[p] * (a[p] - 2.0 * b[p] + d[p]);
+    double *t = q0; q0 = q1; q1 = q2; q2 = t;
+  }
+  for (size_t p = 0; p < n; p++) grad[p] /= vel[p] * vel[p];
+  free(u); free(c); free(q0); free(q1); free(q2); free(cq); free(lap);
   return 0;
 }

@@ -339,3 +339,76 @@ def test_zero_halo_matches_embedding(oracle_mod):
     lap = oracle_mod.laplacian(u, sp)
     lap_big = oracle_mod.laplacian(big, sp, periodic=True)
     np.testing.assert_allclose(lap, lap_big[R:-R, R:-R, R:-R], rtol=1e-14, atol=1e-14)
+
+
+def _misfit(oracle_mod, vel, sp, dt, nsteps, shot, rec, obs):
+    _, _, tr = oracle_mod.propagate(vel, sp, dt, nsteps, source=shot, receivers=rec)
+    return 0.5 * float(np.sum((tr - obs) ** 2)), tr
+
+
+def _gradient_case(n=9, nsteps=30, seed=1):
+    rng = np.random.default_rng(seed)
+    sp = (10.0, 11.0, 9.0)
+    vel = rng.uniform(1800.0, 3200.0, size=(n, n + 1, n + 2))
+    true = vel * (1.0 + 0.05 * rng.standard_normal(vel.shape))
+    shot = (3, 4, 2, 25.0, 0.03, 1e3)
+    rec = np.array([[1, 1, 1], [n - 2, n - 3, n - 4], [5, n - 1, n - 3], [n + 1, 2, 3],
+                    [n - 2, n - 3, n - 4]], dtype=np.int32)  # (x, y, z); one repeated
+    return sp, vel, true, shot, rec
+
+
+def test_adjoint_gradient_matches_finite_differences(oracle_mod):
+    """The oracle gradient against central differences of the oracle misfit
+    (FP64, step 1e-5 relative: truncation ~1e-10, rounding ~1e-9)."""
+    sp, vel, true, shot, rec = _gradient_case()
+    dt = 0.5 * oracle_mod.cfl_dt(sp, max(vel.max(), true.max()) * 1.01)
+    nsteps = 30
+    _, _, obs = oracle_mod.propagate(true, sp, dt, nsteps, source=shot, receivers=rec)
+    _, tr = _misfit(oracle_mod, vel, sp, dt, nsteps, shot, rec, obs)
+    g = oracle_mod.gradient(vel, sp, dt, nsteps, shot, rec, tr - obs)
+    m = vel ** 2
+    rng = np.random.default_rng(2)
+    pts = [(2, 4, 3), (4, 6, 7), (0, 0, 0), (8, 9, 10)] + [
+        tuple(int(rng.integers(s)) for s in m.shape) for _ in range(4)]
+    for idx in pts:
+        h = 1e-5 * m[idx]
+        mp, mm = m.copy(), m.copy()
+        mp[idx] += h
+        mm[idx] -= h
+        jp, _ = _misfit(oracle_mod, np.sqrt(mp), sp, dt, nsteps, shot, rec, obs)
+        jm, _ = _misfit(oracle_mod, np.sqrt(mm), sp, dt, nsteps, shot, rec, obs)
+        fd = (jp - jm) / (2 * h)
+        assert fd == pytest.approx(g[idx], rel=2e-5, abs=1e-6 * np.max(np.abs(g))), idx
+    # and along a smooth direction through the whole model
+    z, y, x = np.meshgrid(*[np.arange(s) for s in m.shape], indexing="ij")
+    dm = np.exp(-((x - 5.0) ** 2 + (y - 5.0) ** 2 + (z - 4.0) ** 2) / 8.0) * m
+    eps = 1e-6
+    jp, _ = _misfit(oracle_mod, np.sqrt(m + eps * dm), sp, dt, nsteps, shot, rec, obs)
+    jm, _ = _misfit(oracle_mod, np.sqrt(m - eps * dm), sp, dt, nsteps, shot, rec, obs)
+    assert (jp - jm) / (2 * eps) == pytest.approx(float(np.sum(g * dm)), rel=1e-6)
+
+
+def test_oracle_rejects_points_outside_the_grid(oracle_mod):
+    vel = np.full((5, 6, 7), 2000.0)
+    dt = 0.5 * oracle_mod.cfl_dt((10.0,) * 3, 2000.0)
+    with pytest.raises(ValueError):
+        oracle_mod.propagate(vel, (10.0,) * 3, dt, 2, receivers=np.array([[7, 0, 0]]))
+    with pytest.raises(ValueError):
+        oracle_mod.propagate(vel, (10.0,) * 3, dt, 2, source=(0, 6, 0, 15.0, -1.0, 1.0))
+    with pytest.raises(ValueError):
+        oracle_mod.gradient(vel, (10.0,) * 3, dt, 2, (0, 0, 5, 15.0, -1.0, 1.0),
+                            np.array([[0, 0, 0]]), np.zeros((2, 1)))
+
+
+def test_adjoint_gradient_linear_in_residual_and_zero_without_it(oracle_mod):
+    sp, vel, _, shot, rec = _gradient_case(n=7, nsteps=12)
+    dt = 0.5 * oracle_mod.cfl_dt(sp, vel.max())
+    rng = np.random.default_rng(9)
+    r1 = rng.standard_normal((12, rec.shape[0]))
+    r2 = rng.standard_normal((12, rec.shape[0]))
+    g1 = oracle_mod.gradient(vel, sp, dt, 12, shot, rec, r1)
+    g2 = oracle_mod.gradient(vel, sp, dt, 12, shot, rec, r2)
+    g12 = oracle_mod.gradient(vel, sp, dt, 12, shot, rec, 2.0 * r1 - 3.0 * r2)
+    np.testing.assert_allclose(g12, 2.0 * g1 - 3.0 * g2, rtol=1e-12, atol=1e-12 * np.abs(g1).max())
+    g0 = oracle_mod.gradient(vel, sp, dt, 12, shot, rec, np.zeros_like(r1))
+    assert np.all(g0 == 0.0)
