@@ -298,6 +298,48 @@ def serve_saturated(gw, torch, n_requests=48):
     return out
 
 
+def gradient_workload(gw, torch, cfg=wl.CFG_GRAD):
+    """L2 trace misfit gradient d/d(v^2): true model = layers + Gaussian
+    300 m/s anomaly, start = smoothed truth, 256^3, 800 steps, checkpoint
+    every 40 steps. Observed traces come from a forward run of the true model
+    (not timed); the timed region is one wave_gradient call (forward with
+    checkpoints, residual and FP64 misfit, segment recomputes, adjoint,
+    FP64 time sums)."""
+    nx, ny, nz = cfg["shape"]
+    true = wl.anomaly_model(nx, ny, nz, seed=cfg["seed"], anomaly=cfg["anomaly_mps"])
+    start = wl.smoothed_start(true)
+    rec = torch.from_numpy(wl.receiver_plane(nx, ny, cfg["rec_z"], cfg["rec_stride"])).cuda()
+    shot = (nx // 2, ny // 2, 10, cfg["f_peak"], -1.0, 1.0)
+    n = cfg["nsteps"]
+    dt = 0.5 * gw.wave_cfl_dt(cfg["spacing"], max(float(true.max()), float(start.max())))
+    obs = torch.zeros((n, rec.shape[0]), device="cuda")
+    st = gw.WaveSolver((nx, ny, nz), cfg["spacing"], dt, torch.from_numpy(true).cuda())
+    st.propagate(shot, n, rec, obs)
+    st.close()
+    s = gw.WaveSolver((nx, ny, nz), cfg["spacing"], dt, torch.from_numpy(start).cuda())
+    g = torch.empty((nz, ny, nx), device="cuda")
+    # forward alone, for the cost ratio
+    tr = torch.empty_like(obs)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    s.propagate(shot, n, rec, tr)
+    s.synchronize()
+    t_fwd = time.perf_counter() - t0
+    s.reset()
+    t0 = time.perf_counter()
+    misfit = s.gradient(shot, n, rec, obs, g, ckpt_every=cfg["ckpt_every"])
+    t_grad = time.perf_counter() - t0
+    s.close()
+    pts = nx * ny * nz * n
+    return {"workload": "%s, %d steps, checkpoint every %d" % (cfg["name"], n, cfg["ckpt_every"]),
+            "seconds": t_grad, "forward_seconds": t_fwd, "cost_vs_forward": t_grad / t_fwd,
+            "gpts_model_steps": pts / t_grad / 1e9, "misfit": misfit,
+            "grad_finite": bool(torch.isfinite(g).all().item()),
+            "grad_max_abs": float(g.abs().max().item()),
+            "device_memory_fields": 2 * ((n + cfg["ckpt_every"] - 1) // cfg["ckpt_every"])
+            + cfg["ckpt_every"] + 3}
+
+
 def run_reference(args, cfg):
     """The reference arm: the FP64 CPU oracle on this machine's host cores."""
     rank, world, _ = dist_env()
@@ -363,6 +405,8 @@ def main():
     ap.add_argument("--no-serve", action="store_true",
                     help="skip the shot-serving stream")
     ap.add_argument("--serve-requests", type=int, default=wl.SERVE_STREAM["n"])
+    ap.add_argument("--no-gradient", action="store_true",
+                    help="skip the adjoint-gradient workload")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
     cfg = WORKLOADS[args.workload]
@@ -518,6 +562,10 @@ def main():
                    for name in ("f32", "f16")}
         serving["saturated_mix"] = serve_saturated(gw, torch)
 
+    gradient = None
+    if not args.no_gradient:
+        gradient = gradient_workload(gw, torch)
+
     cpu = None
     if rank == 0 and not args.no_cpu_baseline:
         g, cores, sample, el = oracle_sample(vel, cfg, dt, budget_s=15.0)
@@ -540,7 +588,7 @@ def main():
                        "launch": info},
             "e2e": e2e, "gpu_launches": launches, "roofline": roofline,
             "cpu_baseline": cpu, "clocks": clocks, "traces_finite": tr_ok,
-            "precision_forms": precision, "serving": serving,
+            "precision_forms": precision, "serving": serving, "gradient": gradient,
         }
         print(json.dumps(line), flush=True)
     if world > 1:

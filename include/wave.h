@@ -183,6 +183,45 @@ int wave_get_launch_info(const wave_ctx *ctx, int *tile_x, int *tile_y,
 int wave_selftest_wait(int64_t limit_ns, void *stream);
 
 /*
+ * Gradient of a trace objective with respect to m = v^2 at every point: the
+ * discrete adjoint of wave_propagate from rest (u = u_prev = 0, step 0).
+ *
+ * With the forward recursion u^{n+1} = 2u^n - u^{n-1} + C L u^n + C_s w_n
+ * (C = m dt^2, Eq. 1 for L) and traces d^n = R u^{n+1}, the adjoint field
+ * q^k = 2q^{k+1} - q^{k+2} + L(C q^{k+1}) + R^T r^{k-1} runs backwards from
+ * zero, r^n = dJ/dd^n, and dJ/dm = (1/m) sum_n q^{n+1} (u^{n+1} - 2u^n +
+ * u^{n-1}): the back-propagated residual correlated with the forward second
+ * time difference. The library runs p = C q, which obeys the forward update
+ * with the residuals injected at the receivers, on the same sweep kernel;
+ * the forward fields come from checkpoints every ckpt_every steps, one
+ * segment recomputed at a time; the time sum is accumulated in FP64.
+ *
+ *   shot         Ricker source of the forward run (NULL: none)
+ *   rec_xyz      nrec*3 int32 receivers (host or device), as wave_propagate
+ *   resid        nsteps*nrec float32 dJ/dtraces (host or device)
+ *   ckpt_every   steps per checkpoint segment (>= 1); device memory holds
+ *                2 * ceil(nsteps/ckpt_every) + ckpt_every + 3 fields
+ *   grad_v2      nx*ny*nz float32 output (host or device), dense, x fastest
+ *   traces       optional nsteps*nrec float32 output of the forward traces
+ * FP32 storage and the default kernel variant only (else WAVE_ENOTSUP). The
+ * call synchronizes; it leaves the context reset (zero fields, step 0).
+ */
+int wave_adjoint(wave_ctx *ctx, const wave_shot *shot, int nsteps,
+                 const int32_t *rec_xyz, int nrec, const float *resid,
+                 int ckpt_every, float *grad_v2, float *traces);
+
+/*
+ * The L2 trace misfit J = 1/2 sum_{n,r} (d^n_r - observed^n_r)^2 of a run
+ * from rest and its gradient dJ/d(v^2) (wave_adjoint with resid = d -
+ * observed). The residual and the misfit sum are formed on the GPU, the sum
+ * in FP64. observed: nsteps*nrec float32, host or device; misfit: host.
+ */
+int wave_gradient(wave_ctx *ctx, const wave_shot *shot, int nsteps,
+                  const int32_t *rec_xyz, int nrec, const float *observed,
+                  int ckpt_every, double *misfit, float *grad_v2,
+                  float *traces);
+
+/*
  * Allocation-free propagation. The paper has no counterpart to this entry
  * point; it exists for callers that must not allocate device memory: code
  * running inside an application whose memory pool already owns the whole

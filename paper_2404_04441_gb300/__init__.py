@@ -17,7 +17,7 @@ __all__ = [
     "wave_get_field", "wave_set_state", "wave_get_step", "wave_reset",
     "wave_synchronize", "wave_destroy", "wave_strerror", "wave_get_launch_info",
     "wave_selftest_wait", "wave_propagate_noalloc", "WaveSolver", "library_path",
-    "ShotServer",
+    "ShotServer", "wave_adjoint", "wave_gradient", "WaveTraces", "wave_traces",
 ]
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
@@ -106,6 +106,11 @@ def load(path=None):
     lib.wave_strerror.restype = ctypes.c_char_p
     lib.wave_get_launch_info.argtypes = [vp] + [ctypes.POINTER(ctypes.c_int)] * 5
     lib.wave_selftest_wait.argtypes = [ctypes.c_int64, vp]
+    lib.wave_adjoint.argtypes = [vp, ctypes.POINTER(_Shot), ip, vp, ip, vp, ip, vp, vp]
+    lib.wave_gradient.argtypes = [vp, ctypes.POINTER(_Shot), ip, vp, ip, vp, ip,
+                                  ctypes.POINTER(ctypes.c_double), vp, vp]
+    lib.wave_adjoint.restype = ctypes.c_int
+    lib.wave_gradient.restype = ctypes.c_int
     lib.serve_create.argtypes = [ctypes.c_size_t, ip, vp, ctypes.POINTER(vp)]
     lib.serve_submit.argtypes = [vp, ctypes.POINTER(_Request), ctypes.POINTER(ctypes.c_int64)]
     lib.serve_poll.argtypes = [vp, ctypes.c_int64, ctypes.POINTER(_Result)]
@@ -270,6 +275,38 @@ def wave_propagate_noalloc(grid, spacing, dt, velocity, u, u_prev, shot, step0, 
     return newest.value
 
 
+def _shot_ref(shot):
+    if shot is None:
+        return None
+    sx, sy, sz, f, t0, amp = shot
+    return ctypes.byref(_Shot(int(sx), int(sy), int(sz), float(f),
+                              -1.0 if t0 is None else float(t0), float(amp)))
+
+
+def wave_adjoint(ctx, shot, nsteps, rec, resid, ckpt_every, grad, count, traces=None):
+    """dJ/d(v^2) of a run from rest given resid = dJ/dtraces (nsteps, nrec)."""
+    nrec = 0 if rec is None else int(rec.shape[0])
+    _check(load().wave_adjoint(
+        ctx, _shot_ref(shot), int(nsteps), _ptr(rec, "int32", 3 * nrec, "rec") if nrec else None,
+        nrec, _ptr(resid, "float32", int(nsteps) * nrec, "resid") if nrec else None,
+        int(ckpt_every), _ptr(grad, "float32", count, "grad"),
+        _ptr(traces, "float32", int(nsteps) * nrec, "traces") if traces is not None else None),
+        "wave_adjoint")
+
+
+def wave_gradient(ctx, shot, nsteps, rec, observed, ckpt_every, grad, count, traces=None):
+    """L2 trace misfit of a run from rest and its gradient dJ/d(v^2); returns the misfit."""
+    nrec = 0 if rec is None else int(rec.shape[0])
+    mis = ctypes.c_double(0.0)
+    _check(load().wave_gradient(
+        ctx, _shot_ref(shot), int(nsteps), _ptr(rec, "int32", 3 * nrec, "rec") if nrec else None,
+        nrec, _ptr(observed, "float32", int(nsteps) * nrec, "observed") if nrec else None,
+        int(ckpt_every), ctypes.byref(mis), _ptr(grad, "float32", count, "grad"),
+        _ptr(traces, "float32", int(nsteps) * nrec, "traces") if traces is not None else None),
+        "wave_gradient")
+    return mis.value
+
+
 def wave_selftest_wait(limit_ns, stream=None):
     """Run the bounded-wait self-test; returns the library status (WAVE_ETIMEOUT expected)."""
     st = _default_stream() if stream is None else int(stream)
@@ -323,6 +360,14 @@ class WaveSolver:
 
     def launch_info(self):
         return wave_get_launch_info(self.ctx)
+
+    def adjoint(self, shot, nsteps, rec, resid, grad, ckpt_every=40, traces=None):
+        wave_adjoint(self.ctx, shot, nsteps, rec, resid, ckpt_every, grad, self.count, traces)
+        return grad
+
+    def gradient(self, shot, nsteps, rec, observed, grad, ckpt_every=40, traces=None):
+        return wave_gradient(self.ctx, shot, nsteps, rec, observed, ckpt_every, grad,
+                             self.count, traces)
 
     def close(self):
         if getattr(self, "ctx", None):
@@ -413,3 +458,54 @@ class ShotServer:
             self.close()
         except Exception:
             pass
+
+
+def _make_traces_function():
+    import torch
+
+    class WaveTraces(torch.autograd.Function):
+        """Receiver traces of a run from rest as a differentiable function of
+        the squared velocity m = v^2 (a CUDA tensor of shape (nz, ny, nx)).
+
+        forward: the 25-point leapfrog with the given source and receivers
+        (wave_propagate). backward: the discrete adjoint (wave_adjoint) with
+        the incoming gradient as dJ/dtraces, checkpointing every ``ckpt_every``
+        steps. dt stays fixed, so the map m -> traces is a fixed discrete
+        function; the model used is v = sqrt(m) rounded to FP32.
+        """
+
+        @staticmethod
+        def forward(fctx, m, spacing, dt, shot, nsteps, rec, ckpt_every=40):
+            nz, ny, nx = m.shape
+            vel = torch.sqrt(m.detach()).to(torch.float32).contiguous()
+            solver = WaveSolver((nx, ny, nz), spacing, dt, vel)
+            traces = torch.zeros((nsteps, rec.shape[0]), dtype=torch.float32, device=m.device)
+            solver.propagate(shot, nsteps, rec, traces)
+            solver.synchronize()
+            fctx.solver = solver
+            fctx.args = (shot, int(nsteps), rec, int(ckpt_every))
+            return traces
+
+        @staticmethod
+        def backward(fctx, grad_traces):
+            shot, nsteps, rec, ckpt = fctx.args
+            solver = fctx.solver
+            grad = torch.empty((solver.grid[2], solver.grid[1], solver.grid[0]),
+                               dtype=torch.float32, device=grad_traces.device)
+            solver.adjoint(shot, nsteps, rec, grad_traces.to(torch.float32).contiguous(), grad,
+                           ckpt_every=ckpt)
+            solver.close()
+            return grad, None, None, None, None, None, None
+
+    return WaveTraces
+
+
+def wave_traces(m, spacing, dt, shot, nsteps, rec, ckpt_every=40):
+    """Differentiable traces(m = v^2); see WaveTraces."""
+    return _make_traces_function().apply(m, spacing, dt, shot, nsteps, rec, ckpt_every)
+
+
+def __getattr__(name):
+    if name == "WaveTraces":
+        return _make_traces_function()
+    raise AttributeError(name)

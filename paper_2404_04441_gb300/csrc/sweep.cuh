@@ -50,6 +50,13 @@ struct StepDesc {
   int nrec;
   int src_active;
   int sx, sy, sz;
+  // Point injection (adjoint sources): row n of inj_val holds the values of
+  // step n; entry {z, local, id, tile} adds v^2 dt^2 * inj_val[n][id] at its
+  // point; entries sorted by (tile, z) with per-tile starts like receivers.
+  const float *inj_val;
+  const int4 *inj;
+  const int *inj_start;
+  int ninj;
   int error;              // first error recorded by a kernel (0 = none)
   // 16-bit storage only: the field holding absolute step k has scale
   // 2^exps[k & 3] and largest magnitude maxbits[k & 3] (bits of a float).
@@ -58,6 +65,11 @@ struct StepDesc {
 };
 
 constexpr int kMaxLayers = 16;
+
+// Extra work of a sweep (template bit mask), used by the adjoint gradient:
+constexpr int kModeStoreD = 1;   // write D = v^2 dt^2 (L u) + source to a.dout
+constexpr int kModeInject = 2;   // add the StepDesc's point injections
+constexpr int kModeGradAcc = 4;  // a.gacc += u * a.dsrc (FP64), per point
 
 // Eq. 1 coefficients of one grid spacing.
 struct StencilCoefs {
@@ -79,6 +91,9 @@ struct SweepArgs {
   int koff;            // step offset of this launch within a graph chunk
   float dt2;           // dt^2, used only when the c field holds velocities
   float cmax;          // largest v^2 dt^2 (16-bit storage: growth bound)
+  float *dout;         // kModeStoreD: D of this step (field layout)
+  const float *dsrc;   // kModeGradAcc: D paired with this step's u
+  double *gacc;        // kModeGradAcc: FP64 sum of u * D (field layout)
 };
 
 // Element access per storage type: 4 consecutive elements to/from float4.
@@ -226,7 +241,7 @@ __device__ __forceinline__ float exp2_int(int k) {
 // memory), co to the coefficients (kept in kernel parameter space, where the
 // arithmetic can use them as constant operands), smem_raw to the dynamic
 // shared memory.
-template <class C, bool kVelocityField>
+template <class C, bool kVelocityField, int kMode>
 __device__ __forceinline__ void sweep_cta(const CUtensorMap *tm_u,
                                           const CUtensorMap *tm_up,
                                           const CUtensorMap *tm_c,
@@ -271,6 +286,20 @@ __device__ __forceinline__ void sweep_cta(const CUtensorMap *tm_u,
   }
   int rz = (rcur < rend) ? rec[rcur].x : 0x7fffffff;  // z of the next receiver
   float *trow = (nrec > 0) ? d->traces + (size_t)n * nrec : nullptr;
+  int icur = 0, iend = 0, iz = 0x7fffffff;  // injections (kModeInject)
+  const int4 *inj = nullptr;
+  const float *irow = nullptr;
+  if constexpr ((kMode & kModeInject) != 0) {
+    if (d->ninj > 0) {
+      const int tile = by * a.ntx + bx;
+      inj = d->inj;
+      irow = d->inj_val + (size_t)n * d->ninj;
+      icur = d->inj_start[tile];
+      iend = d->inj_start[tile + 1];
+      while (icur < iend && inj[icur].x < zb) ++icur;
+      if (icur < iend) iz = inj[icur].x;
+    }
+  }
 
   // 16-bit storage: scales of the input fields (absolute steps ab and ab-1)
   // and of the output field (step ab+1). The output scale bounds the new
@@ -370,6 +399,7 @@ __device__ __forceinline__ void sweep_cta(const CUtensorMap *tm_u,
       const T *pp = sp + (s % C::SP) * C::P_SLOT;
       const float *pc = sc + (s % C::SP) * C::P_SLOT;
       float4 res[C::VY];
+      float4 dres[C::VY];  // kModeStoreD: c (L u) + source
 #pragma unroll
       for (int v = 0; v < C::VY; ++v) {
         const int r = ty * C::VY + v + kR;  // smem row of this point row
@@ -483,24 +513,80 @@ __device__ __forceinline__ void sweep_cta(const CUtensorMap *tm_u,
           oh = __ffma2_rn(cvh, hi, __ffma2_rn(two, uh, ph));
         }
         float4 o = make_float4(ol.x, ol.y, oh.x, oh.y);
+        float4 dv = make_float4(0.f, 0.f, 0.f, 0.f);
+        if constexpr ((kMode & kModeStoreD) != 0) {
+          const float2 dl = __fmul2_rn(cvl, lo), dh = __fmul2_rn(cvh, hi);
+          dv = make_float4(dl.x, dl.y, dh.x, dh.y);
+        }
         if (src_here && j == sz && sy == ty * C::VY + v) {
           const int e = sx - 4 * tx;
           if (e == 0) o.x = fmaf(cv.x, wsrc, o.x);
           if (e == 1) o.y = fmaf(cv.y, wsrc, o.y);
           if (e == 2) o.z = fmaf(cv.z, wsrc, o.z);
           if (e == 3) o.w = fmaf(cv.w, wsrc, o.w);
+          if constexpr ((kMode & kModeStoreD) != 0) {
+            if (e == 0) dv.x = fmaf(cv.x, wsrc, dv.x);
+            if (e == 1) dv.y = fmaf(cv.y, wsrc, dv.y);
+            if (e == 2) dv.z = fmaf(cv.z, wsrc, dv.z);
+            if (e == 3) dv.w = fmaf(cv.w, wsrc, dv.w);
+          }
         }
         if constexpr (C::kScaled) {
           vmax_out = fmaxf(vmax_out, fmaxf(fmaxf(fabsf(o.x), fabsf(o.y)),
                                            fmaxf(fabsf(o.z), fabsf(o.w))));
         }
         res[v] = o;
+        dres[v] = dv;
+      }
+
+      // Point injections on this plane (adjoint sources): stage the plane,
+      // add v^2 dt^2 * value per entry (repeated points add up), read back.
+      if constexpr ((kMode & kModeInject) != 0) {
+        if (j == iz) {
+#pragma unroll
+          for (int v = 0; v < C::VY; ++v)
+            *reinterpret_cast<float4 *>(sr + (ty * C::VY + v) * C::TX + 4 * tx) =
+                res[v];
+          __syncthreads();
+          int last = icur;
+          while (last < iend && inj[last].x == j) ++last;
+          for (int e = icur + tid; e < last; e += C::THREADS) {
+            const int4 r4 = inj[e];
+            atomicAdd(&sr[r4.y], pc[r4.y] * irow[r4.z]);
+          }
+          __syncthreads();
+#pragma unroll
+          for (int v = 0; v < C::VY; ++v)
+            res[v] = *reinterpret_cast<const float4 *>(
+                sr + (ty * C::VY + v) * C::TX + 4 * tx);
+          __syncthreads();  // the staging plane is free again
+          icur = last;
+          iz = (icur < iend) ? inj[icur].x : 0x7fffffff;
+        }
+      }
+#pragma unroll
+      for (int v = 0; v < C::VY; ++v) {
         const int y = y0 + ty * C::VY + v;
         const int x = x0 + 4 * tx;
-        if (y < a.ny && x < a.px)
-          E::store4_cs(reinterpret_cast<T *>(a.unext) +
-                           ((size_t)j * a.ny + y) * a.px + x,
-                       o);
+        if (y < a.ny && x < a.px) {
+          const size_t idx = ((size_t)j * a.ny + y) * a.px + x;
+          E::store4_cs(reinterpret_cast<T *>(a.unext) + idx, res[v]);
+          if constexpr ((kMode & kModeStoreD) != 0)
+            __stcs(reinterpret_cast<float4 *>(a.dout + idx), dres[v]);
+          if constexpr ((kMode & kModeGradAcc) != 0) {
+            // FP64 time sum of this step's u (centre of the queue) times D.
+            const float4 uc4 = q[v][(p + 5) % 9];
+            const float4 d4 = __ldcs(reinterpret_cast<const float4 *>(a.dsrc + idx));
+            double2 *g = reinterpret_cast<double2 *>(a.gacc + idx);
+            double2 g0 = g[0], g1 = g[1];
+            g0.x = fma((double)uc4.x, (double)d4.x, g0.x);
+            g0.y = fma((double)uc4.y, (double)d4.y, g0.y);
+            g1.x = fma((double)uc4.z, (double)d4.z, g1.x);
+            g1.y = fma((double)uc4.w, (double)d4.w, g1.y);
+            g[0] = g0;
+            g[1] = g1;
+          }
+        }
       }
 
       // Receivers on this plane: stage the plane, then one thread per entry.
@@ -556,15 +642,15 @@ wait_failed:
 }
 
 // One step of one grid: CTA (blockIdx.x, .y) is a tile, blockIdx.z a z layer.
-template <class C, bool kVelocityField = false>
+template <class C, bool kVelocityField = false, int kMode = 0>
 __global__ void __launch_bounds__(C::THREADS, C::MINB)
     wave_sweep_kernel(const __grid_constant__ CUtensorMap tm_u,
                       const __grid_constant__ CUtensorMap tm_up,
                       const __grid_constant__ CUtensorMap tm_c,
                       const SweepArgs a) {
   extern __shared__ __align__(128) unsigned char smem_raw[];
-  sweep_cta<C, kVelocityField>(&tm_u, &tm_up, &tm_c, a, a.k, blockIdx.x,
-                               blockIdx.y, blockIdx.z, smem_raw);
+  sweep_cta<C, kVelocityField, kMode>(&tm_u, &tm_up, &tm_c, a, a.k, blockIdx.x,
+                                      blockIdx.y, blockIdx.z, smem_raw);
 }
 
 // One shot of a batch (device memory, 128-byte aligned): its tensor maps for
@@ -625,8 +711,8 @@ __global__ void __launch_bounds__(C::THREADS, C::MINB)
     tensormap_acquire(&sh.cmap);
   }
   __syncthreads();
-  sweep_cta<C, false>(&sh.halo[cur], &sh.tile[cur ^ 1], &sh.cmap, a, co, bx, by,
-                      bz, smem_raw);
+  sweep_cta<C, false, 0>(&sh.halo[cur], &sh.tile[cur ^ 1], &sh.cmap, a, co, bx,
+                         by, bz, smem_raw);
 }
 
 }  // namespace gbw

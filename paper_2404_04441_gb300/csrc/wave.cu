@@ -733,6 +733,263 @@ int wave_selftest_wait(int64_t limit_ns, void *stream) {
 }  // extern "C"
 
 // ---------------------------------------------------------------------------
+// Adjoint gradient (wave_adjoint, wave_gradient).
+namespace {
+
+template <int kMode>
+void launch_mode(const wave_ctx *c, const CUtensorMap &tu,
+                 const CUtensorMap &tup, const SweepArgs &a) {
+  wave_sweep_kernel<Cfg0, false, kMode>
+      <<<c->grid, Cfg0::THREADS, Cfg0::SMEM_BYTES, c->stream>>>(tu, tup,
+                                                                 c->tm_c, a);
+}
+
+// r = traces - observed; misfit += 1/2 sum r^2 in FP64.
+__global__ void residual_kernel(const float *tr, const float *obs, float *r,
+                                long long n, double *misfit) {
+  double local = 0.0;
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
+       i += (long long)gridDim.x * blockDim.x) {
+    const float d = tr[i] - obs[i];
+    r[i] = d;
+    local += (double)d * (double)d;
+  }
+  for (int o = 16; o > 0; o >>= 1)
+    local += __shfl_xor_sync(0xffffffffu, local, o);
+  if ((threadIdx.x & 31) == 0 && local != 0.0) atomicAdd(misfit, 0.5 * local);
+}
+
+// Injection rows in adjoint launch order: row a = resid row N-1-a, row N = 0.
+__global__ void reverse_rows_kernel(const float *res, float *inj, int N,
+                                    int nrec) {
+  const long long total = (long long)(N + 1) * nrec;
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+       i < total; i += (long long)gridDim.x * blockDim.x) {
+    const int a = (int)(i / nrec), r = (int)(i - (long long)a * nrec);
+    inj[i] = a < N ? res[(long long)(N - 1 - a) * nrec + r] : 0.f;
+  }
+}
+
+// dJ/dm = sum / (m^2 dt^2) = sum * dt^2 / c^2 with c = m dt^2; dense output.
+__global__ void grad_assemble_kernel(const double *gacc, const float *c,
+                                     float *grad, int nx, int px,
+                                     long long rows, double dt2) {
+  const long long total = rows * (long long)nx;
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+       i < total; i += (long long)gridDim.x * blockDim.x) {
+    const long long r = i / nx;
+    const int x = (int)(i - r * nx);
+    const double cv = c[r * px + x];
+    grad[i] = (float)(gacc[r * px + x] * dt2 / (cv * cv));
+  }
+}
+
+struct DevFree {  // frees the registered device buffers on scope exit
+  std::vector<void *> ptrs;
+  ~DevFree() {
+    for (void *p : ptrs) cudaFree(p);
+  }
+  template <class T>
+  int alloc(T **p, size_t bytes) {
+    *p = nullptr;
+    cudaError_t e = cudaMalloc((void **)p, std::max<size_t>(bytes, 256));
+    if (e != cudaSuccess) return cuda_status(e);
+    ptrs.push_back(*p);
+    return WAVE_OK;
+  }
+};
+
+int gradient_impl(wave_ctx *c, const wave_shot *shot, int N,
+                  const int32_t *rec_xyz, int nrec, const float *data,
+                  bool data_is_resid, int K, double *misfit, float *grad,
+                  float *traces_out) {
+  if (!c || N < 1 || nrec < 0 || K < 1 || !grad) return WAVE_EINVAL;
+  if (nrec > 0 && (!rec_xyz || !data)) return WAVE_EINVAL;
+  if (c->storage != WAVE_STORAGE_F32 ||
+      c->var.func != reinterpret_cast<const void *>(&wave_sweep_kernel<Cfg0>))
+    return WAVE_ENOTSUP;
+  cudaStream_t st = c->stream;
+  const size_t fe = (size_t)c->px * c->ny * c->nz;  // field elements
+  const size_t fb = fe * 4;
+  const int ncp = (N + K - 1) / K;
+  const size_t tn = (size_t)N * nrec;
+  DevFree mem;
+  float *ckpt, *dbuf, *padj[2], *trd, *res, *inj, *wl;
+  double *gacc, *dmis;
+  StepDesc *dadj, *dfwd;
+  int e;
+  if ((e = mem.alloc(&ckpt, fb * 2 * ncp)) || (e = mem.alloc(&dbuf, fb * K)) ||
+      (e = mem.alloc(&padj[0], fb)) || (e = mem.alloc(&padj[1], fb)) ||
+      (e = mem.alloc(&trd, tn * 4)) || (e = mem.alloc(&res, tn * 4)) ||
+      (e = mem.alloc(&inj, (tn + nrec) * 4)) || (e = mem.alloc(&wl, (size_t)N * 4)) ||
+      (e = mem.alloc(&gacc, fe * 8)) || (e = mem.alloc(&dmis, 8)) ||
+      (e = mem.alloc(&dadj, sizeof(StepDesc))) ||
+      (e = mem.alloc(&dfwd, sizeof(StepDesc))))
+    return e;
+  const int mode_attr[3] = {kModeStoreD, kModeInject, kModeInject | kModeGradAcc};
+  const void *fns[3] = {
+      reinterpret_cast<const void *>(&wave_sweep_kernel<Cfg0, false, kModeStoreD>),
+      reinterpret_cast<const void *>(&wave_sweep_kernel<Cfg0, false, kModeInject>),
+      reinterpret_cast<const void *>(
+          &wave_sweep_kernel<Cfg0, false, kModeInject | kModeGradAcc>)};
+  (void)mode_attr;
+  for (const void *f : fns)
+    WAVE_TRY_CUDA(cudaFuncSetAttribute(
+        f, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)Cfg0::SMEM_BYTES));
+
+  // Forward run from rest with a checkpoint (u^{sK}, u^{sK-1}) per segment.
+  if ((e = wave_reset(c))) return e;
+  for (int sgm = 0; sgm < ncp; ++sgm) {
+    WAVE_TRY_CUDA(cudaMemcpyAsync(ckpt + (size_t)2 * sgm * fe, c->buf[c->cur],
+                                  fb, cudaMemcpyDeviceToDevice, st));
+    WAVE_TRY_CUDA(cudaMemcpyAsync(ckpt + (size_t)(2 * sgm + 1) * fe,
+                                  c->buf[c->cur ^ 1], fb,
+                                  cudaMemcpyDeviceToDevice, st));
+    const int len = std::min(K, N - sgm * K);
+    if ((e = wave_propagate(c, shot, len, rec_xyz, nrec,
+                            nrec ? trd + (size_t)sgm * K * nrec : nullptr)))
+      return e;
+  }
+
+  // Residual (dJ/dtraces) and, for the L2 misfit, its FP64 sum.
+  if (nrec > 0) {
+    WAVE_TRY_CUDA(cudaMemcpyAsync(res, data, tn * 4, cudaMemcpyDefault, st));
+    if (!data_is_resid) {
+      WAVE_TRY_CUDA(cudaMemsetAsync(dmis, 0, 8, st));
+      residual_kernel<<<c->sms * 4, 256, 0, st>>>(trd, res, res, (long long)tn,
+                                                  dmis);
+      WAVE_TRY_CUDA(cudaGetLastError());
+    }
+    reverse_rows_kernel<<<c->sms * 4, 256, 0, st>>>(res, inj, N, nrec);
+    WAVE_TRY_CUDA(cudaGetLastError());
+  } else if (!data_is_resid) {
+    WAVE_TRY_CUDA(cudaMemsetAsync(dmis, 0, 8, st));
+  }
+
+  // Descriptors: forward recompute (source, no receivers) and adjoint
+  // (receiver injections, no source).
+  std::vector<float> hw(N, 0.f);
+  StepDesc hf{}, ha{};
+  if (shot) {
+    const double t0 = shot->t0 < 0 ? 1.0 / shot->f_peak : shot->t0;
+    for (int n = 0; n < N; ++n)
+      hw[n] = (float)ricker(n * c->dt, shot->f_peak, t0, shot->amp);
+    hf.wavelet = wl;
+    hf.src_active = 1;
+    hf.sx = shot->sx;
+    hf.sy = shot->sy;
+    hf.sz = shot->sz;
+  }
+  WAVE_TRY_CUDA(cudaMemcpyAsync(wl, hw.data(), (size_t)N * 4,
+                                cudaMemcpyHostToDevice, st));
+  if (nrec > 0) {
+    ha.inj_val = inj;
+    ha.inj = (const int4 *)c->rec.p;  // receiver table of the forward run
+    ha.inj_start = (const int *)c->rec_start.p;
+    ha.ninj = nrec;
+  }
+  WAVE_TRY_CUDA(cudaMemcpyAsync(dfwd, &hf, sizeof(hf), cudaMemcpyHostToDevice, st));
+  WAVE_TRY_CUDA(cudaMemcpyAsync(dadj, &ha, sizeof(ha), cudaMemcpyHostToDevice, st));
+  CUtensorMap ahalo[2], atile[2];
+  for (int b = 0; b < 2; ++b) {
+    if ((e = make_map(&ahalo[b], padj[b], c, c->var.tx + 2 * c->var.halo_x,
+                      c->var.ty + 2 * kR, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, c->pxu,
+                      4)))
+      return e;
+    if ((e = make_map(&atile[b], padj[b], c, c->var.tx, c->var.ty,
+                      CU_TENSOR_MAP_DATA_TYPE_FLOAT32, c->pxu, 4)))
+      return e;
+  }
+  WAVE_TRY_CUDA(cudaMemsetAsync(padj[0], 0, fb, st));
+  WAVE_TRY_CUDA(cudaMemsetAsync(padj[1], 0, fb, st));
+  WAVE_TRY_CUDA(cudaMemsetAsync(gacc, 0, fe * 8, st));
+
+  // Adjoint launch a = N - k computes p^k from p^{k+1} (padj[ca]) and
+  // p^{k+2}; with kModeGradAcc it adds p^{k+1} D^k to the FP64 sum.
+  int ca = 0;
+  auto adjoint_step = [&](int k, const float *dsrc) {
+    SweepArgs a = c->args;
+    a.desc = dadj;
+    a.koff = N - k;
+    a.unext = padj[ca ^ 1];
+    a.dsrc = dsrc;
+    a.gacc = gacc;
+    if (dsrc)
+      launch_mode<kModeInject | kModeGradAcc>(c, ahalo[ca], atile[ca ^ 1], a);
+    else
+      launch_mode<kModeInject>(c, ahalo[ca], atile[ca ^ 1], a);
+    ca ^= 1;
+  };
+  adjoint_step(N, nullptr);  // p^N (no D^N term)
+  for (int sgm = ncp - 1; sgm >= 0; --sgm) {
+    const int s0 = sgm * K, s1 = std::min(N, s0 + K);
+    // Recompute the segment's forward steps from its checkpoint, keeping
+    // D^n = C L u^n + source for n in [s0, s1).
+    WAVE_TRY_CUDA(cudaMemcpyAsync(c->buf[0], ckpt + (size_t)2 * sgm * fe, fb,
+                                  cudaMemcpyDeviceToDevice, st));
+    WAVE_TRY_CUDA(cudaMemcpyAsync(c->buf[1], ckpt + (size_t)(2 * sgm + 1) * fe,
+                                  fb, cudaMemcpyDeviceToDevice, st));
+    int cur = 0;
+    for (int n = s0; n < s1; ++n) {
+      SweepArgs a = c->args;
+      a.desc = dfwd;
+      a.koff = n;
+      a.unext = c->buf[cur ^ 1];
+      a.dout = dbuf + (size_t)(n - s0) * fe;
+      launch_mode<kModeStoreD>(c, c->tm_halo[cur], c->tm_tile[cur ^ 1], a);
+      cur ^= 1;
+    }
+    for (int k = s1 - 1; k >= s0; --k)
+      adjoint_step(k, dbuf + (size_t)(k - s0) * fe);
+  }
+  WAVE_TRY_CUDA(cudaGetLastError());
+
+  // Gradient, traces, misfit.
+  const size_t ne = (size_t)c->nx * c->ny * c->nz;
+  float *gout = grad;
+  const bool host_grad = !is_device_ptr(grad);
+  if (host_grad && (e = mem.alloc(&gout, ne * 4))) return e;
+  grad_assemble_kernel<<<c->sms * 4, 256, 0, st>>>(
+      gacc, c->c, gout, c->nx, c->px, (long long)c->ny * c->nz, c->dt * c->dt);
+  WAVE_TRY_CUDA(cudaGetLastError());
+  if (host_grad)
+    WAVE_TRY_CUDA(cudaMemcpyAsync(grad, gout, ne * 4, cudaMemcpyDeviceToHost, st));
+  if (traces_out && nrec > 0)
+    WAVE_TRY_CUDA(cudaMemcpyAsync(traces_out, trd, tn * 4, cudaMemcpyDefault, st));
+  double hm = 0.0;
+  if (!data_is_resid)
+    WAVE_TRY_CUDA(cudaMemcpyAsync(&hm, dmis, 8, cudaMemcpyDeviceToHost, st));
+  int errs[2] = {0, 0};
+  WAVE_TRY_CUDA(cudaMemcpyAsync(&errs[0], &dfwd->error, 4, cudaMemcpyDeviceToHost, st));
+  WAVE_TRY_CUDA(cudaMemcpyAsync(&errs[1], &dadj->error, 4, cudaMemcpyDeviceToHost, st));
+  WAVE_TRY_CUDA(cudaStreamSynchronize(st));
+  if (misfit && !data_is_resid) *misfit = hm;
+  if ((e = wave_reset(c))) return e;
+  if ((e = read_device_error(c))) return e;
+  if (errs[0] || errs[1]) return WAVE_ETIMEOUT;
+  return WAVE_OK;
+}
+
+}  // namespace
+
+extern "C" int wave_adjoint(wave_ctx *ctx, const wave_shot *shot, int nsteps,
+                            const int32_t *rec_xyz, int nrec,
+                            const float *resid, int ckpt_every, float *grad_v2,
+                            float *traces) {
+  return gradient_impl(ctx, shot, nsteps, rec_xyz, nrec, resid, true,
+                       ckpt_every, nullptr, grad_v2, traces);
+}
+
+extern "C" int wave_gradient(wave_ctx *ctx, const wave_shot *shot, int nsteps,
+                             const int32_t *rec_xyz, int nrec,
+                             const float *observed, int ckpt_every,
+                             double *misfit, float *grad_v2, float *traces) {
+  if (!misfit) return WAVE_EINVAL;
+  return gradient_impl(ctx, shot, nsteps, rec_xyz, nrec, observed, false,
+                       ckpt_every, misfit, grad_v2, traces);
+}
+
+// ---------------------------------------------------------------------------
 // Allocation-free entry point (wave_propagate_noalloc).
 //
 // Its tables live in g_noalloc_scratch, a fixed device array declared here;

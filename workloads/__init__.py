@@ -176,6 +176,32 @@ def serving_requests(n=256, rate_per_s=20.0, seed=0, sizes=tuple(range(128, 513,
     return out
 
 
+# Gradient workload: layered truth with a Gaussian anomaly, smoothed start.
+CFG_GRAD = dict(name="anomaly_256cube", shape=(256, 256, 256), spacing=(10.0, 10.0, 10.0),
+                nsteps=800, ckpt_every=40, f_peak=15.0, seed=0, anomaly_mps=300.0,
+                rec_z=8, rec_stride=4)
+CFG_GRAD_SMALL = dict(CFG_GRAD, name="anomaly_32cube", shape=(32, 32, 32), nsteps=60,
+                      ckpt_every=7, rec_z=4, rec_stride=2)
+
+
+def anomaly_model(nx, ny, nz, seed=0, anomaly=300.0):
+    """Layered model (3 layers, seeded velocities) plus a Gaussian velocity
+    anomaly of `anomaly` m/s at the grid centre (radius nz/6); float32."""
+    rng = np.random.default_rng(seed)
+    v = np.sort(rng.uniform(1800.0, 3200.0, size=3)).astype(np.float32)
+    out = layered3(nx, ny, nz, v=tuple(float(x) for x in v))
+    z, y, x = np.meshgrid(np.arange(nz), np.arange(ny), np.arange(nx), indexing="ij")
+    r2 = ((x - nx / 2) ** 2 + (y - ny / 2) ** 2 + (z - nz / 2) ** 2) / (nz / 6.0) ** 2
+    out += np.float32(anomaly) * np.exp(-r2).astype(np.float32)
+    return out
+
+
+def smoothed_start(model, sigma=3.0):
+    """The starting model: the true model smoothed by a Gaussian (sigma cells)
+    without the anomaly's sharp contrast; float32."""
+    return smooth_gaussian(model, sigma)
+
+
 def velocity_for(cfg):
     """The velocity model a workload description names."""
     nx, ny, nz = cfg["shape"]
