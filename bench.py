@@ -139,6 +139,24 @@ class ClockSampler:
                 "power_w_max": max(power), "reasons": sorted(reasons), "samples": len(sm)}
 
 
+def replica_max(value, device):
+    """Largest `value` over the ranks of the default process group (the value
+    itself when not distributed): each replica times its own work and the job
+    takes the slowest, as the multi-GPU timing rule asks."""
+    import torch
+    import torch.distributed as dist
+    if not (dist.is_available() and dist.is_initialized()) or dist.get_world_size() == 1:
+        return float(value)
+    t = torch.tensor([float(value)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def replica_value(points_per_replica, steps, seconds_max, world):
+    """Whole-job throughput of `world` independent replicas (Gpts/s)."""
+    return world * points_per_replica * steps / seconds_max / 1e9
+
+
 def dist_env():
     rank = int(os.environ.get("RANK", "0"))
     world = int(os.environ.get("WORLD_SIZE", "1"))
@@ -468,13 +486,9 @@ def main():
     torch.cuda.synchronize()
     sampler.stop()
     solver.synchronize()
-    ms = ev0.elapsed_time(ev1)
-    if world > 1:
-        t = torch.tensor([ms], device="cuda")
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        ms = float(t.item())
+    ms = replica_max(ev0.elapsed_time(ev1), "cuda")
     clocks = sampler.summary(tw0, tw1)
-    value = world * npts * K / (ms * 1e-3) / 1e9
+    value = replica_value(npts, K, ms * 1e-3, world)
     launches = (K // GRAPH_STEPS) * (GRAPH_STEPS + 1) + ((K % GRAPH_STEPS) + 1 if K % GRAPH_STEPS else 0)
     tr_ok = bool(torch.isfinite(traces_d[:K]).all().item())
     solver.close()
@@ -493,12 +507,8 @@ def main():
         s2.propagate(shot, K, rec_h, tr_h)
         s2.close()
         torch.cuda.synchronize()
-        el = time.perf_counter() - t0
-        if world > 1:
-            t = torch.tensor([el], device="cuda")
-            torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-            el = float(t.item())
-        e2e = {"value": world * npts * K / el / 1e9, "unit": "Gpts/s",
+        el = replica_max(time.perf_counter() - t0, "cuda")
+        e2e = {"value": replica_value(npts, K, el, world), "unit": "Gpts/s",
                "h2d_bytes_per_step": (vel.nbytes + rec.nbytes) / K,
                "d2h_bytes_per_step": nrec * 4,
                "note": "wave_create(host velocity) + wave_propagate(host receivers, "
@@ -534,14 +544,10 @@ def main():
             e1.record(stream)
             e1.synchronize()
             s16.synchronize()
-            ms16 = e0.elapsed_time(e1)
-            if world > 1:
-                t = torch.tensor([ms16], device="cuda")
-                torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-                ms16 = float(t.item())
+            ms16 = replica_max(e0.elapsed_time(e1), "cuda")
             s16.close()
             del tr16
-            v16 = world * npts * K / (ms16 * 1e-3) / 1e9
+            v16 = replica_value(npts, K, ms16 * 1e-3, world)
             ach = BYTES_PER_POINT_16 * npts / (ms16 * 1e-3 / K) / 1e9
             precision[name] = {"value": v16, "unit": "Gpts/s", "ms_per_step": ms16 / K,
                                "vs_f32": v16 / value,
