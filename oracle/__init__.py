@@ -46,6 +46,17 @@ def _load():
             + [ctypes.c_int] * 3 + [ctypes.c_double] * 3
             + [ctypes.c_void_p, ctypes.c_int, ctypes.c_void_p, ctypes.c_void_p])
         lib.oracle_gradient.restype = ctypes.c_int
+        lib.oracle_first_weights.argtypes = [dp]
+        lib.oracle_first_weights.restype = None
+        lib.oracle_cpml_profile.argtypes = [ctypes.c_int, ctypes.c_int] + [ctypes.c_double] * 5 + [
+            ctypes.c_void_p, ctypes.c_void_p]
+        lib.oracle_cpml_profile.restype = None
+        lib.oracle_propagate_cpml.argtypes = (
+            [ctypes.c_int] * 3 + [ctypes.c_double] * 4 + [ctypes.c_void_p] * 5
+            + [ctypes.c_int64, ctypes.c_int, ctypes.c_int] + [ctypes.c_double] * 3
+            + [ctypes.c_int] * 4 + [ctypes.c_double] * 3
+            + [ctypes.c_void_p, ctypes.c_int, ctypes.c_void_p])
+        lib.oracle_propagate_cpml.restype = ctypes.c_int
         _lib = lib
     return _lib
 
@@ -148,6 +159,55 @@ def gradient(vel, spacing, dt, nsteps, source, receivers, resid):
     if rc != 0:
         raise ValueError("oracle_gradient rejected its input (rc=%d)" % rc)
     return g
+
+
+def first_weights():
+    """The 8th-order central first-derivative weights (index 1..4; index 0 unused)."""
+    w = np.zeros(5, dtype=np.float64)
+    _load().oracle_first_weights(w.ctypes.data_as(ctypes.POINTER(ctypes.c_double)))
+    return w
+
+
+def cpml_profile(n, npml, h, dt, vmax, R=1e-3, fcps=15.0):
+    """(b, a) recursive-convolution coefficients of one axis of n cells."""
+    b = np.zeros(n)
+    a = np.zeros(n)
+    _load().oracle_cpml_profile(int(n), int(npml), float(h), float(dt), float(vmax), float(R),
+                                float(fcps), b.ctypes.data, a.ctypes.data)
+    return b, a
+
+
+def propagate_cpml(vel, spacing, dt, nsteps, npml, R=1e-3, fcps=15.0, vmax=None, u=None,
+                   u_prev=None, psi=None, zeta=None, step0=0, source=None, receivers=None):
+    """oracle propagate with the CPML layer; returns (u, u_prev, psi, zeta, traces)
+    with psi and zeta of shape (3, nz, ny, nx) (axis x, y, z)."""
+    vel = _f64(vel)
+    nz, ny, nx = vel.shape
+    u = np.zeros_like(vel) if u is None else _f64(u, vel.shape).copy()
+    up = np.zeros_like(vel) if u_prev is None else _f64(u_prev, vel.shape).copy()
+    ps = np.zeros((3,) + vel.shape) if psi is None else _f64(psi).copy()
+    ze = np.zeros((3,) + vel.shape) if zeta is None else _f64(zeta).copy()
+    rec = (np.zeros((0, 3), dtype=np.int32) if receivers is None
+           else np.ascontiguousarray(receivers, dtype=np.int32).reshape(-1, 3))
+    nrec = rec.shape[0]
+    traces = np.zeros((nsteps, nrec))
+    if source is None:
+        has, sx, sy, sz, f, t0, amp = 0, 0, 0, 0, 0.0, 0.0, 0.0
+    else:
+        sx, sy, sz, f, t0, amp = source
+        has = 1
+        if t0 is None or t0 < 0:
+            t0 = 1.0 / f
+    vm = float(vel.max()) if vmax is None else float(vmax)
+    rc = _load().oracle_propagate_cpml(
+        nx, ny, nz, *map(float, spacing), float(dt), vel.ctypes.data, u.ctypes.data,
+        up.ctypes.data, ps.ctypes.data, ze.ctypes.data, int(step0), int(nsteps), int(npml),
+        float(R), float(fcps), vm, has, int(sx), int(sy), int(sz), float(f), float(t0),
+        float(amp), rec.ctypes.data if nrec else None, nrec,
+        traces.ctypes.data if nrec else None)
+    if rc != 0:
+        raise ValueError("oracle_propagate_cpml rejected its input (rc=%d)" % rc)
+    return u, up, ps, ze, traces
 
 
 def threads_used():

@@ -288,3 +288,168 @@ int oracle_gradient(int nx, int ny, int nz, double dx, double dy, double dz,
   free(u); free(c); free(q0); free(q1); free(q2); free(cq); free(lap);
   return 0;
 }
+
+/*
+ * Convolutional PML (CPML) around the grid, for the second-order equation.
+ *
+ * The paper surrounds its domain with a CPML-like layer after Komatitsch and
+ * Martin (2007) (Sec. 2, Sec. 4.1) without printing its equations. This
+ * restatement follows from complex-frequency-shifted coordinate stretching
+ * of each axis, s_a = 1 + d_a / (alpha_a + i omega): with
+ * 1/s_a = 1 + chi_a, chi_a(t) = -d_a exp(-(d_a + alpha_a) t) for t > 0,
+ *     u_tt = v^2 sum_a ( d_aa u + d_a psi_a + zeta_a ),
+ *     psi_a  = chi_a * d_a u,   zeta_a = chi_a * ( d_aa u + d_a psi_a ),
+ * and the recursive convolution of Komatitsch and Martin (2007) gives per
+ * step  psi^n = b psi^{n-1} + a (d_a u)^n  (same for zeta) with
+ *     b = exp(-(d + alpha) dt),  a = d / (d + alpha) (b - 1).
+ * Discretised: d_aa by the axis part of Eq. 1, d_a by the 8th-order central
+ * first derivative (weights 4/5, -1/5, 4/105, -1/280), zero outside the grid.
+ * Step n: psi_a^n from u^n; then zeta_a^n from u^n and psi_a^n; then
+ *     u^{n+1} = 2u^n - u^{n-1} + v^2 dt^2 sum_a (D2_a u^n + D1_a psi_a^n + zeta_a^n),
+ * then source and receivers as in oracle_propagate.
+ * Profiles (readings, the paper gives none): layer of npml cells on every
+ * face; xi = depth into the layer / npml in (0, 1] (1 at the outer cell);
+ * d = d0 xi^2 with d0 = 3 vmax ln(1/R) / (2 npml h_a); alpha = pi f_cps (1 -
+ * xi) inside the layer; d = alpha = 0 (b = 1, a = 0) elsewhere.
+ */
+static const double ORACLE_W1[ORACLE_R + 1] = {0.0, 4.0 / 5.0, -1.0 / 5.0,
+                                               4.0 / 105.0, -1.0 / 280.0};
+
+void oracle_first_weights(double *w) {
+  for (int m = 0; m <= ORACLE_R; m++) w[m] = ORACLE_W1[m];
+}
+
+/* b and a of one axis of n cells (spacing h). */
+void oracle_cpml_profile(int n, int npml, double h, double dt, double vmax,
+                         double R, double fcps, double *b, double *a) {
+  const double pi = 3.14159265358979323846;
+  const double L = npml * h;
+  const double d0 = (npml > 0) ? 3.0 * vmax * log(1.0 / R) / (2.0 * L) : 0.0;
+  for (int i = 0; i < n; i++) {
+    double xi = 0.0;
+    if (i < npml) xi = (double)(npml - i) / npml;
+    if (i >= n - npml) {
+      double xr = (double)(i - (n - npml - 1)) / npml;
+      if (xr > xi) xi = xr;
+    }
+    if (xi <= 0.0) {
+      b[i] = 1.0;
+      a[i] = 0.0;
+      continue;
+    }
+    const double d = d0 * xi * xi;
+    const double al = pi * fcps * (1.0 - xi);
+    b[i] = exp(-(d + al) * dt);
+    a[i] = (d + al > 0.0) ? d / (d + al) * (b[i] - 1.0) : 0.0;
+  }
+}
+
+/* axis part of Eq. 1 (second derivative) and the first derivative of f at
+ * (i,j,k) along axis ax (0 = x, 1 = y, 2 = z), zero outside the grid */
+static double oracle_d2(const double *f, int nx, int ny, int nz, int i, int j,
+                        int k, int ax, double h) {
+  int di = ax == 0, dj = ax == 1, dk = ax == 2;
+  double s = ORACLE_W[0] * oracle_at(f, nx, ny, nz, i, j, k, 0);
+  for (int m = 1; m <= ORACLE_R; m++)
+    s += ORACLE_W[m] * (oracle_at(f, nx, ny, nz, i + m * di, j + m * dj, k + m * dk, 0) +
+                        oracle_at(f, nx, ny, nz, i - m * di, j - m * dj, k - m * dk, 0));
+  return s / (h * h);
+}
+
+static double oracle_d1(const double *f, int nx, int ny, int nz, int i, int j,
+                        int k, int ax, double h) {
+  int di = ax == 0, dj = ax == 1, dk = ax == 2;
+  double s = 0.0;
+  for (int m = 1; m <= ORACLE_R; m++)
+    s += ORACLE_W1[m] * (oracle_at(f, nx, ny, nz, i + m * di, j + m * dj, k + m * dk, 0) -
+                         oracle_at(f, nx, ny, nz, i - m * di, j - m * dj, k - m * dk, 0));
+  return s / h;
+}
+
+/*
+ * oracle_propagate with the CPML above (zero halo beyond it). psi and zeta
+ * are 3 arrays each of nx*ny*nz (axis x, y, z), in/out, zero to start.
+ * vmax sets d0 (pass the model's largest velocity).
+ */
+int oracle_propagate_cpml(int nx, int ny, int nz, double dx, double dy,
+                          double dz, double dt, const double *vel, double *u,
+                          double *u_prev, double *psi, double *zeta,
+                          int64_t step0, int nsteps, int npml, double R,
+                          double fcps, double vmax, int has_source, int sx,
+                          int sy, int sz, double f, double t0, double amp,
+                          const int32_t *rec, int nrec, double *traces) {
+  if (nx < 1 || ny < 1 || nz < 1 || nsteps < 0 || nrec < 0 || npml < 0 ||
+      !(R > 0.0 && R <= 1.0))
+    return -1;
+  if (has_source && (sx < 0 || sx >= nx || sy < 0 || sy >= ny || sz < 0 || sz >= nz))
+    return -1;
+  for (int r = 0; r < nrec; r++)
+    if (rec[3 * r] < 0 || rec[3 * r] >= nx || rec[3 * r + 1] < 0 ||
+        rec[3 * r + 1] >= ny || rec[3 * r + 2] < 0 || rec[3 * r + 2] >= nz)
+      return -1;
+  const size_t n = (size_t)nx * ny * nz;
+  const int dims[3] = {nx, ny, nz};
+  const double hs[3] = {dx, dy, dz};
+  double *b[3], *a[3];
+  double *c = (double *)malloc(n * sizeof(double));
+  double *unext = (double *)malloc(n * sizeof(double));
+  int ok = c && unext;
+  for (int ax = 0; ax < 3; ax++) {
+    b[ax] = (double *)malloc(dims[ax] * sizeof(double));
+    a[ax] = (double *)malloc(dims[ax] * sizeof(double));
+    ok = ok && b[ax] && a[ax];
+  }
+  if (!ok) {
+    free(c); free(unext);
+    for (int ax = 0; ax < 3; ax++) { free(b[ax]); free(a[ax]); }
+    return -1;
+  }
+  for (int ax = 0; ax < 3; ax++)
+    oracle_cpml_profile(dims[ax], npml, hs[ax], dt, vmax, R, fcps, b[ax], a[ax]);
+  for (size_t p = 0; p < n; p++) c[p] = vel[p] * vel[p] * dt * dt;
+  for (int s = 0; s < nsteps; s++) {
+    /* psi_a^n from u^n */
+#pragma omp parallel for schedule(static)
+    for (int k = 0; k < nz; k++)
+      for (int j = 0; j < ny; j++)
+        for (int i = 0; i < nx; i++) {
+          const size_t p = ((size_t)k * ny + j) * nx + i;
+          const int idx[3] = {i, j, k};
+          for (int ax = 0; ax < 3; ax++)
+            psi[ax * n + p] = b[ax][idx[ax]] * psi[ax * n + p] +
+                              a[ax][idx[ax]] *
+                                  oracle_d1(u, nx, ny, nz, i, j, k, ax, hs[ax]);
+        }
+    /* zeta_a^n and u^{n+1} */
+#pragma omp parallel for schedule(static)
+    for (int k = 0; k < nz; k++)
+      for (int j = 0; j < ny; j++)
+        for (int i = 0; i < nx; i++) {
+          const size_t p = ((size_t)k * ny + j) * nx + i;
+          const int idx[3] = {i, j, k};
+          double sum = 0.0;
+          for (int ax = 0; ax < 3; ax++) {
+            const double d2 = oracle_d2(u, nx, ny, nz, i, j, k, ax, hs[ax]);
+            const double d1p =
+                oracle_d1(psi + ax * n, nx, ny, nz, i, j, k, ax, hs[ax]);
+            zeta[ax * n + p] = b[ax][idx[ax]] * zeta[ax * n + p] +
+                               a[ax][idx[ax]] * (d2 + d1p);
+            sum += d2 + d1p + zeta[ax * n + p];
+          }
+          unext[p] = 2.0 * u[p] - u_prev[p] + c[p] * sum;
+        }
+    if (has_source) {
+      size_t ps = ((size_t)sz * ny + sy) * nx + sx;
+      unext[ps] += c[ps] * oracle_ricker((double)(step0 + s) * dt, f, t0, amp);
+    }
+    for (int r = 0; r < nrec; r++) {
+      size_t pr = ((size_t)rec[3 * r + 2] * ny + rec[3 * r + 1]) * nx + rec[3 * r];
+      traces[(size_t)s * nrec + r] = unext[pr];
+    }
+    memcpy(u_prev, u, n * sizeof(double));
+    memcpy(u, unext, n * sizeof(double));
+  }
+  free(c); free(unext);
+  for (int ax = 0; ax < 3; ax++) { free(b[ax]); free(a[ax]); }
+  return 0;
+}

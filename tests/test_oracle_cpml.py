@@ -1,0 +1,180 @@
+"""Pins of the oracle's CPML layer (FP64, CPU): the first-derivative weights
+from an exact solve, reduction to the plain scheme when the layer does not
+damp, a dense state-space brute force on a tiny grid, measured absorption
+against the reflecting zero boundary, and mirror symmetry."""
+import math
+from fractions import Fraction
+
+import numpy as np
+import pytest
+
+R4 = 4
+
+
+def _exact_first_derivative_weights(radius):
+    """Antisymmetric a_1..a_R with sum_m a_m (f(m) - f(-m)) ~ h f'(0):
+    odd moments 2 sum_m a_m m^(2p+1) = 1 for p = 0, 0 for p = 1..R-1."""
+    n = radius
+    a = [[Fraction(2 * m ** (2 * p + 1)) for m in range(1, n + 1)] + [Fraction(1 if p == 0 else 0)]
+         for p in range(n)]
+    for col in range(n):
+        piv = next(r for r in range(col, n) if a[r][col] != 0)
+        a[col], a[piv] = a[piv], a[col]
+        pv = a[col][col]
+        a[col] = [x / pv for x in a[col]]
+        for r in range(n):
+            if r != col and a[r][col] != 0:
+                f = a[r][col]
+                a[r] = [x - f * y for x, y in zip(a[r], a[col])]
+    return [a[i][n] for i in range(n)]
+
+
+def test_first_derivative_weights(oracle_mod):
+    ex = _exact_first_derivative_weights(R4)
+    assert ex == [Fraction(4, 5), Fraction(-1, 5), Fraction(4, 105), Fraction(-1, 280)]
+    w = oracle_mod.first_weights()
+    assert list(w[1:]) == [float(x) for x in ex]
+
+
+def _profile_closed_form(n, npml, h, dt, vmax, R, fcps):
+    d0 = 3.0 * vmax * math.log(1.0 / R) / (2.0 * npml * h)
+    b = np.ones(n)
+    a = np.zeros(n)
+    for i in range(n):
+        xi = max((npml - i) / npml if i < npml else 0.0,
+                 (i - (n - npml - 1)) / npml if i >= n - npml else 0.0)
+        if xi > 0:
+            d = d0 * xi * xi
+            al = math.pi * fcps * (1.0 - xi)
+            b[i] = math.exp(-(d + al) * dt)
+            a[i] = d / (d + al) * (b[i] - 1.0)
+    return b, a
+
+
+def test_profile(oracle_mod):
+    b, a = oracle_mod.cpml_profile(30, 6, 10.0, 1e-3, 3000.0, 1e-3, 15.0)
+    eb, ea = _profile_closed_form(30, 6, 10.0, 1e-3, 3000.0, 1e-3, 15.0)
+    np.testing.assert_allclose(b, eb, rtol=1e-14)
+    np.testing.assert_allclose(a, ea, rtol=1e-14, atol=1e-300)
+    assert np.all(b[6:24] == 1.0) and np.all(a[6:24] == 0.0)
+    assert b[0] == b[29] and a[0] == a[29]           # symmetric layer
+    assert np.all((a[:6] < 0) & (b[:6] < 1))          # damping inside
+
+
+def test_undamped_layer_is_the_plain_scheme(oracle_mod):
+    rng = np.random.default_rng(4)
+    nz, ny, nx = 11, 12, 13
+    vel = rng.uniform(1500, 3000, size=(nz, ny, nx))
+    sp = (10.0, 9.0, 11.0)
+    dt = 0.5 * oracle_mod.cfl_dt(sp, vel.max())
+    u0 = rng.standard_normal(vel.shape)
+    up0 = rng.standard_normal(vel.shape)
+    rec = np.array([[1, 2, 3], [12, 11, 10], [6, 6, 5]], dtype=np.int32)
+    shot = (6, 5, 4, 20.0, -1.0, 1.0)
+    u1, up1, ps, ze, tr1 = oracle_mod.propagate_cpml(vel, sp, dt, 17, npml=4, R=1.0, u=u0,
+                                                     u_prev=up0, source=shot, receivers=rec)
+    u2, up2, tr2 = oracle_mod.propagate(vel, sp, dt, 17, u=u0, u_prev=up0, source=shot,
+                                        receivers=rec)
+    assert np.all(ps == 0) and np.all(ze == 0)
+    sc = np.abs(u2).max()
+    np.testing.assert_allclose(u1, u2, rtol=0, atol=1e-12 * sc)
+    np.testing.assert_allclose(tr1, tr2, rtol=0, atol=1e-12 * sc)
+
+
+def _dense_axis(n, h, w, first):
+    D = np.zeros((n, n))
+    for i in range(n):
+        if not first:
+            D[i, i] += w[0] / h ** 2
+        for m in range(1, R4 + 1):
+            for j, sgn in ((i + m, 1.0), (i - m, -1.0 if first else 1.0)):
+                if 0 <= j < n:
+                    D[i, j] += (sgn * w[m] / h) if first else (w[m] / h ** 2)
+    return D
+
+
+def test_dense_state_space_brute_force(oracle_mod):
+    nz, ny, nx = 7, 8, 9
+    sp = (10.0, 12.0, 9.0)
+    npml, R, fcps = 2, 1e-3, 20.0
+    rng = np.random.default_rng(8)
+    vel = rng.uniform(1500, 3000, size=(nz, ny, nx))
+    dt = 0.45 * oracle_mod.cfl_dt(sp, vel.max())
+    w2 = [-205 / 72, 8 / 5, -1 / 5, 8 / 315, -1 / 560]
+    w1 = [0.0, 4 / 5, -1 / 5, 4 / 105, -1 / 280]
+    dims = (nx, ny, nz)
+    I = [np.eye(d) for d in dims]
+
+    def lift(M, ax):  # 1D operator on axis ax -> full flat (z slowest, x fastest)
+        mats = [I[2], I[1], I[0]]
+        mats[2 - ax] = M
+        return np.kron(mats[0], np.kron(mats[1], mats[2]))
+
+    D1 = [lift(_dense_axis(dims[ax], sp[ax], w1, True), ax) for ax in range(3)]
+    D2 = [lift(_dense_axis(dims[ax], sp[ax], w2, False), ax) for ax in range(3)]
+    B, A = [], []
+    for ax in range(3):
+        b, a = _profile_closed_form(dims[ax], npml, sp[ax], dt, vel.max(), R, fcps)
+        B.append(np.diag(lift(np.diag(b), ax)))
+        A.append(np.diag(lift(np.diag(a), ax)))
+    c = (vel ** 2 * dt ** 2).ravel()
+    N = c.size
+    u = rng.standard_normal(N)
+    up = rng.standard_normal(N)
+    psi = [np.zeros(N) for _ in range(3)]
+    zeta = [np.zeros(N) for _ in range(3)]
+    src = (4, 3, 5)
+    ps_i = (src[2] * ny + src[1]) * nx + src[0]
+    rec = np.array([[0, 0, 0], [8, 7, 6], [4, 3, 5], [1, 6, 2]], dtype=np.int32)
+    pr = (rec[:, 2] * ny + rec[:, 1]) * nx + rec[:, 0]
+    f, t0 = 25.0, 0.04
+    nsteps = 11
+    tr = np.zeros((nsteps, len(rec)))
+    u_init, up_init = u.copy(), up.copy()
+    for n in range(nsteps):
+        psi = [B[ax] * psi[ax] + A[ax] * (D1[ax] @ u) for ax in range(3)]
+        zeta = [B[ax] * zeta[ax] + A[ax] * (D2[ax] @ u + D1[ax] @ psi[ax]) for ax in range(3)]
+        s = sum(D2[ax] @ u + D1[ax] @ psi[ax] + zeta[ax] for ax in range(3))
+        un = 2 * u - up + c * s
+        t = n * dt
+        aa = (math.pi * f * (t - t0)) ** 2
+        un[ps_i] += c[ps_i] * (1 - 2 * aa) * math.exp(-aa)
+        tr[n] = un[pr]
+        up, u = u, un
+    ou, oup, ops, oze, otr = oracle_mod.propagate_cpml(
+        vel, sp, dt, nsteps, npml, R=R, fcps=fcps, u=u_init.reshape(vel.shape),
+        u_prev=up_init.reshape(vel.shape), source=(*src, f, t0, 1.0), receivers=rec)
+    sc = np.abs(u).max()
+    np.testing.assert_allclose(ou.ravel(), u, rtol=0, atol=1e-12 * sc)
+    np.testing.assert_allclose(otr, tr, rtol=0, atol=1e-12 * sc)
+    for ax in range(3):
+        np.testing.assert_allclose(ops[ax].ravel(), psi[ax], rtol=0,
+                                   atol=1e-12 * max(1e-300, np.abs(psi[ax]).max()))
+        np.testing.assert_allclose(oze[ax].ravel(), zeta[ax], rtol=0,
+                                   atol=1e-12 * max(1e-300, np.abs(zeta[ax]).max()))
+
+
+def test_layer_absorbs_what_the_zero_boundary_reflects(oracle_mod):
+    n, npml = 40, 10
+    vel = np.full((n, n, n), 2000.0)
+    sp = (10.0, 10.0, 10.0)
+    dt = 0.5 * oracle_mod.cfl_dt(sp, 2000.0)
+    shot = (20, 20, 20, 25.0, 0.04, 1.0)
+    steps = 360  # the pulse reaches the faces near step 90 and is back by 180
+    u_d, _, _ = oracle_mod.propagate(vel, sp, dt, steps, source=shot)
+    u_p, _, _, _, _ = oracle_mod.propagate_cpml(vel, sp, dt, steps, npml, R=1e-3, fcps=25.0,
+                                                source=shot)
+    inner = (slice(npml, n - npml),) * 3
+    ratio = np.linalg.norm(u_p[inner]) / np.linalg.norm(u_d[inner])
+    assert ratio < 0.03, ratio
+
+
+def test_cpml_keeps_mirror_symmetry(oracle_mod):
+    n = 21
+    vel = np.full((n, n, n), 2500.0)
+    dt = 0.5 * oracle_mod.cfl_dt((10.0,) * 3, 2500.0)
+    u, _, _, _, _ = oracle_mod.propagate_cpml(vel, (10.0,) * 3, dt, 80, 5, source=(10, 10, 10, 25.0, -1.0, 1.0))
+    sc = np.abs(u).max()
+    for axis in range(3):
+        assert np.max(np.abs(u - np.flip(u, axis))) <= 1e-12 * sc
+    assert np.max(np.abs(u - np.transpose(u, (2, 1, 0)))) <= 1e-12 * sc
