@@ -156,6 +156,30 @@ int wave_get_step(const wave_ctx *ctx, int64_t *step);
 /* Zero both wavefields and the step counter. */
 int wave_reset(wave_ctx *ctx);
 
+/*
+ * Absorbing boundary: a convolutional PML (CPML) of npml cells inside every
+ * face of the grid, in place of the bare zero halo (the paper's domain is
+ * surrounded by a CPML-like layer after Komatitsch and Martin 2007, Sec. 2).
+ * Second-order form from complex-frequency-shifted coordinate stretching:
+ *   u_tt = v^2 sum_a (d_aa u + d_a psi_a + zeta_a),
+ *   psi_a^n = b psi_a^{n-1} + a D1_a u^n,
+ *   zeta_a^n = b zeta_a^{n-1} + a (D2_a u^n + D1_a psi_a^n),
+ *   b = exp(-(d + alpha) dt), a = d / (d + alpha) (b - 1),
+ * with D2_a the axis part of Eq. 1, D1_a the 8th-order central first
+ * derivative (4/5, -1/5, 4/105, -1/280), and per axis the profile
+ * d = d0 xi^2, d0 = 3 vmax ln(1/reflection) / (2 npml h_a), alpha =
+ * pi f_cps (1 - xi), xi in (0, 1] the depth into the layer (1 at the face).
+ *   npml        layer cells per face; 0 switches the layer off; otherwise
+ *               1 <= npml and 2 npml <= nx, ny, nz
+ *   reflection  target reflection coefficient, 0 < reflection < 1
+ *   f_cps       frequency shift (Hz, >= 0), typically the source's peak
+ * FP32 storage only (WAVE_ENOTSUP otherwise). The layer's memory variables
+ * start at zero here and are zeroed by wave_reset and wave_set_state. The
+ * source and receivers may lie in the layer. wave_adjoint / wave_gradient
+ * do not support the layer (WAVE_ENOTSUP).
+ */
+int wave_set_cpml(wave_ctx *ctx, int npml, double reflection, double f_cps);
+
 /* Wait for the context's stream; return any error a kernel recorded. */
 int wave_synchronize(wave_ctx *ctx);
 

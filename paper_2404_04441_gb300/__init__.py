@@ -18,6 +18,7 @@ __all__ = [
     "wave_synchronize", "wave_destroy", "wave_strerror", "wave_get_launch_info",
     "wave_selftest_wait", "wave_propagate_noalloc", "WaveSolver", "library_path",
     "ShotServer", "wave_adjoint", "wave_gradient", "WaveTraces", "wave_traces",
+    "wave_set_cpml",
 ]
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
@@ -99,6 +100,7 @@ def load(path=None):
     lib.wave_set_state.argtypes = [vp, vp, vp, ctypes.c_int64]
     lib.wave_get_step.argtypes = [vp, ctypes.POINTER(ctypes.c_int64)]
     lib.wave_reset.argtypes = [vp]
+    lib.wave_set_cpml.argtypes = [vp, ip, ctypes.c_double, ctypes.c_double]
     lib.wave_synchronize.argtypes = [vp]
     lib.wave_destroy.argtypes = [vp]
     lib.wave_destroy.restype = None
@@ -125,7 +127,8 @@ def load(path=None):
         ctypes.POINTER(_Shot), ctypes.c_int64, ip, vp, ip, vp, vp, ctypes.POINTER(ip)]
     for name in ("wave_create", "wave_step", "wave_propagate", "wave_get_field",
                  "wave_set_state", "wave_get_step", "wave_reset", "wave_synchronize",
-                 "wave_get_launch_info", "wave_selftest_wait", "wave_propagate_noalloc"):
+                 "wave_get_launch_info", "wave_selftest_wait", "wave_propagate_noalloc",
+                 "wave_set_cpml"):
         getattr(lib, name).restype = ctypes.c_int
     _lib = lib
     return lib
@@ -233,6 +236,12 @@ def wave_get_step(ctx):
 
 def wave_reset(ctx):
     _check(load().wave_reset(ctx), "wave_reset")
+
+
+def wave_set_cpml(ctx, npml, reflection=1e-3, f_cps=15.0):
+    """Absorbing CPML layer of npml cells at every face (0 switches it off)."""
+    _check(load().wave_set_cpml(ctx, int(npml), float(reflection), float(f_cps)),
+           "wave_set_cpml")
 
 
 def wave_synchronize(ctx):
@@ -354,6 +363,9 @@ class WaveSolver:
 
     def reset(self):
         wave_reset(self.ctx)
+
+    def set_cpml(self, npml, reflection=1e-3, f_cps=15.0):
+        wave_set_cpml(self.ctx, npml, reflection, f_cps)
 
     def synchronize(self):
         wave_synchronize(self.ctx)

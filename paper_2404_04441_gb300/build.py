@@ -14,7 +14,7 @@ CSRC = os.path.join(HERE, "csrc")
 OUT_DIR = os.path.join(HERE, "_build")
 LIB = os.path.join(OUT_DIR, "libgbwave.so")
 SOURCES = [os.path.join(CSRC, f) for f in ("wave.cu", "serve.cu")]
-DEPS = SOURCES + [os.path.join(CSRC, f) for f in ("sweep.cuh", "ptx.cuh", "common.cuh")] + [
+DEPS = SOURCES + [os.path.join(CSRC, f) for f in ("sweep.cuh", "ptx.cuh", "common.cuh", "cpml.cuh")] + [
     os.path.join(ROOT, "include", f) for f in ("wave.h", "wave_serve.h")]
 
 NVCC_FLAGS = [

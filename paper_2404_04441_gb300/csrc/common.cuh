@@ -24,6 +24,8 @@ using namespace gbw;
 // discretization parameters, c_am = w_m / h_a^2).
 constexpr double kW[5] = {-205.0 / 72.0, 8.0 / 5.0, -1.0 / 5.0, 8.0 / 315.0,
                           -1.0 / 560.0};
+// 8th-order central first-derivative weights (index 1..4), for the CPML.
+constexpr double kW1[5] = {0.0, 4.0 / 5.0, -1.0 / 5.0, 4.0 / 105.0, -1.0 / 280.0};
 
 // Velocity scan over the dense-in-x pitched buffer: max, and count of values
 // that are not finite and positive.

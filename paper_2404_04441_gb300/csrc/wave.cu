@@ -17,6 +17,7 @@
 
 #include "../../include/wave.h"
 #include "common.cuh"
+#include "cpml.cuh"
 #include "sweep.cuh"
 
 using namespace gbw;
@@ -135,6 +136,15 @@ struct wave_ctx {
   std::vector<int> h_rec_start;
   std::vector<float> h_wavelet;
   unsigned char scale_image[32];  // host staging of the 16-bit scale state
+  // CPML layer (wave_set_cpml).
+  bool cpml = false;
+  CpmlGeom cg{};
+  std::vector<void *> cpml_mem;
+  std::vector<int> czl, czm, cyl, cym, cxl;  // shell lists (host copies)
+  DeviceBuf srec;            // receivers in the shell: {shell index, id}
+  int *d_nsrec = nullptr;    // their count (device: graphs stay valid)
+  std::vector<int2> h_srec;
+  int cpml_nsrec_host = 0;
 };
 
 namespace {
@@ -179,12 +189,70 @@ void set_coeffs(wave_ctx *c) {
   a.desc = c->d_desc;
 }
 
-// Enqueue one step on stream st: u = buf[cur], u_prev = buf[cur ^ 1].
+// Enqueue one step on stream st: u = buf[cur], u_prev = buf[cur ^ 1]. With
+// the CPML layer: memory variables and shell points before the sweep, the
+// shell values committed after it.
 void enqueue_step(wave_ctx *c, cudaStream_t st, int cur, int koff) {
   SweepArgs a = c->args;
   a.unext = c->buf[cur ^ 1];
   a.koff = koff;
+  const float *u = (const float *)c->buf[cur];
+  if (c->cpml) {
+    cpml_psi_kernel<<<c->sms * 4, 256, 0, st>>>(c->cg, u);
+    cpml_shell_kernel<<<c->sms * 4, 256, 0, st>>>(
+        c->cg, u, (const float *)c->buf[cur ^ 1], c->c, c->d_desc, koff);
+  }
   c->var.launch(c->grid, st, c->tm_halo[cur], c->tm_tile[cur ^ 1], c->tm_c, a);
+  if (c->cpml)
+    cpml_commit_kernel<<<c->sms * 4, 256, 0, st>>>(
+        c->cg, (float *)c->buf[cur ^ 1], c->d_desc, (const int2 *)c->srec.p,
+        c->d_nsrec, koff);
+}
+
+void drop_graphs(wave_ctx *c) {
+  for (int p = 0; p < 2; ++p)
+    if (c->graph[p]) {
+      cudaGraphExecDestroy(c->graph[p]);
+      c->graph[p] = nullptr;
+    }
+}
+
+void free_cpml(wave_ctx *c) {
+  for (void *p : c->cpml_mem) cudaFree(p);
+  c->cpml_mem.clear();
+  c->cpml = false;
+  c->cg = CpmlGeom{};
+}
+
+int zero_cpml(wave_ctx *c) {
+  if (!c->cpml) return WAVE_OK;
+  const size_t sl[3] = {2ull * c->cg.npml * c->ny * c->nz,
+                        2ull * c->cg.npml * c->nz * c->nx,
+                        2ull * c->cg.npml * c->ny * c->nx};
+  for (int ax = 0; ax < 3; ++ax) {
+    WAVE_TRY_CUDA(cudaMemsetAsync(c->cg.psi[ax], 0, sl[ax] * 4, c->stream));
+    WAVE_TRY_CUDA(cudaMemsetAsync(c->cg.zeta[ax], 0, sl[ax] * 4, c->stream));
+  }
+  return WAVE_OK;
+}
+
+// Compact index of a point in the CPML shell (enumeration of cpml.cuh), or
+// -1 when the point is not in the shell.
+long long cpml_shell_index(const wave_ctx *c, int x, int y, int z) {
+  auto pos = [](const std::vector<int> &v, int val) -> long long {
+    auto it = std::lower_bound(v.begin(), v.end(), val);
+    return (it != v.end() && *it == val) ? (long long)(it - v.begin()) : -1;
+  };
+  const CpmlGeom &g = c->cg;
+  long long i = pos(c->czl, z);
+  if (i >= 0) return i * c->nx * c->ny + (long long)y * c->nx + x;
+  const long long izm = pos(c->czm, z);
+  i = pos(c->cyl, y);
+  if (i >= 0) return g.cz + izm * g.nyl * c->nx + i * c->nx + x;
+  const long long iym = pos(c->cym, y);
+  i = pos(c->cxl, x);
+  if (i >= 0) return g.cz + g.cy + izm * g.nym * g.nxl + iym * g.nxl + i;
+  return -1;
 }
 
 int build_graph(wave_ctx *c, int parity) {
@@ -289,6 +357,9 @@ void wave_destroy(wave_ctx *c) {
   cudaFree(c->rec_start.p);
   cudaFree(c->traces.p);
   if (c->capture_stream) cudaStreamDestroy(c->capture_stream);
+  free_cpml(c);
+  cudaFree(c->srec.p);
+  cudaFree(c->d_nsrec);
   delete c;
 }
 
@@ -422,6 +493,11 @@ int wave_step(wave_ctx *c, int nsteps) {
   if (nsteps == 0) return WAVE_OK;
   StepDesc &d = c->host_desc;
   std::memset(&d, 0, sizeof(d));
+  if (c->cpml) {
+    c->cpml_nsrec_host = 0;
+    WAVE_TRY_CUDA(cudaMemcpyAsync(c->d_nsrec, &c->cpml_nsrec_host, sizeof(int),
+                                  cudaMemcpyHostToDevice, c->stream));
+  }
   int st = upload_desc(c);
   if (st) return st;
   return run_steps(c, nsteps);
@@ -512,6 +588,27 @@ int wave_propagate(wave_ctx *c, const wave_shot *shot, int nsteps,
     d.rec = (const int4 *)c->rec.p;
     d.rec_start = (const int *)c->rec_start.p;
     d.nrec = nrec;
+  }
+  if (c->cpml) {
+    // receivers inside the CPML shell are recorded from the shell values
+    c->h_srec.clear();
+    for (int r = 0; r < nrec; ++r) {
+      const long long t = cpml_shell_index(c, hrec[3 * r], hrec[3 * r + 1],
+                                           hrec[3 * r + 2]);
+      if (t >= 0) c->h_srec.push_back(make_int2((int)t, r));
+    }
+    const int ns = (int)c->h_srec.size();
+    if (ns > 0) {
+      void *old = c->srec.p;
+      if ((s = ensure(c->srec, (size_t)ns * sizeof(int2), st))) return s;
+      if (c->srec.p != old) drop_graphs(c);  // graphs hold the list's address
+      WAVE_TRY_CUDA(cudaMemcpyAsync(c->srec.p, c->h_srec.data(),
+                                    (size_t)ns * sizeof(int2),
+                                    cudaMemcpyHostToDevice, st));
+    }
+    c->cpml_nsrec_host = ns;
+    WAVE_TRY_CUDA(cudaMemcpyAsync(c->d_nsrec, &c->cpml_nsrec_host, sizeof(int),
+                                  cudaMemcpyHostToDevice, st));
   }
   if ((s = upload_desc(c))) return s;
   if ((s = run_steps(c, nsteps))) return s;
@@ -671,6 +768,8 @@ int wave_set_state(wave_ctx *c, const float *u, const float *u_prev,
                                     (size_t)c->ny * c->nz, cudaMemcpyDefault,
                                     c->stream));
   c->step = step;
+  int zs = zero_cpml(c);
+  if (zs) return zs;
   if (!is_device_ptr(u) || !is_device_ptr(u_prev))
     WAVE_TRY_CUDA(cudaStreamSynchronize(c->stream));
   return WAVE_OK;
@@ -692,6 +791,124 @@ int wave_reset(wave_ctx *c) {
       sizeof(int) * 4 + sizeof(unsigned) * 4, c->stream));
   c->cur = 0;
   c->step = 0;
+  return zero_cpml(c);
+}
+
+int wave_set_cpml(wave_ctx *c, int npml, double R, double f_cps) {
+  if (!c || npml < 0) return WAVE_EINVAL;
+  if (npml == 0) {
+    WAVE_TRY_CUDA(cudaStreamSynchronize(c->stream));
+    free_cpml(c);
+  } else {
+    if (2 * npml > std::min(c->nx, std::min(c->ny, c->nz)) || !(R > 0.0 && R < 1.0) ||
+        !(f_cps >= 0.0) || !std::isfinite(f_cps))
+      return WAVE_EINVAL;
+    if (c->storage != WAVE_STORAGE_F32) return WAVE_ENOTSUP;
+    WAVE_TRY_CUDA(cudaStreamSynchronize(c->stream));
+    free_cpml(c);
+    CpmlGeom &g = c->cg;
+    g.nx = c->nx;
+    g.ny = c->ny;
+    g.nz = c->nz;
+    g.px = c->px;
+    g.npml = npml;
+    g.w = npml + 4;
+    auto lists = [&](int n, std::vector<int> &shell, std::vector<int> &mid) {
+      shell.clear();
+      mid.clear();
+      for (int i = 0; i < n; ++i)
+        (i < g.w || i >= n - g.w ? shell : mid).push_back(i);
+    };
+    std::vector<int> xmid;
+    lists(c->nz, c->czl, c->czm);
+    lists(c->ny, c->cyl, c->cym);
+    lists(c->nx, c->cxl, xmid);
+    g.nzl = (int)c->czl.size();
+    g.nzm = (int)c->czm.size();
+    g.nyl = (int)c->cyl.size();
+    g.nym = (int)c->cym.size();
+    g.nxl = (int)c->cxl.size();
+    g.cz = (long long)g.nzl * c->nx * c->ny;
+    g.cy = (long long)g.nzm * g.nyl * c->nx;
+    g.cx = (long long)g.nzm * g.nym * g.nxl;
+    const size_t sl[3] = {2ull * npml * c->ny * c->nz, 2ull * npml * c->nz * c->nx,
+                          2ull * npml * c->ny * c->nx};
+    auto dalloc = [&](void **p, size_t bytes) -> int {
+      cudaError_t e = cudaMalloc(p, std::max<size_t>(bytes, 256));
+      if (e != cudaSuccess) return cuda_status(e);
+      c->cpml_mem.push_back(*p);
+      return WAVE_OK;
+    };
+    int e;
+    const int dims[3] = {c->nx, c->ny, c->nz};
+    const double hs[3] = {c->dx, c->dy, c->dz};
+    for (int ax = 0; ax < 3; ++ax) {
+      if ((e = dalloc((void **)&g.psi[ax], sl[ax] * 4)) ||
+          (e = dalloc((void **)&g.zeta[ax], sl[ax] * 4)) ||
+          (e = dalloc((void **)&g.bprof[ax], dims[ax] * 4)) ||
+          (e = dalloc((void **)&g.aprof[ax], dims[ax] * 4))) {
+        free_cpml(c);
+        return e;
+      }
+      // Profiles (FP64, stored FP32) and derivative coefficients.
+      std::vector<float> hb(dims[ax]), ha(dims[ax]);
+      const double pi = 3.14159265358979323846;
+      const double d0 = 3.0 * c->vmax * std::log(1.0 / R) / (2.0 * npml * hs[ax]);
+      for (int i = 0; i < dims[ax]; ++i) {
+        double xi = 0.0;
+        if (i < npml) xi = (double)(npml - i) / npml;
+        if (i >= dims[ax] - npml)
+          xi = std::max(xi, (double)(i - (dims[ax] - npml - 1)) / npml);
+        if (xi <= 0.0) {
+          hb[i] = 1.f;
+          ha[i] = 0.f;
+          continue;
+        }
+        const double dd = d0 * xi * xi, al = pi * f_cps * (1.0 - xi);
+        const double bb = std::exp(-(dd + al) * c->dt);
+        hb[i] = (float)bb;
+        ha[i] = (float)(dd + al > 0.0 ? dd / (dd + al) * (bb - 1.0) : 0.0);
+      }
+      WAVE_TRY_CUDA(cudaMemcpy((void *)g.bprof[ax], hb.data(), dims[ax] * 4,
+                               cudaMemcpyHostToDevice));
+      WAVE_TRY_CUDA(cudaMemcpy((void *)g.aprof[ax], ha.data(), dims[ax] * 4,
+                               cudaMemcpyHostToDevice));
+      g.c2[ax][0] = (float)(kW[0] / (hs[ax] * hs[ax]));
+      g.c1[ax][0] = 0.f;
+      for (int m = 1; m <= 4; ++m) {
+        g.c2[ax][m] = (float)(kW[m] / (hs[ax] * hs[ax]));
+        g.c1[ax][m] = (float)(kW1[m] / hs[ax]);
+      }
+    }
+    int *lz, *lzm, *ly, *lym, *lx;
+    float *sb;
+    if ((e = dalloc((void **)&lz, c->czl.size() * 4)) ||
+        (e = dalloc((void **)&lzm, c->czm.size() * 4)) ||
+        (e = dalloc((void **)&ly, c->cyl.size() * 4)) ||
+        (e = dalloc((void **)&lym, c->cym.size() * 4)) ||
+        (e = dalloc((void **)&lx, c->cxl.size() * 4)) ||
+        (e = dalloc((void **)&sb, (size_t)(g.cz + g.cy + g.cx) * 4))) {
+      free_cpml(c);
+      return e;
+    }
+    const std::vector<int> *hl[5] = {&c->czl, &c->czm, &c->cyl, &c->cym, &c->cxl};
+    int *dl[5] = {lz, lzm, ly, lym, lx};
+    for (int i = 0; i < 5; ++i)
+      if (!hl[i]->empty())
+        WAVE_TRY_CUDA(cudaMemcpy(dl[i], hl[i]->data(), hl[i]->size() * 4,
+                                 cudaMemcpyHostToDevice));
+    g.zlist = lz;
+    g.zmid = lzm;
+    g.ylist = ly;
+    g.ymid = lym;
+    g.xlist = lx;
+    g.sbuf = sb;
+    if (!c->d_nsrec) WAVE_TRY_CUDA(cudaMalloc((void **)&c->d_nsrec, sizeof(int)));
+    WAVE_TRY_CUDA(cudaMemset(c->d_nsrec, 0, sizeof(int)));
+    c->cpml = true;
+    if ((e = zero_cpml(c))) return e;
+  }
+  drop_graphs(c);  // captured graphs hold the previous step sequence
   return WAVE_OK;
 }
 
@@ -805,7 +1022,7 @@ int gradient_impl(wave_ctx *c, const wave_shot *shot, int N,
                   float *traces_out) {
   if (!c || N < 1 || nrec < 0 || K < 1 || !grad) return WAVE_EINVAL;
   if (nrec > 0 && (!rec_xyz || !data)) return WAVE_EINVAL;
-  if (c->storage != WAVE_STORAGE_F32 ||
+  if (c->storage != WAVE_STORAGE_F32 || c->cpml ||
       c->var.func != reinterpret_cast<const void *>(&wave_sweep_kernel<Cfg0>))
     return WAVE_ENOTSUP;
   cudaStream_t st = c->stream;

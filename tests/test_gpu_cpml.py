@@ -1,0 +1,214 @@
+"""GPU parity of the CPML absorbing layer against the FP64 oracle.
+
+The layer (complex-frequency-shifted CPML for the second-order equation,
+after Komatitsch and Martin 2007, which the paper's boundary follows, Sec. 2)
+adds per-axis memory variables psi, zeta in slabs of npml cells at each
+face. The CUDA path computes the points within npml + 4 cells of a face in
+separate kernels and leaves the rest to the standard sweep; these tests check
+the whole field, the traces (receivers inside and outside that shell) and
+the continuation of the memory variables across calls and graph chunks.
+
+Tolerance: the FP32 path's bar, relative L2 <= max(1e-5, 1e-7 per step):
+one step rounds at ~1e-7 relative and the error grows about linearly with
+the steps (the plain FP32 path measures 3.8e-5 after 500 steps); a wrong
+profile, sign, index or slab offset gives errors of 1e-3 or more.
+"""
+import numpy as np
+import pytest
+
+import workloads as wl
+
+pytestmark = pytest.mark.gpu
+
+
+
+def tol(nsteps):
+    return max(1e-5, 1e-7 * nsteps)
+
+
+def rel_l2(a, b):
+    a = np.asarray(a, dtype=np.float64)
+    b = np.asarray(b, dtype=np.float64)
+    nb = np.linalg.norm(b)
+    return np.linalg.norm(a - b) / (nb if nb > 0 else 1.0)
+
+
+def gpu_cpml(pkg, vel, spacing, dt, chunks, npml, R, fcps, shot, rec, u0=None, up0=None,
+             step0=0):
+    import torch
+    nz, ny, nx = vel.shape
+    solver = pkg.WaveSolver((nx, ny, nz), spacing, dt, torch.from_numpy(vel).cuda())
+    try:
+        solver.set_cpml(npml, R, fcps)
+        if u0 is not None:
+            solver.set_state(torch.from_numpy(u0).cuda(), torch.from_numpy(up0).cuda(), step0)
+        nrec = rec.shape[0]
+        r = torch.from_numpy(rec).cuda()
+        rows = []
+        for k in chunks:
+            t = torch.zeros((k, nrec), dtype=torch.float32, device="cuda")
+            solver.propagate(shot, k, r, t)
+            rows.append(t.cpu().numpy())
+        u = np.empty((nz, ny, nx), dtype=np.float32)
+        up = np.empty((nz, ny, nx), dtype=np.float32)
+        solver.get_field(0, u)
+        solver.get_field(1, up)
+        assert solver.step_count == step0 + sum(chunks)
+        solver.synchronize()
+    finally:
+        solver.close()
+    return u.astype(np.float64), up.astype(np.float64), np.concatenate(rows).astype(np.float64)
+
+
+def shell_receivers(nx, ny, nz, w):
+    """Receivers at corners, edges and faces of the layer shell, plus interior."""
+    pts = {(0, 0, 0), (nx - 1, ny - 1, nz - 1), (nx // 2, ny // 2, 0),
+           (nx // 2, 0, nz // 2), (0, ny // 2, nz // 2), (nx - 1, ny // 2, nz // 2),
+           (min(w, nx - 1), ny // 2, nz // 2), (nx // 2, ny // 2, nz // 2),
+           (max(nx - w - 1, 0), max(ny - w - 1, 0), max(nz - w - 1, 0))}
+    return np.ascontiguousarray(sorted(pts), dtype=np.int32)
+
+
+def test_layered_workload_reaches_the_layer(wave_lib, oracle_mod):
+    """64^3 layered model, npml 10, 240 steps: the wave crosses the layer."""
+    cfg = wl.CFG_SMALL
+    nx, ny, nz = cfg["shape"]
+    vel = wl.velocity_for(cfg)
+    sp = cfg["spacing"]
+    dt = cfg["cfl_fraction"] * wave_lib.wave_cfl_dt(sp, float(vel.max()))
+    rec = np.concatenate([wl.receiver_plane(nx, ny, cfg["rec_z"], cfg["rec_stride"]),
+                          shell_receivers(nx, ny, nz, 14)])
+    rec = np.ascontiguousarray(rec, dtype=np.int32)
+    shot = (*cfg["source"], cfg["f_peak"], -1.0, 1.0)
+    n = 240
+    gu, gup, gtr = gpu_cpml(wave_lib, vel, sp, dt, [n], 10, 1e-3, 15.0, shot, rec)
+    ou, oup, _, _, otr = oracle_mod.propagate_cpml(vel, sp, dt, n, 10, R=1e-3, fcps=15.0,
+                                                   source=shot, receivers=rec)
+    assert np.linalg.norm(ou) > 0
+    assert rel_l2(gu, ou) <= tol(n)
+    assert rel_l2(gup, oup) <= tol(n)
+    assert rel_l2(gtr, otr) <= tol(n)
+    # the layer's own effect is resolved far below its size
+    pu, _, ptr = oracle_mod.propagate(vel, sp, dt, n, source=shot, receivers=rec)
+    assert rel_l2(gu, ou) <= 1e-3 * rel_l2(pu, ou)
+    assert rel_l2(gtr, otr) <= 1e-3 * rel_l2(ptr, otr)
+
+
+CASES = [
+    # shape, spacing, npml, chunks, source (in the shell or not)
+    ((70, 37, 23), (10.0, 12.0, 8.0), 5, [7, 40, 1], (2, 3, 20)),
+    ((33, 65, 17), (10.0, 10.0, 13.0), 8, [33], (16, 30, 8)),     # shell is all of z
+    ((9, 8, 2), (9.0, 10.0, 11.0), 1, [5, 3], (0, 7, 1)),          # tiny grid
+    ((131, 19, 40), (12.0, 9.0, 10.0), 6, [34, 30], (130, 0, 39)),  # source at a corner
+]
+
+
+@pytest.mark.parametrize("shape,spacing,npml,chunks,src", CASES)
+def test_ragged_random_state(wave_lib, oracle_mod, shape, spacing, npml, chunks, src):
+    nx, ny, nz = shape
+    rng = np.random.default_rng(nx * 7919 + ny * 31 + nz + npml)
+    vel = rng.uniform(1500.0, 4500.0, size=(nz, ny, nx)).astype(np.float32)
+    u0, up0 = wl.random_state((nz, ny, nx), seed=nx + 2 * ny + 3 * nz)
+    dt = 0.45 * wave_lib.wave_cfl_dt(spacing, float(vel.max()))
+    rec = np.concatenate([wl.random_receivers(nx, ny, nz, 23, seed=5),
+                          shell_receivers(nx, ny, nz, npml + 4)])
+    rec = np.ascontiguousarray(rec, dtype=np.int32)
+    shot = (*src, 15.0, 0.01, 1e-3)
+    fc = 20.0
+    gu, gup, gtr = gpu_cpml(wave_lib, vel, spacing, dt, chunks, npml, 1e-4, fc, shot, rec,
+                            u0, up0, step0=3)
+    ou, oup, _, _, otr = oracle_mod.propagate_cpml(
+        vel, spacing, dt, sum(chunks), npml, R=1e-4, fcps=fc, u=u0, u_prev=up0, step0=3,
+        source=shot, receivers=rec)
+    n = sum(chunks)
+    assert rel_l2(gu, ou) <= tol(n)
+    assert rel_l2(gup, oup) <= tol(n)
+    assert rel_l2(gtr, otr) <= tol(n)
+
+
+def test_layer_absorbs_compared_with_the_zero_halo(wave_lib):
+    """After the wavelet has crossed the grid, the field left with the layer is
+    a small fraction of the field left with the bare zero (reflecting) halo."""
+    import torch
+    n = 48
+    vel = np.full((n, n, n), 2000.0, dtype=np.float32)
+    sp = (10.0, 10.0, 10.0)
+    dt = 0.5 * wave_lib.wave_cfl_dt(sp, 2000.0)
+    shot = (24, 24, 24, 20.0, -1.0, 1.0)
+    out = []
+    for npml in (0, 12):
+        s = wave_lib.WaveSolver((n, n, n), sp, dt, torch.from_numpy(vel).cuda())
+        try:
+            s.set_cpml(npml, 1e-3, 20.0)
+            s.propagate(shot, 500)
+            u = np.empty((n, n, n), dtype=np.float32)
+            s.get_field(0, u)
+        finally:
+            s.close()
+        out.append(np.linalg.norm(u[12:-12, 12:-12, 12:-12]))
+    assert out[1] < 1e-3 * out[0]
+
+
+def test_switching_off_and_reset(wave_lib):
+    """npml 0 gives the plain path bitwise; reset clears the memory variables."""
+    import torch
+    nx, ny, nz = 40, 30, 20
+    vel = wl.layered3(nx, ny, nz)
+    sp = (10.0, 10.0, 10.0)
+    dt = 0.5 * wave_lib.wave_cfl_dt(sp, 3500.0)
+    rec = torch.from_numpy(wl.receiver_plane(nx, ny, 2, 3)).cuda()
+    shot = (20, 15, 3, 15.0, -1.0, 1.0)
+
+    def run(s, k=70):
+        t = torch.zeros((k, rec.shape[0]), device="cuda")
+        s.propagate(shot, k, rec, t)
+        return t.cpu().numpy()
+
+    plain = wave_lib.WaveSolver((nx, ny, nz), sp, dt, torch.from_numpy(vel).cuda())
+    s = wave_lib.WaveSolver((nx, ny, nz), sp, dt, torch.from_numpy(vel).cuda())
+    try:
+        ref = run(plain)
+        s.set_cpml(6)
+        a = run(s)
+        s.reset()
+        b = run(s)
+        assert np.array_equal(a, b)
+        assert not np.array_equal(a, ref)
+        s.set_cpml(0)
+        s.reset()
+        assert np.array_equal(run(s), ref)
+    finally:
+        plain.close()
+        s.close()
+
+
+def test_invalid_and_unsupported(wave_lib):
+    import torch
+    E = wave_lib.WaveError
+    nx, ny, nz = 24, 20, 16
+    vel = torch.from_numpy(wl.layered3(nx, ny, nz)).cuda()
+    sp = (10.0, 10.0, 10.0)
+    dt = 0.5 * wave_lib.wave_cfl_dt(sp, 3500.0)
+    s = wave_lib.WaveSolver((nx, ny, nz), sp, dt, vel)
+    try:
+        for args in ((-1, 1e-3, 15.0), (9, 1e-3, 15.0), (4, 0.0, 15.0), (4, 1.0, 15.0),
+                     (4, 1e-3, -1.0), (4, float("nan"), 15.0)):
+            with pytest.raises(E) as ei:
+                s.set_cpml(*args)
+            assert ei.value.code == -1
+        s.set_cpml(8, 1e-3, 15.0)  # 2 npml == nz: allowed
+        rec = torch.zeros((1, 3), dtype=torch.int32, device="cuda")
+        obs = torch.zeros((5, 1), device="cuda")
+        g = torch.zeros((nz, ny, nx), device="cuda")
+        with pytest.raises(E) as ei:
+            s.gradient((5, 5, 5, 15.0, -1.0, 1.0), 5, rec, obs, g, 2)
+        assert ei.value.code == -8
+    finally:
+        s.close()
+    h = wave_lib.WaveSolver((nx, ny, nz), sp, dt, vel, storage=2)
+    try:
+        with pytest.raises(E) as ei:
+            h.set_cpml(4)
+        assert ei.value.code == -8
+    finally:
+        h.close()
