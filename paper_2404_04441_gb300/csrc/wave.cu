@@ -140,10 +140,9 @@ struct wave_ctx {
   bool cpml = false;
   CpmlGeom cg{};
   std::vector<void *> cpml_mem;
-  std::vector<int> czl, czm, cyl, cym, cxl;  // shell lists (host copies)
-  DeviceBuf srec;            // receivers in the shell: {shell index, id}
+  DeviceBuf srec;            // receivers within w of a face: {x, y, z, id}
   int *d_nsrec = nullptr;    // their count (device: graphs stay valid)
-  std::vector<int2> h_srec;
+  std::vector<int4> h_srec;
   int cpml_nsrec_host = 0;
 };
 
@@ -196,17 +195,17 @@ void enqueue_step(wave_ctx *c, cudaStream_t st, int cur, int koff) {
   SweepArgs a = c->args;
   a.unext = c->buf[cur ^ 1];
   a.koff = koff;
-  const float *u = (const float *)c->buf[cur];
-  if (c->cpml) {
-    cpml_psi_kernel<<<c->sms * 4, 256, 0, st>>>(c->cg, u);
-    cpml_shell_kernel<<<c->sms * 4, 256, 0, st>>>(
-        c->cg, u, (const float *)c->buf[cur ^ 1], c->c, c->d_desc, koff);
-  }
   c->var.launch(c->grid, st, c->tm_halo[cur], c->tm_tile[cur ^ 1], c->tm_c, a);
-  if (c->cpml)
-    cpml_commit_kernel<<<c->sms * 4, 256, 0, st>>>(
-        c->cg, (float *)c->buf[cur ^ 1], c->d_desc, (const int2 *)c->srec.p,
-        c->d_nsrec, koff);
+  if (c->cpml) {
+    const float *u = (const float *)c->buf[cur];
+    float *un = (float *)c->buf[cur ^ 1];
+    const CpmlGeom &g = c->cg;
+    cpml_x_kernel<<<dim3((c->ny + 7) / 8, c->nz), 256, 0, st>>>(g, u, un, c->c);
+    cpml_line_kernel<1><<<dim3((c->nx + 127) / 128, c->nz), 128, 0, st>>>(g, u, un, c->c);
+    cpml_line_kernel<2><<<dim3((c->nx + 127) / 128, c->ny), 128, 0, st>>>(g, u, un, c->c);
+    cpml_record_kernel<<<c->sms, 256, 0, st>>>(g, un, c->d_desc,
+                                               (const int4 *)c->srec.p, c->d_nsrec, koff);
+  }
 }
 
 void drop_graphs(wave_ctx *c) {
@@ -236,23 +235,11 @@ int zero_cpml(wave_ctx *c) {
   return WAVE_OK;
 }
 
-// Compact index of a point in the CPML shell (enumeration of cpml.cuh), or
-// -1 when the point is not in the shell.
-long long cpml_shell_index(const wave_ctx *c, int x, int y, int z) {
-  auto pos = [](const std::vector<int> &v, int val) -> long long {
-    auto it = std::lower_bound(v.begin(), v.end(), val);
-    return (it != v.end() && *it == val) ? (long long)(it - v.begin()) : -1;
-  };
-  const CpmlGeom &g = c->cg;
-  long long i = pos(c->czl, z);
-  if (i >= 0) return i * c->nx * c->ny + (long long)y * c->nx + x;
-  const long long izm = pos(c->czm, z);
-  i = pos(c->cyl, y);
-  if (i >= 0) return g.cz + izm * g.nyl * c->nx + i * c->nx + x;
-  const long long iym = pos(c->cym, y);
-  i = pos(c->cxl, x);
-  if (i >= 0) return g.cz + g.cy + izm * g.nym * g.nxl + iym * g.nxl + i;
-  return -1;
+// A point whose update carries a layer term: within w = npml + 4 of a face.
+bool cpml_in_shell(const wave_ctx *c, int x, int y, int z) {
+  const int w = c->cg.w;
+  return x < w || x >= c->nx - w || y < w || y >= c->ny - w || z < w ||
+         z >= c->nz - w;
 }
 
 int build_graph(wave_ctx *c, int parity) {
@@ -592,18 +579,16 @@ int wave_propagate(wave_ctx *c, const wave_shot *shot, int nsteps,
   if (c->cpml) {
     // receivers inside the CPML shell are recorded from the shell values
     c->h_srec.clear();
-    for (int r = 0; r < nrec; ++r) {
-      const long long t = cpml_shell_index(c, hrec[3 * r], hrec[3 * r + 1],
-                                           hrec[3 * r + 2]);
-      if (t >= 0) c->h_srec.push_back(make_int2((int)t, r));
-    }
+    for (int r = 0; r < nrec; ++r)
+      if (cpml_in_shell(c, hrec[3 * r], hrec[3 * r + 1], hrec[3 * r + 2]))
+        c->h_srec.push_back(make_int4(hrec[3 * r], hrec[3 * r + 1], hrec[3 * r + 2], r));
     const int ns = (int)c->h_srec.size();
     if (ns > 0) {
       void *old = c->srec.p;
-      if ((s = ensure(c->srec, (size_t)ns * sizeof(int2), st))) return s;
+      if ((s = ensure(c->srec, (size_t)ns * sizeof(int4), st))) return s;
       if (c->srec.p != old) drop_graphs(c);  // graphs hold the list's address
       WAVE_TRY_CUDA(cudaMemcpyAsync(c->srec.p, c->h_srec.data(),
-                                    (size_t)ns * sizeof(int2),
+                                    (size_t)ns * sizeof(int4),
                                     cudaMemcpyHostToDevice, st));
     }
     c->cpml_nsrec_host = ns;
@@ -803,7 +788,9 @@ int wave_set_cpml(wave_ctx *c, int npml, double R, double f_cps) {
     if (2 * npml > std::min(c->nx, std::min(c->ny, c->nz)) || !(R > 0.0 && R < 1.0) ||
         !(f_cps >= 0.0) || !std::isfinite(f_cps))
       return WAVE_EINVAL;
-    if (c->storage != WAVE_STORAGE_F32) return WAVE_ENOTSUP;
+    // FP32 fields only; the axis kernels index one grid row of blocks per y or z.
+    if (c->storage != WAVE_STORAGE_F32 || c->ny > 65535 || c->nz > 65535)
+      return WAVE_ENOTSUP;
     WAVE_TRY_CUDA(cudaStreamSynchronize(c->stream));
     free_cpml(c);
     CpmlGeom &g = c->cg;
@@ -813,24 +800,6 @@ int wave_set_cpml(wave_ctx *c, int npml, double R, double f_cps) {
     g.px = c->px;
     g.npml = npml;
     g.w = npml + 4;
-    auto lists = [&](int n, std::vector<int> &shell, std::vector<int> &mid) {
-      shell.clear();
-      mid.clear();
-      for (int i = 0; i < n; ++i)
-        (i < g.w || i >= n - g.w ? shell : mid).push_back(i);
-    };
-    std::vector<int> xmid;
-    lists(c->nz, c->czl, c->czm);
-    lists(c->ny, c->cyl, c->cym);
-    lists(c->nx, c->cxl, xmid);
-    g.nzl = (int)c->czl.size();
-    g.nzm = (int)c->czm.size();
-    g.nyl = (int)c->cyl.size();
-    g.nym = (int)c->cym.size();
-    g.nxl = (int)c->cxl.size();
-    g.cz = (long long)g.nzl * c->nx * c->ny;
-    g.cy = (long long)g.nzm * g.nyl * c->nx;
-    g.cx = (long long)g.nzm * g.nym * g.nxl;
     const size_t sl[3] = {2ull * npml * c->ny * c->nz, 2ull * npml * c->nz * c->nx,
                           2ull * npml * c->ny * c->nx};
     auto dalloc = [&](void **p, size_t bytes) -> int {
@@ -880,29 +849,6 @@ int wave_set_cpml(wave_ctx *c, int npml, double R, double f_cps) {
         g.c1[ax][m] = (float)(kW1[m] / hs[ax]);
       }
     }
-    int *lz, *lzm, *ly, *lym, *lx;
-    float *sb;
-    if ((e = dalloc((void **)&lz, c->czl.size() * 4)) ||
-        (e = dalloc((void **)&lzm, c->czm.size() * 4)) ||
-        (e = dalloc((void **)&ly, c->cyl.size() * 4)) ||
-        (e = dalloc((void **)&lym, c->cym.size() * 4)) ||
-        (e = dalloc((void **)&lx, c->cxl.size() * 4)) ||
-        (e = dalloc((void **)&sb, (size_t)(g.cz + g.cy + g.cx) * 4))) {
-      free_cpml(c);
-      return e;
-    }
-    const std::vector<int> *hl[5] = {&c->czl, &c->czm, &c->cyl, &c->cym, &c->cxl};
-    int *dl[5] = {lz, lzm, ly, lym, lx};
-    for (int i = 0; i < 5; ++i)
-      if (!hl[i]->empty())
-        WAVE_TRY_CUDA(cudaMemcpy(dl[i], hl[i]->data(), hl[i]->size() * 4,
-                                 cudaMemcpyHostToDevice));
-    g.zlist = lz;
-    g.zmid = lzm;
-    g.ylist = ly;
-    g.ymid = lym;
-    g.xlist = lx;
-    g.sbuf = sb;
     if (!c->d_nsrec) WAVE_TRY_CUDA(cudaMalloc((void **)&c->d_nsrec, sizeof(int)));
     WAVE_TRY_CUDA(cudaMemset(c->d_nsrec, 0, sizeof(int)));
     c->cpml = true;
