@@ -173,8 +173,9 @@ int wave_reset(wave_ctx *ctx);
  *               1 <= npml and 2 npml <= nx, ny, nz
  *   reflection  target reflection coefficient, 0 < reflection < 1
  *   f_cps       frequency shift (Hz, >= 0), typically the source's peak
- * FP32 storage and ny, nz <= 65535 only (WAVE_ENOTSUP otherwise). The layer's memory variables
- * start at zero here and are zeroed by wave_reset and wave_set_state. The
+ * FP32 storage and ny, nz <= 65535 only (WAVE_ENOTSUP otherwise). The
+ * layer's memory variables start at zero here and are zeroed by wave_reset
+ * and wave_set_state. The
  * source and receivers may lie in the layer. wave_adjoint / wave_gradient
  * do not support the layer (WAVE_ENOTSUP).
  */

@@ -14,12 +14,12 @@
 //     C * sum_a ( D1_a psi_a^n + zeta_a^n ),
 // and the axis-a term is non-zero only within w = npml + 4 cells of the two
 // faces normal to a. So the sweep runs unchanged over the whole grid, and
-// afterwards one kernel per axis walks every line along that axis through
-// its two end segments of w cells (one segment of the whole line when the
-// two would overlap): it updates psi_a and zeta_a from u^n (which the sweep
-// does not overwrite) and adds the axis term to u^{n+1}. The three axis
-// kernels run one after another, so corner points are updated by each axis
-// in turn with no race. Receivers within w of a face are then re-recorded.
+// afterwards one kernel per axis walks every line along that axis through its
+// two end segments of w cells (one segment of the whole line when the two would
+// overlap): it updates psi_a and zeta_a from u^n (which the sweep does not
+// overwrite) and adds the axis term to u^{n+1}. The three axis kernels run
+// one after another, so corner points are updated by each axis in turn with
+// no race. Receivers within w of a face are then re-recorded.
 #pragma once
 
 #include <cstdint>
@@ -37,9 +37,10 @@ struct CpmlGeom {
   float c1[3][5];  // D1 weights / h_a (index 1..4)
 };
 
-// Slab storage: the x slabs hold ((z ny + y) 2npml + cell), the y slabs
-// ((cell nz + z) nx + x), the z slabs ((cell ny + y) nx + x), where cell in
-// [0, 2 npml) counts the low slab's npml cells, then the high slab's.
+// Slab storage, cell-major: cell in [0, 2 npml) counts the low slab's npml
+// cells, then the high slab's; the x slabs hold ((cell nz + z) ny + y), the y
+// slabs ((cell nz + z) nx + x), the z slabs ((cell ny + y) nx + x), so that
+// adjacent lines (adjacent threads) are adjacent in memory.
 __device__ __forceinline__ bool cpml_in_slab(int i, int n, int npml) {
   return i < npml || i >= n - npml;
 }
@@ -48,130 +49,173 @@ __device__ __forceinline__ int cpml_cell(int i, int n, int npml) {
   return i < npml ? i : i - (n - 2 * npml);
 }
 
-// y (AX = 1) and z (AX = 2): one thread per line, x across the threads of a
-// warp (coalesced), walking the line with register windows of u^n
-// (positions i-4 .. i+8) and psi^n (i-4 .. i+4); psi(i+4) is computed as it
-// enters the window, so each slab cell's psi is computed once per step.
+constexpr int kCpmlChunk = 4;  // positions per batch of loads
+
+// Four consecutive values of an x row from position p (p a multiple of 4,
+// the row 16-byte aligned with its padding up to a multiple of 4 in
+// bounds); positions outside [0, n) read as zero.
+__device__ __forceinline__ void cpml_row4(const float *row, int p, int n, float *v) {
+  if (p < 0 || p >= n) {
+    v[0] = v[1] = v[2] = v[3] = 0.f;
+    return;
+  }
+  const float4 t = *reinterpret_cast<const float4 *>(row + p);
+  v[0] = t.x;
+  v[1] = p + 1 < n ? t.y : 0.f;
+  v[2] = p + 2 < n ? t.z : 0.f;
+  v[3] = p + 3 < n ? t.w : 0.f;
+}
+
+// One kernel per axis AX (0 = x, 1 = y, 2 = z): one thread per line along
+// AX, adjacent lines (adjacent y for x, adjacent x for y and z) in adjacent
+// threads. A thread walks its line's end segments, positions i0 .. i1-1
+// ([0, w) and [n - w, n), or [0, n) when they would overlap), with register
+// windows of u^n (positions i-4 .. i+F+7) and psi^n (i-4 .. i+F+3), F
+// positions per batch: at position i it computes psi(k), k = i + 4, in the
+// slab cells of the segment's own range i0 .. i1 + 3 (exactly the segment's
+// slab cells, so each is updated once per step), then, for i0 <= i < i1,
+// zeta^n(i) in the slab cells and u^{n+1}(i) += C (D1 psi^n + zeta^n). The
+// walk starts at or before i0 - 4, where the psi used by the corrections is
+// zero (before the grid, or between the slabs). The loads of the next batch
+// are in flight while the current one is computed. x rows are walked in
+// batches aligned to 4 positions and moved as float4 (a row is contiguous
+// in one thread); y and z lines are coalesced across the threads.
 template <int AX>
 __global__ void __launch_bounds__(128)
     cpml_line_kernel(CpmlGeom g, const float *__restrict__ u,
                      float *__restrict__ unext, const float *__restrict__ c) {
-  const int x = blockIdx.x * blockDim.x + threadIdx.x;
-  const int o = blockIdx.y;  // z for the y lines, y for the z lines
-  if (x >= g.nx) return;
-  const int n = AX == 1 ? g.ny : g.nz;
-  const long long us = AX == 1 ? (long long)g.px : (long long)g.ny * g.px;
-  const long long ub = AX == 1 ? (long long)o * g.ny * g.px + x
-                               : (long long)o * g.px + x;
-  const long long ss = AX == 1 ? (long long)g.nz * g.nx : (long long)g.ny * g.nx;
-  float *psi = g.psi[AX] + (long long)o * g.nx + x;
-  float *zeta = g.zeta[AX] + (long long)o * g.nx + x;
+  constexpr int F = kCpmlChunk;
+  const int t = blockIdx.x * blockDim.x + threadIdx.x;
+  const int q = blockIdx.y;  // z for x and y lines, y for z lines
+  int n;
+  long long ub, us, sb, ss;  // u offset and stride; slab offset and stride
+  if (AX == 0) {
+    if (t >= g.ny) return;
+    n = g.nx;
+    ub = ((long long)q * g.ny + t) * g.px;
+    us = 1;
+    sb = (long long)q * g.ny + t;
+    ss = (long long)g.nz * g.ny;
+  } else {
+    if (t >= g.nx) return;
+    n = AX == 1 ? g.ny : g.nz;
+    ub = AX == 1 ? (long long)q * g.ny * g.px + t : (long long)q * g.px + t;
+    us = AX == 1 ? (long long)g.px : (long long)g.ny * g.px;
+    sb = (long long)q * g.nx + t;
+    ss = AX == 1 ? (long long)g.nz * g.nx : (long long)g.ny * g.nx;
+  }
+  const float *__restrict__ ul = u + ub;
+  const float *__restrict__ cl = c + ub;
+  float *__restrict__ nl = unext + ub;
+  float *__restrict__ psi = g.psi[AX] + sb;
+  float *__restrict__ zeta = g.zeta[AX] + sb;
   const float *bp = g.bprof[AX];
   const float *ap = g.aprof[AX];
   const int npml = g.npml, w = g.w;
-  const int nseg = n >= 2 * w ? 2 : 1;
-  for (int s = 0; s < nseg; ++s) {
-    const int i0 = (nseg == 2 && s == 1) ? n - w : 0;
-    const int i1 = nseg == 1 ? n : (s == 0 ? w : n);
-    // Start 4 positions early so psi(i0 .. i0+3) enter the window; psi at
-    // i0-8 .. i0-1 is zero (before the grid, or between the slabs).
-    int i = i0 - 4;
-    float U[13], P[9];
+  const bool two = n >= 2 * w;
+  for (int sg = 0; sg < (two ? 2 : 1); ++sg) {
+    const int i0 = (two && sg == 1) ? n - w : 0;
+    const int i1 = two ? (sg == 0 ? w : n) : n;
+    // Batch of positions i .. i+F-1: u(i+8+f), psi^{n-1}(i+4+f), zeta^{n-1},
+    // C and u^{n+1} at i+f.
+    float nw[F], npp[F], nzp[F], ncc[F], nun[F];
+    auto load = [&](int i) {
+      if (AX == 0) {
+        cpml_row4(ul, i + 8, n, nw);
+        if (i + F > i0 && i < i1) {
+          cpml_row4(cl, i, n, ncc);
+          cpml_row4(nl, i, n, nun);
+        } else {
 #pragma unroll
-    for (int m = 0; m < 13; ++m) {
-      const int k = i - 4 + m;
-      U[m] = (k >= 0 && k < n) ? u[ub + k * us] : 0.f;
+          for (int f = 0; f < F; ++f) ncc[f] = nun[f] = 0.f;
+        }
+      }
+#pragma unroll
+      for (int f = 0; f < F; ++f) {
+        const int k = i + 4 + f;
+        npp[f] = (k >= 0 && k < n && k < i1 + 4 && cpml_in_slab(k, n, npml))
+                     ? psi[cpml_cell(k, n, npml) * ss] : 0.f;
+        const int p = i + f;
+        const bool act = p >= i0 && p < i1;
+        nzp[f] = (act && cpml_in_slab(p, n, npml)) ? zeta[cpml_cell(p, n, npml) * ss] : 0.f;
+        if (AX != 0) {
+          const int kw = i + 8 + f;
+          nw[f] = (kw < n) ? ul[kw * us] : 0.f;
+          ncc[f] = act ? cl[p * us] : 0.f;
+          nun[f] = act ? nl[p * us] : 0.f;
+        }
+      }
+    };
+    float W[12 + F];  // W[m] = u(i - 4 + m)
+    float P[8 + F];   // P[m] = psi(i - 4 + m)
+    int i = AX == 0 ? ((i0 - 4) & ~3) : i0 - 4;
+    if (AX == 0) {
+#pragma unroll
+      for (int m = 0; m < 12; m += 4) cpml_row4(ul, i - 4 + m, n, W + m);
+    } else {
+#pragma unroll
+      for (int m = 0; m < 12; ++m) {
+        const int k = i - 4 + m;
+        W[m] = (k >= 0 && k < n) ? ul[k * us] : 0.f;
+      }
     }
 #pragma unroll
-    for (int m = 0; m < 9; ++m) P[m] = 0.f;
-    for (; i < i1; ++i) {
-      const int k = i + 4;  // psi(k) from U(k-4 .. k+4) = U[4 .. 12]
-      float pk = 0.f;
-      if (k < n && cpml_in_slab(k, n, npml)) {
-        float d1 = 0.f;
+    for (int m = 0; m < 8; ++m) P[m] = 0.f;
+    load(i);
+    for (; i < i1; i += F) {
+      float pp[F], zp[F], cc[F], un[F];
 #pragma unroll
-        for (int m = 1; m <= kR; ++m) d1 = fmaf(g.c1[AX][m], U[8 + m] - U[8 - m], d1);
-        float *pp = psi + (long long)cpml_cell(k, n, npml) * ss;
-        pk = fmaf(bp[k], *pp, ap[k] * d1);
-        *pp = pk;
+      for (int f = 0; f < F; ++f) {
+        W[12 + f] = nw[f];
+        pp[f] = npp[f];
+        zp[f] = nzp[f];
+        cc[f] = ncc[f];
+        un[f] = nun[f];
       }
-      P[8] = pk;
-      if (i >= i0) {
+      if (i + F < i1) load(i + F);
+#pragma unroll
+      for (int f = 0; f < F; ++f) {  // psi(i + 4 + f) from u(i + f .. i + f + 8)
+        const int k = i + 4 + f;
+        float v = 0.f;
+        if (k >= 0 && k < n && k < i1 + 4 && cpml_in_slab(k, n, npml)) {
+          float d1 = 0.f;
+#pragma unroll
+          for (int m = 1; m <= kR; ++m) d1 = fmaf(g.c1[AX][m], W[8 + f + m] - W[8 + f - m], d1);
+          v = fmaf(__ldg(bp + k), pp[f], __ldg(ap + k) * d1);
+          psi[cpml_cell(k, n, npml) * ss] = v;
+        }
+        P[8 + f] = v;
+      }
+      float out[F];
+#pragma unroll
+      for (int f = 0; f < F; ++f) {  // u^{n+1}(i + f) += C (D1 psi + zeta)
+        const int p = i + f;
+        out[f] = un[f];
+        if (p < i0 || p >= i1) continue;
         float d1p = 0.f;
 #pragma unroll
-        for (int m = 1; m <= kR; ++m) d1p = fmaf(g.c1[AX][m], P[4 + m] - P[4 - m], d1p);
+        for (int m = 1; m <= kR; ++m) d1p = fmaf(g.c1[AX][m], P[4 + f + m] - P[4 + f - m], d1p);
         float corr = d1p;
-        if (cpml_in_slab(i, n, npml)) {
-          float d2 = g.c2[AX][0] * U[4];
+        if (cpml_in_slab(p, n, npml)) {
+          float d2 = g.c2[AX][0] * W[4 + f];
 #pragma unroll
-          for (int m = 1; m <= kR; ++m) d2 = fmaf(g.c2[AX][m], U[4 + m] + U[4 - m], d2);
-          float *zp = zeta + (long long)cpml_cell(i, n, npml) * ss;
-          const float zt = fmaf(bp[i], *zp, ap[i] * (d2 + d1p));
-          *zp = zt;
+          for (int m = 1; m <= kR; ++m) d2 = fmaf(g.c2[AX][m], W[4 + f + m] + W[4 + f - m], d2);
+          const float zt = fmaf(__ldg(bp + p), zp[f], __ldg(ap + p) * (d2 + d1p));
+          zeta[cpml_cell(p, n, npml) * ss] = zt;
           corr += zt;
         }
-        const long long off = ub + i * us;
-        unext[off] = fmaf(c[off], corr, unext[off]);
+        out[f] = fmaf(cc[f], corr, un[f]);
+        if (AX != 0) nl[p * us] = out[f];
       }
+      // x: the whole aligned batch in one store (positions outside the
+      // segment keep the value just read; this thread owns the row)
+      if (AX == 0 && i + F > i0 && i < i1)
+        *reinterpret_cast<float4 *>(nl + i) = make_float4(out[0], out[1], out[2], out[3]);
 #pragma unroll
-      for (int m = 0; m < 12; ++m) U[m] = U[m + 1];
-      const int kn = i + 9;
-      U[12] = (kn < n) ? u[ub + kn * us] : 0.f;
+      for (int m = 0; m < 12; ++m) W[m] = W[m + F];
 #pragma unroll
-      for (int m = 0; m < 8; ++m) P[m] = P[m + 1];
+      for (int m = 0; m < 8; ++m) P[m] = P[m + F];
     }
-  }
-}
-
-// x: one warp per row (y, z), lanes across the row's cells; psi of the row's
-// slab cells first, then (after the warp's stores are visible) the
-// corrections of its end segments.
-__global__ void __launch_bounds__(256)
-    cpml_x_kernel(CpmlGeom g, const float *__restrict__ u,
-                  float *__restrict__ unext, const float *__restrict__ c) {
-  const int lane = threadIdx.x & 31;
-  const int y = blockIdx.x * 8 + (threadIdx.x >> 5);
-  const int z = blockIdx.y;
-  if (y >= g.ny) return;
-  const int n = g.nx, npml = g.npml, w = g.w;
-  const long long row = ((long long)z * g.ny + y) * g.px;
-  const float *ur = u + row;
-  const float *cr = c + row;
-  float *unr = unext + row;
-  float *psi = g.psi[0] + ((long long)z * g.ny + y) * (2 * npml);
-  float *zeta = g.zeta[0] + ((long long)z * g.ny + y) * (2 * npml);
-  const float *bp = g.bprof[0];
-  const float *ap = g.aprof[0];
-  auto U = [&](int k) { return (k >= 0 && k < n) ? ur[k] : 0.f; };
-  for (int j = lane; j < 2 * npml; j += 32) {
-    const int i = j < npml ? j : n - 2 * npml + j;
-    float d1 = 0.f;
-#pragma unroll
-    for (int m = 1; m <= kR; ++m) d1 = fmaf(g.c1[0][m], U(i + m) - U(i - m), d1);
-    psi[j] = fmaf(bp[i], psi[j], ap[i] * d1);
-  }
-  __syncwarp();
-  auto P = [&](int k) {
-    return (k >= 0 && k < n && cpml_in_slab(k, n, npml)) ? psi[cpml_cell(k, n, npml)] : 0.f;
-  };
-  const bool two = n >= 2 * w;
-  const int ncorr = two ? 2 * w : n;
-  for (int q = lane; q < ncorr; q += 32) {
-    const int i = (two && q >= w) ? n - 2 * w + q : q;
-    float d1p = 0.f;
-#pragma unroll
-    for (int m = 1; m <= kR; ++m) d1p = fmaf(g.c1[0][m], P(i + m) - P(i - m), d1p);
-    float corr = d1p;
-    if (cpml_in_slab(i, n, npml)) {
-      float d2 = g.c2[0][0] * ur[i];
-#pragma unroll
-      for (int m = 1; m <= kR; ++m) d2 = fmaf(g.c2[0][m], U(i + m) + U(i - m), d2);
-      float *zp = zeta + cpml_cell(i, n, npml);
-      const float zt = fmaf(bp[i], *zp, ap[i] * (d2 + d1p));
-      *zp = zt;
-      corr += zt;
-    }
-    unr[i] = fmaf(cr[i], corr, unr[i]);
   }
 }
 

@@ -200,7 +200,7 @@ void enqueue_step(wave_ctx *c, cudaStream_t st, int cur, int koff) {
     const float *u = (const float *)c->buf[cur];
     float *un = (float *)c->buf[cur ^ 1];
     const CpmlGeom &g = c->cg;
-    cpml_x_kernel<<<dim3((c->ny + 7) / 8, c->nz), 256, 0, st>>>(g, u, un, c->c);
+    cpml_line_kernel<0><<<dim3((c->ny + 127) / 128, c->nz), 128, 0, st>>>(g, u, un, c->c);
     cpml_line_kernel<1><<<dim3((c->nx + 127) / 128, c->nz), 128, 0, st>>>(g, u, un, c->c);
     cpml_line_kernel<2><<<dim3((c->nx + 127) / 128, c->ny), 128, 0, st>>>(g, u, un, c->c);
     cpml_record_kernel<<<c->sms, 256, 0, st>>>(g, un, c->d_desc,
