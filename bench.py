@@ -358,6 +358,56 @@ def gradient_workload(gw, torch, cfg=wl.CFG_GRAD):
             + cfg["ckpt_every"] + 3}
 
 
+def cpml_bytes_per_step(shape, npml):
+    """Algorithmic DRAM bytes of one step with the CPML layer: the sweep's
+    16 B per point, plus per axis a and per line along a, at the 2 w = 2
+    (npml + 4) segment points u^n, C and u^{n+1} read and u^{n+1} written
+    (16 B) and at the 2 npml slab cells psi and zeta read and written (16 B)."""
+    nx, ny, nz = shape
+    npts = nx * ny * nz
+    w = npml + 4
+    lines = npts / nx + npts / ny + npts / nz
+    return BYTES_PER_POINT * npts + 16 * (2 * w + 2 * npml) * lines
+
+
+def cpml_workload(gw, torch, cfg, vel_d, dt, steps, peak_gbs, plain_ms):
+    """The same grid and model stepped with the CPML layer at all six faces
+    (npml 8 and 16, R = 1e-3, f_cps = f_peak); source and receiver plane
+    moved below the top layer."""
+    nx, ny, nz = cfg["shape"]
+    npts = nx * ny * nz
+    out = {}
+    for npml in (8, 16):
+        rec = torch.from_numpy(wl.receiver_plane(nx, ny, npml + 8, cfg["rec_stride"])).cuda()
+        shot = (cfg["source"][0], cfg["source"][1], npml + 10, cfg["f_peak"], -1.0, 1.0)
+        s = gw.WaveSolver((nx, ny, nz), cfg["spacing"], dt, vel_d)
+        s.set_cpml(npml, 1e-3, cfg["f_peak"])
+        tr = torch.empty((steps, rec.shape[0]), device="cuda")
+        s.propagate(shot, min(steps, 64), rec, tr)
+        s.reset()
+        torch.cuda.synchronize()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record()
+        s.propagate(shot, steps, rec, tr)
+        e1.record()
+        e1.synchronize()
+        s.synchronize()
+        ms = e0.elapsed_time(e1) / steps
+        ok = bool(torch.isfinite(tr).all().item())
+        s.close()
+        b = cpml_bytes_per_step((nx, ny, nz), npml)
+        ach = b / (ms * 1e-3) / 1e9
+        out["npml%d" % npml] = {
+            "value": npts / (ms * 1e-3) / 1e9, "unit": "Gpts/s", "ms_per_step": ms,
+            "steps": steps, "vs_plain_step": ms / plain_ms, "traces_finite": ok,
+            "roofline": {"bound": "hbm", "achieved": ach, "peak": peak_gbs,
+                         "unit": "GB/s", "frac": ach / peak_gbs,
+                         "algorithmic_bytes_per_step": b,
+                         "launches_per_step": "sweep + 3 axis kernels + shell receivers"}}
+    return out
+
+
 def run_reference(args, cfg):
     """The reference arm: the FP64 CPU oracle on this machine's host cores."""
     rank, world, _ = dist_env()
@@ -425,6 +475,8 @@ def main():
     ap.add_argument("--serve-requests", type=int, default=wl.SERVE_STREAM["n"])
     ap.add_argument("--no-gradient", action="store_true",
                     help="skip the adjoint-gradient workload")
+    ap.add_argument("--no-cpml", action="store_true",
+                    help="skip the CPML absorbing-layer measurement")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
     cfg = WORKLOADS[args.workload]
@@ -572,6 +624,10 @@ def main():
     if not args.no_gradient:
         gradient = gradient_workload(gw, torch)
 
+    cpml = None
+    if not args.no_cpml:
+        cpml = cpml_workload(gw, torch, cfg, vel_d, dt, min(K, 200), peaks["hbm_gbs"], ms / K)
+
     cpu = None
     if rank == 0 and not args.no_cpu_baseline:
         g, cores, sample, el = oracle_sample(vel, cfg, dt, budget_s=15.0)
@@ -595,6 +651,7 @@ def main():
             "e2e": e2e, "gpu_launches": launches, "roofline": roofline,
             "cpu_baseline": cpu, "clocks": clocks, "traces_finite": tr_ok,
             "precision_forms": precision, "serving": serving, "gradient": gradient,
+            "cpml": cpml,
         }
         print(json.dumps(line), flush=True)
     if world > 1:

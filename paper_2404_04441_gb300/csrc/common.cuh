@@ -28,22 +28,22 @@ constexpr double kW[5] = {-205.0 / 72.0, 8.0 / 5.0, -1.0 / 5.0, 8.0 / 315.0,
 constexpr double kW1[5] = {0.0, 4.0 / 5.0, -1.0 / 5.0, 4.0 / 105.0, -1.0 / 280.0};
 
 // Velocity scan over the dense-in-x pitched buffer: max, and count of values
-// that are not finite and positive.
+// that are not finite and positive. Blocks take whole rows, threads adjacent
+// x (no per-element index division).
 __global__ void scan_velocity_kernel(const float *v, int nx, int px,
                                      long long rows, unsigned *vmax_bits,
                                      unsigned long long *nbad) {
   unsigned local_max = 0;
   unsigned long long local_bad = 0;
-  const long long total = rows * (long long)nx;
-  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
-       i < total; i += (long long)gridDim.x * blockDim.x) {
-    const long long r = i / nx;
-    const int x = (int)(i - r * nx);
-    const float val = v[r * px + x];
-    if (!(val > 0.f) || !isfinite(val)) {
-      ++local_bad;
-    } else {
-      local_max = max(local_max, __float_as_uint(val));
+  for (long long r = blockIdx.x; r < rows; r += gridDim.x) {
+    const float *row = v + r * px;
+    for (int x = threadIdx.x; x < nx; x += blockDim.x) {
+      const float val = row[x];
+      if (!(val > 0.f) || !isfinite(val)) {
+        ++local_bad;
+      } else {
+        local_max = max(local_max, __float_as_uint(val));
+      }
     }
   }
   for (int o = 16; o > 0; o >>= 1) {
@@ -56,13 +56,37 @@ __global__ void scan_velocity_kernel(const float *v, int nx, int px,
   }
 }
 
-// c = v^2 dt^2 in place (FP64 product, rounded once to FP32).
-__global__ void velocity_to_c_kernel(float *c, long long n, double dt2) {
-  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
+// c = v^2 dt^2 in place, in FP32 arithmetic (FP64 runs at a small fraction
+// of the FP32 rate on this part): v^2 = p + e exactly (TwoProduct with an
+// FMA, Ogita, Rump and Oishi 2005), dt^2 = dh + dl (the FP64 value split
+// into two floats), c = p dh + (p dl + e dh), small terms first: within
+// about one unit in the last place of the exact product, and the same on
+// every path. n is a multiple of 4 and c is 16-byte aligned (pitched field).
+__global__ void velocity_to_c_kernel(float *c, long long n, float dh, float dl) {
+  float4 *c4 = reinterpret_cast<float4 *>(c);
+  const long long n4 = n / 4;
+  auto conv = [&](float v) {
+    const float p = v * v;
+    const float e = fmaf(v, v, -p);
+    return fmaf(p, dh, fmaf(p, dl, e * dh));
+  };
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n4;
        i += (long long)gridDim.x * blockDim.x) {
-    const double v = c[i];
-    c[i] = (float)(v * v * dt2);
+    float4 t = c4[i];
+    t.x = conv(t.x);
+    t.y = conv(t.y);
+    t.z = conv(t.z);
+    t.w = conv(t.w);
+    c4[i] = t;
   }
+}
+
+// Launch velocity_to_c_kernel for dt^2 given in FP64.
+inline void launch_velocity_to_c(float *c, long long n, double dt2, int sms,
+                                 cudaStream_t st) {
+  const float dh = (float)dt2;
+  const float dl = (float)(dt2 - (double)dh);
+  velocity_to_c_kernel<<<sms * 4, 256, 0, st>>>(c, n, dh, dl);
 }
 
 template <class T>

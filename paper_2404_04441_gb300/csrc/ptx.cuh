@@ -86,17 +86,4 @@ __device__ __forceinline__ float4 lds4(const float *p) {
   return *reinterpret_cast<const float4 *>(p);
 }
 
-// Asynchronous 4-byte copy global -> shared (cp.async); when !valid nothing
-// is read and the destination is zero-filled (src must still be a mapped
-// address).
-__device__ __forceinline__ void cp_async4(float *dst, const float *src, bool valid) {
-  asm volatile("cp.async.ca.shared.global [%0], [%1], 4, %2;\n" ::"r"(smem_addr(dst)),
-               "l"(src), "r"(valid ? 4 : 0)
-               : "memory");
-}
-
-__device__ __forceinline__ void cp_async_wait_all() {
-  asm volatile("cp.async.commit_group;\ncp.async.wait_group 0;\n" ::: "memory");
-}
-
 }  // namespace gbw

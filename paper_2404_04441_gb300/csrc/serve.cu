@@ -228,8 +228,7 @@ int admit(serve_ctx *s, Request *q) {
   const double dt = r.dt > 0 ? r.dt : 0.5 * lim;
   if (!(dt <= lim * (1.0 + 1e-12))) return WAVE_EUNSTABLE;
   q->dt = dt;
-  velocity_to_c_kernel<<<sms * 4, 256, 0, st>>>(q->c, (long long)px * ny * nz,
-                                                dt * dt);
+  launch_velocity_to_c(q->c, (long long)px * ny * nz, dt * dt, sms, st);
   WAVE_TRY_CUDA(cudaGetLastError());
 
   // Receivers and source wavelet.

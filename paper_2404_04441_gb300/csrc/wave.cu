@@ -404,8 +404,7 @@ static int create_impl(wave_ctx *c, const float *velocity) {
   const double lim = wave_cfl_dt(&h, (double)vmax);
   if (!(c->dt <= lim * (1.0 + 1e-12))) return WAVE_EUNSTABLE;
   c->vmax = vmax;
-  velocity_to_c_kernel<<<sms * 4, 256, 0, st>>>(c->c, (long long)nfield,
-                                                c->dt * c->dt);
+  launch_velocity_to_c(c->c, (long long)nfield, c->dt * c->dt, sms, st);
   WAVE_TRY_CUDA(cudaGetLastError());
 
   // Launch geometry.
