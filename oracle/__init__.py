@@ -16,12 +16,22 @@ import numpy as np
 from . import build as _build
 
 _lib = None
+_lib_override = None
+
+
+def _use_library(path):
+    """Point the wrappers at another build of wave_oracle.c, or back at the
+    normal build with None. Only the pin-strength tests use it: they load
+    deliberately broken copies and check that the pins reject them."""
+    global _lib, _lib_override
+    _lib = None
+    _lib_override = path
 
 
 def _load():
     global _lib
     if _lib is None:
-        path = _build.build()
+        path = _lib_override or _build.build()
         lib = ctypes.CDLL(path)
         dp = ctypes.POINTER(ctypes.c_double)
         lib.oracle_weights.argtypes = [dp]

@@ -39,9 +39,12 @@
  *
  * Pins (tests/test_oracle_pins.py): weights from an exact rational solve,
  * polynomial exactness up to degree 9 and the predicted degree-10 error,
- * 8th-order convergence, the exact discrete dispersion relation, the
- * stability limit, discrete energy conservation, mirror symmetry, Ricker
- * closed-form values, and a dense-matrix brute force on tiny grids.
+ * 8th-order convergence, the exact discrete dispersion relation, second
+ * order in time against a manufactured standing wave, the stability limit,
+ * discrete energy conservation, mirror symmetry, Ricker closed-form values,
+ * and a dense-matrix brute force on tiny grids. tests/test_oracle_mutants.py
+ * plants single mistakes in copies of this file and checks that the pins
+ * reject each one.
  */
 #include <math.h>
 #ifdef _OPENMP

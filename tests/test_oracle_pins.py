@@ -159,6 +159,33 @@ def test_dispersion_relation_exact(oracle_mod):
     np.testing.assert_allclose(up, math.cos((nsteps - 1) * theta) * u0, atol=1e-11)
 
 
+def test_scheme_is_second_order_in_time(oracle_mod):
+    """Manufactured standing wave u = cos(k x) cos(omega t), omega = v k, on a
+    periodic grid, started from the exact u(0) and u(-dt). At fixed T the
+    error is the leapfrog phase error: theta - omega dt = (omega dt)^3 / 24 +
+    O(dt^5) per step, so max |u^N - u(T)| = |sin(omega T)| omega T (omega dt)^2
+    / 24 (1 + O(dt^2)); the spatial error ((k h)^8 / 3150 relative in the
+    symbol, 7e-10 here) is far below. Halving dt divides it by 4."""
+    nx, ny, nz, h, v = 32, 8, 8, 10.0, 2000.0
+    k = 2 * math.pi / (nx * h)
+    w = v * k
+    T = 2.5 / w
+    x = np.arange(nx) * h
+    u0 = np.cos(k * x)[None, None, :] * np.ones((nz, ny, nx))
+    vel = np.full((nz, ny, nx), v)
+    err = {}
+    for N in (80, 160, 320):
+        dt = T / N
+        assert dt < oracle_mod.cfl_dt((h, h, h), v)
+        u, _, _ = oracle_mod.propagate(vel, (h, h, h), dt, N, u=u0,
+                                       u_prev=math.cos(w * dt) * u0, periodic=True)
+        err[N] = np.max(np.abs(u - math.cos(w * T) * u0))
+        pred = abs(math.sin(w * T)) * w * T * (w * dt) ** 2 / 24
+        assert err[N] == pytest.approx(pred, rel=0.02)
+    assert 3.9 < err[80] / err[160] < 4.1
+    assert 3.9 < err[160] / err[320] < 4.1
+
+
 def test_stability_limit(oracle_mod):
     n, h, v = 8, 10.0, 3000.0
     i = np.arange(n)
