@@ -212,3 +212,88 @@ def test_invalid_and_unsupported(wave_lib):
         assert ei.value.code == -8
     finally:
         h.close()
+
+
+def _sub_box_cpml(oracle_mod, vel, u0, up0, sp, dt, n, p, shot, npml, R, fcps, vmax):
+    """Oracle value (and trace) at p after n steps with the layer, from a sub-box.
+
+    Along each axis the sub-box either contains the grid's face (so its layer
+    is the real one) or is cut far enough from p that neither the zero halo
+    nor the layer the oracle also puts at the cut can reach p in n steps: a
+    difference spreads at most 8 cells per step (4 through Eq. 1, 4 more
+    through psi), so the cut keeps npml + 8n + 1 cells of margin."""
+    nz, ny, nx = vel.shape
+    m = npml + 8 * n + 1
+    sl, lo = [], []
+    for c, size in zip(p[::-1], (nz, ny, nx)):
+        a = 0 if c - m <= 0 else c - m
+        b = size if c + m + 1 >= size else c + m + 1
+        sl.append(slice(a, b))
+        lo.append(a)
+    zl, yl, xl = lo
+    sl = tuple(sl)
+    src = None
+    if shot is not None:
+        sx, sy, sz = shot[:3]
+        if sl[2].start <= sx < sl[2].stop and sl[1].start <= sy < sl[1].stop \
+                and sl[0].start <= sz < sl[0].stop:
+            src = (sx - xl, sy - yl, sz - zl, *shot[3:])
+    rec = np.array([[p[0] - xl, p[1] - yl, p[2] - zl]], dtype=np.int32)
+    u, _, _, _, tr = oracle_mod.propagate_cpml(vel[sl], sp, dt, n, npml, R=R, fcps=fcps,
+                                               vmax=vmax, u=u0[sl], u_prev=up0[sl],
+                                               source=src, receivers=rec)
+    return u[p[2] - zl, p[1] - yl, p[0] - xl], tr[:, 0]
+
+
+def test_full_size_sampled_points(wave_lib, oracle_mod):
+    """1024 x 1024 x 512 random 8-layer model with the layer the benchmark
+    measures (npml 16), in its launch configuration: 3 steps from a random
+    state, checked at points in the layers, at corners and edges, across the
+    end of the correction segments, at the source (inside the z layer) and at
+    receivers (all inside the layer's shell), against the oracle on sub-boxes."""
+    import torch
+    cfg = wl.CFG_1024
+    nx, ny, nz = cfg["shape"]
+    vel = wl.velocity_for(cfg)
+    sp = cfg["spacing"]
+    dt = cfg["cfl_fraction"] * wave_lib.wave_cfl_dt(sp, float(vel.max()))
+    npml, R, fcps = 16, 1e-3, cfg["f_peak"]
+    g = torch.Generator(device="cuda")
+    g.manual_seed(4321)
+    u0 = torch.rand((nz, ny, nx), generator=g, device="cuda") * 2 - 1
+    up0 = torch.rand((nz, ny, nx), generator=g, device="cuda") * 2 - 1
+    n = 3
+    shot = (*cfg["source"], cfg["f_peak"], -1.0, 1e4)
+    rec_all = wl.receiver_plane(nx, ny, cfg["rec_z"], cfg["rec_stride"])
+    s = wave_lib.WaveSolver((nx, ny, nz), sp, dt, torch.from_numpy(vel).cuda())
+    s.set_cpml(npml, R, fcps)
+    s.set_state(u0, up0, 0)
+    tr = torch.zeros((n, rec_all.shape[0]), dtype=torch.float32, device="cuda")
+    s.propagate(shot, n, torch.from_numpy(rec_all).cuda(), tr)
+    out = torch.empty((nz, ny, nx), dtype=torch.float32, device="cuda")
+    s.get_field(0, out)
+    s.synchronize()
+    s.close()
+    u0h, up0h = u0.cpu().numpy(), up0.cpu().numpy()
+    outh = out.cpu().numpy()
+    trh = tr.cpu().numpy()
+    vmax = float(vel.max())
+    w = npml + 4
+    pts = [(0, 0, 0), (nx - 1, ny - 1, nz - 1), (nx - 1, 0, nz // 2), (0, ny // 2, nz - 1),
+           (npml - 1, 300, 200), (npml, 301, 201), (w - 1, 302, 202), (w, 303, 203),
+           (nx - w, 500, 100), (nx - w - 1, 501, 101), (700, npml - 1, 250), (701, ny - w, 251),
+           (400, 402, nz - npml), (401, 403, w - 1), (5, 7, 9), (nx - 3, ny - 9, 2),
+           cfg["source"], (cfg["source"][0] + 2, cfg["source"][1], cfg["source"][2] - 3),
+           (512, 512, 256)]
+    for p in pts:
+        want, _ = _sub_box_cpml(oracle_mod, vel, u0h, up0h, sp, dt, n, p, shot, npml, R,
+                                fcps, vmax)
+        got = outh[p[2], p[1], p[0]]
+        assert abs(got - want) <= 2e-5 * max(1.0, abs(want)), (p, got, want)
+    rng = np.random.default_rng(1)
+    near = np.argsort(np.abs(rec_all[:, 0] - cfg["source"][0])
+                      + np.abs(rec_all[:, 1] - cfg["source"][1]))[:3]
+    for r in list(near) + [0, rec_all.shape[0] - 1] + list(rng.integers(0, rec_all.shape[0], 3)):
+        _, want_tr = _sub_box_cpml(oracle_mod, vel, u0h, up0h, sp, dt, n,
+                                   tuple(int(v) for v in rec_all[r]), shot, npml, R, fcps, vmax)
+        np.testing.assert_allclose(trh[:, r], want_tr, rtol=2e-5, atol=2e-5)

@@ -178,3 +178,27 @@ def test_cpml_keeps_mirror_symmetry(oracle_mod):
     for axis in range(3):
         assert np.max(np.abs(u - np.flip(u, axis))) <= 1e-12 * sc
     assert np.max(np.abs(u - np.transpose(u, (2, 1, 0)))) <= 1e-12 * sc
+
+
+def test_sub_box_margin_reproduces_the_whole_grid(oracle_mod):
+    """The sub-box reduction the full-size GPU test relies on: with a margin
+    of npml + 8n + 1 cells at every cut, the oracle on the sub-box gives the
+    whole-grid oracle's value at the point exactly (layers at true faces,
+    source inside the layer, random state)."""
+    from test_gpu_cpml import _sub_box_cpml
+    nx, ny, nz = 120, 110, 100
+    rng = np.random.default_rng(0)
+    vel = rng.uniform(1500, 4500, size=(nz, ny, nx)).astype(np.float32)
+    u0 = rng.uniform(-1, 1, size=vel.shape)
+    up0 = rng.uniform(-1, 1, size=vel.shape)
+    sp = (10.0, 10.0, 10.0)
+    dt = 0.5 * oracle_mod.cfl_dt(sp, float(vel.max()))
+    npml, n = 6, 3
+    shot = (60, 55, 8, 15.0, -1.0, 1e4)
+    vmax = float(vel.max())
+    full, _, _, _, _ = oracle_mod.propagate_cpml(vel, sp, dt, n, npml, R=1e-3, fcps=15.0,
+                                                 vmax=vmax, u=u0, u_prev=up0, source=shot)
+    for p in [(0, 0, 0), (119, 109, 99), (5, 50, 50), (60, 55, 8), (40, 3, 97), (70, 70, 50)]:
+        v, _ = _sub_box_cpml(oracle_mod, vel, u0, up0, sp, dt, n, p, shot, npml, 1e-3, 15.0,
+                             vmax)
+        assert v == full[p[2], p[1], p[0]]
