@@ -149,3 +149,50 @@ def test_host_buffers_and_unsupported_storage(wave_lib, oracle_mod):
         s16.gradient(shot, 25, rec, obs, gh, ckpt_every=5)
     assert ei.value.code == -8
     s16.close()
+
+
+def test_full_size_directional_derivative(wave_lib):
+    """The benchmark's gradient workload (256^3, 800 steps, checkpoint every
+    40): <g, dm> against central differences of the GPU misfit along
+    dm = m g / max|g| (a relative change of m of at most e, largest where the
+    misfit is most sensitive, so the misfit change stands far above the FP32
+    rounding noise of an 800-step run; a wrong sign, scale or pattern of g
+    still shows, since the differences measure the true derivative along
+    dm). Two step sizes must agree with each other and with <g, dm>."""
+    import torch
+    cfg = wl.CFG_GRAD
+    nx, ny, nz = cfg["shape"]
+    true = wl.anomaly_model(nx, ny, nz, seed=cfg["seed"], anomaly=cfg["anomaly_mps"])
+    start = wl.smoothed_start(true)
+    rec = torch.from_numpy(wl.receiver_plane(nx, ny, cfg["rec_z"], cfg["rec_stride"])).cuda()
+    shot = (nx // 2, ny // 2, 10, cfg["f_peak"], -1.0, 1.0)
+    n = cfg["nsteps"]
+    dt = 0.5 * wave_lib.wave_cfl_dt(cfg["spacing"], max(float(true.max()), float(start.max())) * 1.05)
+    obs = torch.zeros((n, rec.shape[0]), device="cuda")
+    st = wave_lib.WaveSolver((nx, ny, nz), cfg["spacing"], dt, torch.from_numpy(true).cuda())
+    st.propagate(shot, n, rec, obs)
+    st.close()
+
+    def misfit_and_grad(v, want_grad):
+        s = wave_lib.WaveSolver((nx, ny, nz), cfg["spacing"], dt, torch.from_numpy(v).cuda())
+        g = torch.empty((nz, ny, nx), device="cuda")
+        mis = s.gradient(shot, n, rec, obs, g, ckpt_every=cfg["ckpt_every"])
+        s.close()
+        return mis, (g.cpu().numpy().astype(np.float64) if want_grad else None)
+
+    j0, g = misfit_and_grad(start, True)
+    assert np.all(np.isfinite(g)) and np.max(np.abs(g)) > 0
+    m = start.astype(np.float64) ** 2
+    dm = m * g / np.max(np.abs(g))
+    dot = float(np.sum(g * dm))
+
+    def fd(eps):
+        jp, _ = misfit_and_grad(np.sqrt(m + eps * dm).astype(np.float32), False)
+        jm, _ = misfit_and_grad(np.sqrt(m - eps * dm).astype(np.float32), False)
+        return (jp - jm) / (2 * eps)
+
+    f1, f2 = fd(2e-3), fd(1e-3)
+    print("full-size gradient test: J %.6g, <g,dm> %.6g, FD(2e-3) %.6g, FD(1e-3) %.6g"
+          % (j0, dot, f1, f2))
+    assert f1 == pytest.approx(f2, rel=1e-3)
+    assert dot == pytest.approx(f1, rel=1e-3)

@@ -134,3 +134,68 @@ def _precision_oracle(oracle_mod, vel, sp, dt, nsteps, shot, rec):
     if key not in _ORACLE_CACHE:
         _ORACLE_CACHE[key] = oracle_mod.propagate(vel, sp, dt, nsteps, source=shot, receivers=rec)
     return _ORACLE_CACHE[key]
+
+
+@pytest.mark.parametrize("mode", ["bf16", "f16"])
+def test_full_size_sampled_points(wave_lib, oracle_mod, mode):
+    """1024 x 1024 x 512 random 8-layer model in the launch configuration the
+    benchmark times for 16-bit storage: 3 steps from a random state, sampled
+    points (grid corners, tile and z-layer edges, the source) and receivers
+    against the oracle on the sub-box each depends on, started from the
+    state as stored (read back after set_state, so the initial rounding is
+    shared). Bound: each step rounds u^{n+1} to the format (|e| <= EPS M, M
+    the largest |u| over the run) and carries earlier errors forward at most
+    7-fold (2|u| + |u_prev| + c|L u| <= 7 max, c |L| <= 4 within the
+    stability limit), so after 3 steps |e| <= (1 + 7 + 6*7 - 6) EPS M < 44 EPS M."""
+    import torch
+    from test_gpu_parity import _sub_box_oracle
+    cfg = wl.CFG_1024
+    nx, ny, nz = cfg["shape"]
+    vel = wl.velocity_for(cfg)
+    sp = cfg["spacing"]
+    dt = cfg["cfl_fraction"] * wave_lib.wave_cfl_dt(sp, float(vel.max()))
+    g = torch.Generator(device="cuda")
+    g.manual_seed(99)
+    u0 = torch.rand((nz, ny, nx), generator=g, device="cuda") * 2 - 1
+    up0 = torch.rand((nz, ny, nx), generator=g, device="cuda") * 2 - 1
+    n = 3
+    shot = (*cfg["source"], cfg["f_peak"], -1.0, 1e2)
+    rec_all = wl.receiver_plane(nx, ny, cfg["rec_z"], cfg["rec_stride"])
+    s = wave_lib.WaveSolver((nx, ny, nz), sp, dt, torch.from_numpy(vel).cuda(),
+                            storage=STORAGE[mode])
+    s.set_state(u0, up0, 0)
+    su = torch.empty((nz, ny, nx), device="cuda")
+    sup = torch.empty((nz, ny, nx), device="cuda")
+    s.get_field(0, su)
+    s.get_field(1, sup)
+    tr = torch.zeros((n, rec_all.shape[0]), device="cuda")
+    s.propagate(shot, n, torch.from_numpy(rec_all).cuda(), tr)
+    out = torch.empty((nz, ny, nx), device="cuda")
+    s.get_field(0, out)
+    s.synchronize()
+    info = s.launch_info()
+    s.close()
+    u0h, up0h = su.cpu().numpy(), sup.cpu().numpy()
+    outh = out.cpu().numpy()
+    trh = tr.cpu().numpy()
+    M = max(float(np.abs(outh).max()), float(np.abs(u0h).max()))
+    tol = 44 * EPS[mode] * M
+    tx, ty, zc = info["tile_x"], info["tile_y"], info["z_chunk"]
+    rng = np.random.default_rng(7)
+    pts = [(0, 0, 0), (nx - 1, ny - 1, nz - 1), (nx - 1, 0, nz // 2), cfg["source"],
+           (tx - 1, ty, zc - 1), (tx, ty - 1, zc), (2 * tx - 1, 2 * ty - 1, min(nz - 1, 2 * zc))]
+    pts += [tuple(int(v) for v in (rng.integers(nx), rng.integers(ny), rng.integers(nz)))
+            for _ in range(8)]
+    worst = 0.0
+    for p in pts:
+        want, _ = _sub_box_oracle(oracle_mod, vel, u0h, up0h, sp, dt, n, p, shot)
+        err = abs(float(outh[p[2], p[1], p[0]]) - want)
+        worst = max(worst, err)
+        assert err <= tol, (p, err, tol)
+    for r in list(rng.integers(0, rec_all.shape[0], 6)):
+        _, want_tr = _sub_box_oracle(oracle_mod, vel, u0h, up0h, sp, dt, n,
+                                     tuple(int(v) for v in rec_all[r]), shot)
+        err = float(np.max(np.abs(trh[:, r] - want_tr)))
+        worst = max(worst, err)
+        assert err <= tol, (r, err, tol)
+    print("%s full size: worst |error| %.3g, bound %.3g (M = %.3g)" % (mode, worst, tol, M))
