@@ -324,9 +324,14 @@ int upload_tables(serve_ctx *s) {
     std::vector<Request *> shots;
     for (Request *q : s->resident)
       if (q->r.storage == kd) shots.push_back(q);
+    // Group by coefficients; within a group, shots with longer z layers
+    // first. A shot's CTAs all stream one layer length, so this hands the
+    // block scheduler the longest CTAs first and shortens the partial last
+    // wave of each batched step.
     std::stable_sort(shots.begin(), shots.end(), [](Request *x, Request *y) {
-      return std::memcmp(&x->shot.args.k, &y->shot.args.k,
-                         sizeof(StencilCoefs)) < 0;
+      const int c = std::memcmp(&x->shot.args.k, &y->shot.args.k, sizeof(StencilCoefs));
+      if (c != 0) return c < 0;
+      return x->shot.args.zl[1] - x->shot.args.zl[0] > y->shot.args.zl[1] - y->shot.args.zl[0];
     });
     auto &t = s->h_table[kd];
     t.clear();
