@@ -579,7 +579,11 @@ def main():
 
     # ---- 16-bit storage forms: same workload and K; error on 128^3 x 500 ---
     precision = None
-    if not args.no_precision:
+    # The storage forms, serving, gradient and CPML lines are single-GPU
+    # measurements beside the headline; with N replicas only the headline
+    # (and its e2e) is run, so the GPUs are held for the scaling line alone.
+    side = world == 1
+    if side and not args.no_precision:
         precision = {}
         for name in ("bf16", "f16"):
             s16 = gw.WaveSolver((nx, ny, nz), sp, dt, vel_d, storage=STORAGE[name],
@@ -615,17 +619,17 @@ def main():
 
     # ---- shot serving: continuous batching of a Poisson request stream -------
     serving = None
-    if not args.no_serve:
+    if side and not args.no_serve:
         serving = {name: serve_stream(gw, torch, STORAGE[name], args.serve_requests)
                    for name in ("f32", "f16")}
         serving["saturated_mix"] = serve_saturated(gw, torch)
 
     gradient = None
-    if not args.no_gradient:
+    if side and not args.no_gradient:
         gradient = gradient_workload(gw, torch)
 
     cpml = None
-    if not args.no_cpml:
+    if side and not args.no_cpml:
         cpml = cpml_workload(gw, torch, cfg, vel_d, dt, min(K, 200), peaks["hbm_gbs"], ms / K)
 
     cpu = None
