@@ -75,6 +75,26 @@ def test_alone_and_in_the_mix_are_identical(wave_lib):
         assert np.abs(tr_mix).max() > 0
 
 
+def test_stream_sized_shots_alone_and_in_the_mix(wave_lib):
+    """Shots of the serving stream's sizes (up to 512 per axis; nz > 256 is
+    split into two z layers per CTA column), FP32 and FP16 in one mix with a
+    small shot: each mixed result is bit-identical to wave_propagate."""
+    import torch
+    specs = [((512, 384, 480), 0, 24, 31), ((448, 512, 320), 2, 20, 32),
+             ((128, 160, 128), 0, 30, 33), ((256, 224, 512), 2, 18, 34)]
+    mix, res, stats = _serve(wave_lib, specs, budget=40 * GB, slots=8)
+    assert stats["completed"] == len(specs) and stats["resident_peak"] >= 2
+    for (grid, storage, nsteps, seed), tr_mix, r in zip(specs, mix, res):
+        vel, rec, shot = _inputs(grid, seed)
+        s = wave_lib.WaveSolver(grid, (10.0, 10.0, 10.0), r["dt"], vel, storage=storage)
+        tr = torch.zeros((nsteps, rec.shape[0]), device="cuda")
+        s.propagate(shot, nsteps, rec, tr)
+        s.synchronize()
+        s.close()
+        assert np.array_equal(tr.cpu().numpy(), tr_mix), grid
+        assert np.abs(tr_mix).max() > 0
+
+
 def test_budget_admission_queues_requests(wave_lib):
     # room for two of these shots at a time
     grid = (96, 96, 96)
