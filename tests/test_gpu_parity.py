@@ -310,3 +310,82 @@ def test_full_size_sampled_points(wave_lib, oracle_mod, cfg):
         _, want_tr = _sub_box_oracle(oracle_mod, vel, u0h, up0h, sp, dt, n,
                                      tuple(int(v) for v in rec_all[r]), shot)
         np.testing.assert_allclose(trh[:, r], want_tr, rtol=2e-5, atol=2e-5)
+
+
+def _hash_field(x, y, z, k):
+    """Deterministic values in [-1, 1) from integer coordinates (numpy or
+    torch int64 arrays): a multiplicative hash keeps 20 bits, so the float32
+    value is exact and the same on the host and the device."""
+    a, b, c = ((73856093, 19349663, 83492791), (50331653, 12582917, 25165843))[k]
+    h = (x * a) ^ (y * b) ^ (z * c)
+    return (h & 0xFFFFF).float() / 524288.0 - 1.0 if hasattr(h, "float") else \
+        (h & 0xFFFFF).astype(np.float32) / np.float32(524288.0) - np.float32(1.0)
+
+
+def test_grid_beyond_2_31_points(wave_lib, oracle_mod):
+    """2048 x 1024 x 1040 = 2.18e9 points (more than 2^31; 26 GB of fields):
+    3 steps from a hashed state with source and receivers, checked at points
+    near the far end of the grid and at tile and layer edges against the
+    oracle on sub-boxes (the state of a sub-box is recomputed on the host from
+    the same hash)."""
+    import torch
+    nx, ny, nz = 2048, 1024, 1040
+    assert nx * ny * nz > 2 ** 31
+    sp = (10.0, 10.0, 10.0)
+    vz = wl.layered_profile(nz, 5)
+    dt = 0.5 * wave_lib.wave_cfl_dt(sp, float(vz.max()))
+    vel = torch.from_numpy(vz).cuda()[:, None, None].expand(nz, ny, nx).contiguous()
+    u0 = torch.empty((nz, ny, nx), device="cuda")
+    up0 = torch.empty((nz, ny, nx), device="cuda")
+    xs = torch.arange(nx, device="cuda", dtype=torch.int64)[None, None, :]
+    ys = torch.arange(ny, device="cuda", dtype=torch.int64)[None, :, None]
+    for z0 in range(0, nz, 64):
+        zs = torch.arange(z0, min(nz, z0 + 64), device="cuda", dtype=torch.int64)[:, None, None]
+        u0[z0:z0 + 64] = _hash_field(xs, ys, zs, 0)
+        up0[z0:z0 + 64] = _hash_field(xs, ys, zs, 1)
+    n = 3
+    shot = (nx - 5, ny - 7, nz - 9, 15.0, -1.0, 1e3)
+    rec = np.array([[nx - 1, ny - 1, nz - 1], [nx - 5, ny - 7, nz - 9], [17, 900, 1030],
+                    [2000, 3, 600]], dtype=np.int32)
+    s = wave_lib.WaveSolver((nx, ny, nz), sp, dt, vel)
+    del vel
+    s.set_state(u0, up0, 0)
+    del u0, up0
+    tr = torch.zeros((n, rec.shape[0]), device="cuda")
+    s.propagate(shot, n, torch.from_numpy(rec).cuda(), tr)
+    out = torch.empty((nz, ny, nx), device="cuda")
+    s.get_field(0, out)
+    s.synchronize()
+    info = s.launch_info()
+    s.close()
+    trh = tr.cpu().numpy()
+    tx, ty, zc = info["tile_x"], info["tile_y"], info["z_chunk"]
+    pts = [(nx - 1, ny - 1, nz - 1), (nx - 5, ny - 7, nz - 9), (0, 0, nz - 1), (nx - 1, 0, 0),
+           (tx, ty - 1, zc), (tx - 1, ty, zc - 1), (1234, 567, 890), (2047, 1023, 520)]
+
+    def sub_box(p):
+        x, y, z = p
+        r = 4 * n
+        lo = [max(0, c - r) for c in (x, y, z)]
+        hi = [min(m, c + r + 1) for c, m in zip((x, y, z), (nx, ny, nz))]
+        X = np.arange(lo[0], hi[0], dtype=np.int64)[None, None, :]
+        Y = np.arange(lo[1], hi[1], dtype=np.int64)[None, :, None]
+        Z = np.arange(lo[2], hi[2], dtype=np.int64)[:, None, None]
+        vb = np.broadcast_to(vz[lo[2]:hi[2], None, None],
+                             (hi[2] - lo[2], hi[1] - lo[1], hi[0] - lo[0])).copy()
+        src = None
+        if all(lo[i] <= shot[i] < hi[i] for i in range(3)):
+            src = (shot[0] - lo[0], shot[1] - lo[1], shot[2] - lo[2], *shot[3:])
+        r1 = np.array([[x - lo[0], y - lo[1], z - lo[2]]], dtype=np.int32)
+        u, _, t = oracle_mod.propagate(vb, sp, dt, n, u=_hash_field(X, Y, Z, 0),
+                                       u_prev=_hash_field(X, Y, Z, 1), source=src,
+                                       receivers=r1)
+        return u[z - lo[2], y - lo[1], x - lo[0]], t[:, 0]
+
+    for p in pts:
+        want, _ = sub_box(p)
+        got = float(out[p[2], p[1], p[0]].item())
+        assert abs(got - want) <= 2e-5 * max(1.0, abs(want)), (p, got, want)
+    for r in range(rec.shape[0]):
+        _, want_tr = sub_box(tuple(int(v) for v in rec[r]))
+        np.testing.assert_allclose(trh[:, r], want_tr, rtol=2e-5, atol=2e-5)
