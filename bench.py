@@ -622,11 +622,24 @@ def main():
     if side and not args.no_serve:
         serving = {name: serve_stream(gw, torch, STORAGE[name], args.serve_requests)
                    for name in ("f32", "f16")}
+        # HBM roofline of the engine's busy time: the batched step moves the
+        # single-grid kernel's algorithmic bytes per point-step.
+        for name, bpp in (("f32", BYTES_PER_POINT), ("f16", BYTES_PER_POINT_16)):
+            ach = serving[name]["gpts_busy"] * bpp
+            serving[name]["roofline_busy"] = {
+                "bound": "hbm", "achieved": ach, "peak": peaks["hbm_gbs"], "unit": "GB/s",
+                "frac": ach / peaks["hbm_gbs"], "algorithmic_bytes_per_point": bpp}
         serving["saturated_mix"] = serve_saturated(gw, torch)
 
     gradient = None
     if side and not args.no_gradient:
         gradient = gradient_workload(gw, torch)
+        # 72 B per model-point-step: forward 16, recompute storing D 20, adjoint
+        # with injection, D read and the FP64 time sum 36.
+        ach = 72.0 * gradient["gpts_model_steps"]
+        gradient["roofline"] = {"bound": "hbm", "achieved": ach, "peak": peaks["hbm_gbs"],
+                                "unit": "GB/s", "frac": ach / peaks["hbm_gbs"],
+                                "algorithmic_bytes_per_model_point_step": 72}
 
     cpml = None
     if side and not args.no_cpml:
