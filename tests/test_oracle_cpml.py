@@ -202,3 +202,23 @@ def test_sub_box_margin_reproduces_the_whole_grid(oracle_mod):
         v, _ = _sub_box_cpml(oracle_mod, vel, u0, up0, sp, dt, n, p, shot, npml, 1e-3, 15.0,
                              vmax)
         assert v == full[p[2], p[1], p[0]]
+
+
+def test_recursive_convolution_is_exact_for_a_step(oracle_mod):
+    """psi^n = b psi^{n-1} + a g^n is the convolution psi = chi * g with the
+    CFS kernel chi(t) = -d exp(-(d + alpha) t) (the inverse transform of
+    1/s - 1, s = 1 + d / (alpha + i omega)), exact when g is constant over each
+    step: for a unit step from t = 0 the continuous result at t = (n+1) dt is
+    -d / (d + alpha) (1 - exp(-(d + alpha)(n + 1) dt)). A wrong sign or factor
+    in a, or alpha missing from b, breaks the match."""
+    n_cells, npml, h, dt, vmax, R, fc = 40, 10, 10.0, 1e-3, 3000.0, 1e-3, 15.0
+    b, a = oracle_mod.cpml_profile(n_cells, npml, h, dt, vmax, R, fc)
+    d0 = 3.0 * vmax * math.log(1.0 / R) / (2.0 * npml * h)
+    for i in (0, 3, 7, 9, 33, 39):
+        xi = (npml - i) / npml if i < npml else (i - (n_cells - npml - 1)) / npml
+        d, al = d0 * xi * xi, math.pi * fc * (1.0 - xi)
+        psi = 0.0
+        for n in range(60):
+            psi = b[i] * psi + a[i] * 1.0
+            exact = -d / (d + al) * (1.0 - math.exp(-(d + al) * (n + 1) * dt))
+            assert psi == pytest.approx(exact, rel=1e-12, abs=1e-15), (i, n)

@@ -63,6 +63,13 @@ MUTANTS = {
     "CPML damping profile linear": (
         "const double d = d0 * xi * xi;", "const double d = d0 * xi;",
         [cpml_pins.test_profile]),
+    "CPML convolution weight with the wrong sign": (
+        "a[i] = (d + al > 0.0) ? d / (d + al) * (b[i] - 1.0) : 0.0;",
+        "a[i] = (d + al > 0.0) ? d / (d + al) * (1.0 - b[i]) : 0.0;",
+        [cpml_pins.test_recursive_convolution_is_exact_for_a_step]),
+    "CPML decay without the frequency shift": (
+        "b[i] = exp(-(d + al) * dt);", "b[i] = exp(-d * dt);",
+        [cpml_pins.test_recursive_convolution_is_exact_for_a_step]),
     "CPML psi term with the wrong sign": (
         "sum += d2 + d1p + zeta[ax * n + p];", "sum += d2 - d1p + zeta[ax * n + p];",
         [cpml_pins.test_dense_state_space_brute_force]),
