@@ -219,7 +219,9 @@ int wave_selftest_wait(int64_t limit_ns, void *stream);
  * time difference. The library runs p = C q, which obeys the forward update
  * with the residuals injected at the receivers, on the same sweep kernel;
  * the forward fields come from checkpoints every ckpt_every steps, one
- * segment recomputed at a time; the time sum is accumulated in FP64.
+ * segment recomputed at a time; the time sum is accumulated in FP64 (each
+ * block of 32 steps, counted from step 0, is first summed exactly as an
+ * FP32 double-float pair, then added to the FP64 sum).
  *
  *   shot         Ricker source of the forward run (NULL: none)
  *   rec_xyz      nrec*3 int32 receivers (host or device), as wave_propagate

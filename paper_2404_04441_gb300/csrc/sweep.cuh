@@ -69,7 +69,7 @@ constexpr int kMaxLayers = 16;
 // Extra work of a sweep (template bit mask), used by the adjoint gradient:
 constexpr int kModeStoreD = 1;   // write D = v^2 dt^2 (L u) + source to a.dout
 constexpr int kModeInject = 2;   // add the StepDesc's point injections
-constexpr int kModeGradAcc = 4;  // a.gacc += u * a.dsrc (FP64), per point
+constexpr int kModeGradAcc = 4;  // (a.ghi, a.glo) += u * a.dsrc, per point
 
 // Eq. 1 coefficients of one grid spacing.
 struct StencilCoefs {
@@ -93,7 +93,7 @@ struct SweepArgs {
   float cmax;          // largest v^2 dt^2 (16-bit storage: growth bound)
   float *dout;         // kModeStoreD: D of this step (field layout)
   const float *dsrc;   // kModeGradAcc: D paired with this step's u
-  double *gacc;        // kModeGradAcc: FP64 sum of u * D (field layout)
+  float *ghi, *glo;    // kModeGradAcc: running sum of u * D as hi + lo (field layout)
 };
 
 // Element access per storage type: 4 consecutive elements to/from float4.
@@ -227,6 +227,20 @@ struct SweepCfg {
                 "slot alignment");
   static_assert(UW <= 256 && UH <= 256, "TMA box limit");
 };
+
+// hi + lo += u d without loss: the product exactly as p + e (an FMA gives
+// the rounding error of u d), p added to hi with Knuth's TwoSum (hi + p = s
+// + err exactly), err + e gathered in lo. A double-float sum of about 48
+// significant bits, in FP32 arithmetic.
+__device__ __forceinline__ void acc_exact(float &hi, float &lo, float u, float d) {
+  const float p = __fmul_rn(u, d);
+  const float e = __fmaf_rn(u, d, -p);
+  const float s = __fadd_rn(hi, p);
+  const float bp = __fsub_rn(s, hi);
+  const float err = __fadd_rn(__fsub_rn(hi, __fsub_rn(s, bp)), __fsub_rn(p, bp));
+  hi = s;
+  lo = __fadd_rn(lo, __fadd_rn(err, e));
+}
 
 __device__ __forceinline__ float exp2_int(int k) {
   return ldexpf(1.0f, max(-126, min(127, k)));
@@ -574,17 +588,20 @@ __device__ __forceinline__ void sweep_cta(const CUtensorMap *tm_u,
           if constexpr ((kMode & kModeStoreD) != 0)
             __stcs(reinterpret_cast<float4 *>(a.dout + idx), dres[v]);
           if constexpr ((kMode & kModeGradAcc) != 0) {
-            // FP64 time sum of this step's u (centre of the queue) times D.
+            // This step's u (centre of the queue) times D into the running
+            // double-float partial; the host folds it into the FP64 time
+            // sum at fixed step boundaries.
             const float4 uc4 = q[v][(p + 5) % 9];
             const float4 d4 = __ldcs(reinterpret_cast<const float4 *>(a.dsrc + idx));
-            double2 *g = reinterpret_cast<double2 *>(a.gacc + idx);
-            double2 g0 = g[0], g1 = g[1];
-            g0.x = fma((double)uc4.x, (double)d4.x, g0.x);
-            g0.y = fma((double)uc4.y, (double)d4.y, g0.y);
-            g1.x = fma((double)uc4.z, (double)d4.z, g1.x);
-            g1.y = fma((double)uc4.w, (double)d4.w, g1.y);
-            g[0] = g0;
-            g[1] = g1;
+            float4 *gh = reinterpret_cast<float4 *>(a.ghi + idx);
+            float4 *gl = reinterpret_cast<float4 *>(a.glo + idx);
+            float4 h = *gh, l = *gl;
+            acc_exact(h.x, l.x, uc4.x, d4.x);
+            acc_exact(h.y, l.y, uc4.y, d4.y);
+            acc_exact(h.z, l.z, uc4.z, d4.z);
+            acc_exact(h.w, l.w, uc4.w, d4.w);
+            *gh = h;
+            *gl = l;
           }
         }
       }

@@ -932,6 +932,21 @@ __global__ void reverse_rows_kernel(const float *res, float *inj, int N,
   }
 }
 
+// FP64 time sum += the double-float partial hi + lo (exact in FP64), and the
+// partial restarts from zero.
+__global__ void grad_fold_kernel(double *gacc, float *ghi, float *glo, long long n) {
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
+       i += (long long)gridDim.x * blockDim.x) {
+    gacc[i] += (double)ghi[i] + (double)glo[i];
+    ghi[i] = 0.f;
+    glo[i] = 0.f;
+  }
+}
+
+// Steps per FP64 fold of the gradient's time sum, counted in absolute steps
+// so the sum's rounding does not depend on the checkpoint interval.
+constexpr int kGradFold = 32;
+
 // dJ/dm = sum / (m^2 dt^2) = sum * dt^2 / c^2 with c = m dt^2; dense output.
 __global__ void grad_assemble_kernel(const double *gacc, const float *c,
                                      float *grad, int nx, int px,
@@ -976,7 +991,7 @@ int gradient_impl(wave_ctx *c, const wave_shot *shot, int N,
   const int ncp = (N + K - 1) / K;
   const size_t tn = (size_t)N * nrec;
   DevFree mem;
-  float *ckpt, *dbuf, *padj[2], *trd, *res, *inj, *wl;
+  float *ckpt, *dbuf, *padj[2], *trd, *res, *inj, *wl, *ghi, *glo;
   double *gacc, *dmis;
   StepDesc *dadj, *dfwd;
   int e;
@@ -985,6 +1000,7 @@ int gradient_impl(wave_ctx *c, const wave_shot *shot, int N,
       (e = mem.alloc(&trd, tn * 4)) || (e = mem.alloc(&res, tn * 4)) ||
       (e = mem.alloc(&inj, (tn + nrec) * 4)) || (e = mem.alloc(&wl, (size_t)N * 4)) ||
       (e = mem.alloc(&gacc, fe * 8)) || (e = mem.alloc(&dmis, 8)) ||
+      (e = mem.alloc(&ghi, fb)) || (e = mem.alloc(&glo, fb)) ||
       (e = mem.alloc(&dadj, sizeof(StepDesc))) ||
       (e = mem.alloc(&dfwd, sizeof(StepDesc))))
     return e;
@@ -1065,9 +1081,13 @@ int gradient_impl(wave_ctx *c, const wave_shot *shot, int N,
   WAVE_TRY_CUDA(cudaMemsetAsync(padj[0], 0, fb, st));
   WAVE_TRY_CUDA(cudaMemsetAsync(padj[1], 0, fb, st));
   WAVE_TRY_CUDA(cudaMemsetAsync(gacc, 0, fe * 8, st));
+  WAVE_TRY_CUDA(cudaMemsetAsync(ghi, 0, fb, st));
+  WAVE_TRY_CUDA(cudaMemsetAsync(glo, 0, fb, st));
 
   // Adjoint launch a = N - k computes p^k from p^{k+1} (padj[ca]) and
-  // p^{k+2}; with kModeGradAcc it adds p^{k+1} D^k to the FP64 sum.
+  // p^{k+2}; with kModeGradAcc it adds p^{k+1} D^k to the double-float
+  // partial, which is folded into the FP64 sum after every step k that is
+  // a multiple of kGradFold (the last fold is after k = 0).
   int ca = 0;
   auto adjoint_step = [&](int k, const float *dsrc) {
     SweepArgs a = c->args;
@@ -1075,11 +1095,14 @@ int gradient_impl(wave_ctx *c, const wave_shot *shot, int N,
     a.koff = N - k;
     a.unext = padj[ca ^ 1];
     a.dsrc = dsrc;
-    a.gacc = gacc;
+    a.ghi = ghi;
+    a.glo = glo;
     if (dsrc)
       launch_mode<kModeInject | kModeGradAcc>(c, ahalo[ca], atile[ca ^ 1], a);
     else
       launch_mode<kModeInject>(c, ahalo[ca], atile[ca ^ 1], a);
+    if (dsrc && k % kGradFold == 0)
+      grad_fold_kernel<<<c->sms * 4, 256, 0, st>>>(gacc, ghi, glo, (long long)fe);
     ca ^= 1;
   };
   adjoint_step(N, nullptr);  // p^N (no D^N term)
