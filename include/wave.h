@@ -9,8 +9,9 @@
  *
  * with w = (-205/72, 8/5, -1/5, 8/315, -1/560) (Eq. 1's c_am = w_m / h_a^2;
  * its m = 0 term counts the centre twice, c_a0 = w0 / (2 h_a^2)). Points
- * outside the interior read as zero (zero Dirichlet halo of width 4); the
- * paper's CPML layer (Sec. 2) is not implemented here. After the update of
+ * outside the interior read as zero (zero Dirichlet halo of width 4); an
+ * absorbing CPML layer like the paper's (Sec. 2) can be switched on per
+ * context with wave_set_cpml. After the update of
  * step n a Ricker point source adds v^2 dt^2 s(t_n) at the source point,
  * t_n = n dt, s(t) = amp (1 - 2 pi^2 f^2 (t-t0)^2) exp(-pi^2 f^2 (t-t0)^2),
  * and every receiver records u_next at its point.
