@@ -21,7 +21,9 @@
  * v^2 dt^2 (FP32), and its tables (source wavelet, receiver table, and a
  * trace staging buffer when `traces` is host memory). Admission is first in,
  * first out: the head request waits until its bytes fit in the budget next to
- * the resident shots and a slot is free.
+ * the resident shots, a slot is free, and one batched step over the resident
+ * shots and it would launch no more than six waves of CTAs (four per SM),
+ * unless nothing is resident (so every admissible request runs eventually).
  */
 #ifndef GBWAVE_WAVE_SERVE_H
 #define GBWAVE_WAVE_SERVE_H
