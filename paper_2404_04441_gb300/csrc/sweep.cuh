@@ -262,7 +262,8 @@ __device__ __forceinline__ void sweep_cta(const CUtensorMap *tm_u,
                                           const SweepArgs &a,
                                           const StencilCoefs &co, int bx,
                                           int by, int bz,
-                                          unsigned char *smem_raw) {
+                                          unsigned char *smem_raw, void *unext,
+                                          int koff) {
   using T = typename C::T;
   using E = Elem<T>;
   unsigned char *base = smem_raw;  // 128-byte aligned (declaration below)
@@ -284,7 +285,7 @@ __device__ __forceinline__ void sweep_cta(const CUtensorMap *tm_u,
 
   // Per-call state.
   StepDesc *d = a.desc;
-  const long long n = d->n + a.koff;
+  const long long n = d->n + koff;
   const int nrec = d->nrec;
   const int sx = d->sx - x0, sy = d->sy - y0, sz = d->sz;
   const bool src_here = d->src_active && sx >= 0 && sx < C::TX && sy >= 0 &&
@@ -584,7 +585,7 @@ __device__ __forceinline__ void sweep_cta(const CUtensorMap *tm_u,
         const int x = x0 + 4 * tx;
         if (y < a.ny && x < a.px) {
           const size_t idx = ((size_t)j * a.ny + y) * a.px + x;
-          E::store4_cs(reinterpret_cast<T *>(a.unext) + idx, res[v]);
+          E::store4_cs(reinterpret_cast<T *>(unext) + idx, res[v]);
           if constexpr ((kMode & kModeStoreD) != 0)
             __stcs(reinterpret_cast<float4 *>(a.dout + idx), dres[v]);
           if constexpr ((kMode & kModeGradAcc) != 0) {
@@ -667,7 +668,8 @@ __global__ void __launch_bounds__(C::THREADS, C::MINB)
                       const SweepArgs a) {
   extern __shared__ __align__(128) unsigned char smem_raw[];
   sweep_cta<C, kVelocityField, kMode>(&tm_u, &tm_up, &tm_c, a, a.k, blockIdx.x,
-                                      blockIdx.y, blockIdx.z, smem_raw);
+                                      blockIdx.y, blockIdx.z, smem_raw, a.unext,
+                                      a.koff);
 }
 
 // One shot of a batch (device memory, 128-byte aligned): its tensor maps for
@@ -676,7 +678,7 @@ struct alignas(128) BatchShot {
   CUtensorMap halo[2];  // u halo box over buf[0] / buf[1]
   CUtensorMap tile[2];  // u_prev tile box over buf[0] / buf[1]
   CUtensorMap cmap;     // v^2 dt^2 tile box
-  SweepArgs args;       // unext and koff are set per launch
+  SweepArgs args;       // unext and koff are not used: passed per launch
   void *buf[2];         // buf[0] holds the shot's step 0
   long long b0;         // batch step at which the shot takes its step 0
   int nsteps;           // the shot's step count: later batch steps skip it
@@ -718,18 +720,18 @@ __global__ void __launch_bounds__(C::THREADS, C::MINB)
   const long long n = k - sh.b0;  // the shot's own step
   if (n >= sh.nsteps) return;     // finished inside this group of steps
   const int cur = (int)(n & 1);   // buffer holding the shot's u
-  __shared__ SweepArgs a;         // uniform per CTA: read with broadcast loads
+  // The shot's arguments are read in place from the table (uniform loads
+  // through the read-only path): a shared copy would add static shared
+  // memory and leave room for only 3 FP32 CTAs per SM instead of 4. Thread 0
+  // issues every TMA load of the CTA, so its acquire orders them after the
+  // host's copy of the table.
   if (threadIdx.x == 0) {
-    a = sh.args;
-    a.unext = sh.buf[cur ^ 1];
-    a.koff = (int)n;
     tensormap_acquire(&sh.halo[cur]);
     tensormap_acquire(&sh.tile[cur ^ 1]);
     tensormap_acquire(&sh.cmap);
   }
-  __syncthreads();
-  sweep_cta<C, false, 0>(&sh.halo[cur], &sh.tile[cur ^ 1], &sh.cmap, a, co, bx,
-                         by, bz, smem_raw);
+  sweep_cta<C, false, 0>(&sh.halo[cur], &sh.tile[cur ^ 1], &sh.cmap, sh.args, co, bx,
+                         by, bz, smem_raw, sh.buf[cur ^ 1], (int)n);
 }
 
 }  // namespace gbw
