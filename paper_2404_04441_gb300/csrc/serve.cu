@@ -30,9 +30,9 @@ constexpr int kLayerPlanes = 256; // target z planes per CTA for batched shots
 // Admission stops adding shots once one batched step would launch more than
 // this many waves of CTAs (4 per SM): enough to keep the GPU full with small
 // shots, few enough that each resident shot gets a large share of it. On the
-// Poisson stream of shots it lowers p99 latency from 2.4 s to 1.6 s (FP32)
-// and 1.5 s to 1.2 s (FP16) for about 5 % (FP32) and 1 % (FP16) less
-// throughput than admitting up to the slot limit.
+// Poisson stream of shots it lowers p99 latency from 1.48 s to 1.22 s
+// (FP32) and 1.38 s to 1.11 s (FP16) against admitting up to the slot
+// limit, for about 5 % less throughput when many shots wait at once.
 constexpr int kTargetWaves = 6;
 
 struct Kind {
