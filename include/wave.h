@@ -33,7 +33,9 @@
  *    are validated before anything is launched.
  *  - Device-side waits are bounded: a kernel whose copy pipeline stalls for
  *    about two seconds records WAVE_ETIMEOUT, which the next synchronizing
- *    call (wave_synchronize, wave_get_field to host, ...) returns.
+ *    call (wave_synchronize, wave_get_field to host, ...) returns. Such a
+ *    recorded error (also WAVE_ENAN) stays until wave_reset or
+ *    wave_set_state replaces the state.
  */
 #ifndef GBWAVE_WAVE_H
 #define GBWAVE_WAVE_H
@@ -53,7 +55,9 @@ enum {
   WAVE_EUNSTABLE = -4, /* dt above the leapfrog stability limit (wave_cfl_dt) */
   WAVE_ETIMEOUT = -5,  /* a bounded device wait gave up */
   WAVE_EBUSY = -6,     /* result not ready yet */
-  WAVE_ENAN = -7,      /* non-finite values in the output */
+  WAVE_ENAN = -7,      /* a receiver trace holds a NaN or an infinity (checked
+                          after every wave_propagate, noalloc call and served
+                          shot; reported by the next synchronizing call) */
   WAVE_ENOTSUP = -8,   /* option not supported by this build */
   WAVE_ETOOBIG = -9    /* request exceeds the fixed scratch of wave_propagate_noalloc */
 };

@@ -27,6 +27,27 @@ constexpr double kW[5] = {-205.0 / 72.0, 8.0 / 5.0, -1.0 / 5.0, 8.0 / 315.0,
 // 8th-order central first-derivative weights (index 1..4), for the CPML.
 constexpr double kW1[5] = {0.0, 4.0 / 5.0, -1.0 / 5.0, 4.0 / 105.0, -1.0 / 280.0};
 
+// Device error word value: a receiver trace holds a NaN or an infinity.
+constexpr int kErrNonFinite = 2;
+
+// Records kErrNonFinite in *err (if no error is recorded yet) when any of the
+// n values is not finite.
+__global__ void finite_check_kernel(const float *v, long long n, int *err) {
+  bool bad = false;
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
+       i += (long long)gridDim.x * blockDim.x)
+    bad |= !isfinite(v[i]);
+  if (__syncthreads_or(bad) && threadIdx.x == 0) atomicCAS(err, 0, kErrNonFinite);
+}
+
+// Device error word (kErr* values) to a status.
+inline int device_error_status(int err) {
+  if (err == 0) return WAVE_OK;
+  if (err == kErrTimeout) return WAVE_ETIMEOUT;
+  if (err == kErrNonFinite) return WAVE_ENAN;
+  return WAVE_ECUDA;
+}
+
 // Velocity scan over the dense-in-x pitched buffer: max, and count of values
 // that are not finite and positive. Blocks take whole rows, threads adjacent
 // x (no per-element index division).

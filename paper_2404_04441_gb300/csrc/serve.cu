@@ -135,6 +135,7 @@ struct serve_ctx {
   // serves the next admission without being returned to the driver and
   // mapped again (which cost ~18 ms per shot of the stream).
   cudaMemPool_t pool = nullptr;
+  int sms = 1;
   int device = 0;
   std::chrono::steady_clock::time_point t0;
   std::mutex mu;
@@ -384,8 +385,15 @@ int upload_tables(serve_ctx *s) {
 void complete(serve_ctx *s, Request *q) {
   int status = WAVE_OK;
   int err = 0;
-  cudaError_t e = cudaMemcpyAsync(&err, &q->desc->error, sizeof(int),
-                                  cudaMemcpyDeviceToHost, s->stream);
+  if (q->r.nrec > 0) {  // NaN / infinity in the traces: WAVE_ENAN
+    finite_check_kernel<<<s->sms * 4, 256, 0, s->stream>>>(
+        q->host_traces ? q->stage : q->r.traces, (long long)q->r.nsteps * q->r.nrec,
+        &q->desc->error);
+  }
+  cudaError_t e = cudaGetLastError();
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(&err, &q->desc->error, sizeof(int), cudaMemcpyDeviceToHost,
+                        s->stream);
   if (e == cudaSuccess && q->host_traces)
     e = cudaMemcpyAsync(q->r.traces, q->stage,
                         (size_t)q->r.nsteps * q->r.nrec * 4,
@@ -394,7 +402,7 @@ void complete(serve_ctx *s, Request *q) {
   if (e != cudaSuccess)
     status = cuda_status(e);
   else if (err)
-    status = err == kErrTimeout ? WAVE_ETIMEOUT : WAVE_ECUDA;
+    status = device_error_status(err);
   release(s, q);
   finish(s, q, status);
 }
@@ -547,7 +555,8 @@ int serve_create(size_t hbm_budget_bytes, int max_slots, void *stream,
   {
     int sms = 0;
     WAVE_TRY_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, s->device));
-    s->target_ctas = (long long)kTargetWaves * 4 * std::max(sms, 1);
+    s->sms = std::max(sms, 1);
+    s->target_ctas = (long long)kTargetWaves * 4 * s->sms;
   }
   if (stream) {
     s->stream = reinterpret_cast<cudaStream_t>(stream);

@@ -284,8 +284,7 @@ int read_device_error(const wave_ctx *c) {
   WAVE_TRY_CUDA(cudaMemcpyAsync(&err, &c->d_desc->error, sizeof(int),
                                 cudaMemcpyDeviceToHost, c->stream));
   WAVE_TRY_CUDA(cudaStreamSynchronize(c->stream));
-  if (err == kErrTimeout) return WAVE_ETIMEOUT;
-  return err ? WAVE_ECUDA : WAVE_OK;
+  return device_error_status(err);
 }
 
 int upload_desc(wave_ctx *c) {
@@ -596,6 +595,11 @@ int wave_propagate(wave_ctx *c, const wave_shot *shot, int nsteps,
   }
   if ((s = upload_desc(c))) return s;
   if ((s = run_steps(c, nsteps))) return s;
+  if (nrec > 0) {  // NaN / infinity in the traces: WAVE_ENAN at the next sync
+    finite_check_kernel<<<c->sms * 4, 256, 0, st>>>(
+        c->host_desc.traces, (long long)nsteps * nrec, &c->d_desc->error);
+    WAVE_TRY_CUDA(cudaGetLastError());
+  }
   if (host_traces) {
     WAVE_TRY_CUDA(cudaMemcpyAsync(traces, c->traces.p, (size_t)nsteps * nrec * 4,
                                   cudaMemcpyDeviceToHost, st));
@@ -743,6 +747,7 @@ extern "C" {
 int wave_set_state(wave_ctx *c, const float *u, const float *u_prev,
                    int64_t step) {
   if (!c || !u || !u_prev || step < 0) return WAVE_EINVAL;
+  WAVE_TRY_CUDA(cudaMemsetAsync(&c->d_desc->error, 0, sizeof(int), c->stream));
   if (c->storage != WAVE_STORAGE_F32) return set_state_16(c, u, u_prev, step);
   c->cur = 0;
   const float *src[2] = {u, u_prev};
@@ -768,6 +773,8 @@ int wave_get_step(const wave_ctx *c, int64_t *step) {
 int wave_reset(wave_ctx *c) {
   if (!c) return WAVE_EINVAL;
   const size_t bytes = field_bytes(c);
+  // the state is replaced: an error recorded for the old one no longer holds
+  WAVE_TRY_CUDA(cudaMemsetAsync(&c->d_desc->error, 0, sizeof(int), c->stream));
   WAVE_TRY_CUDA(cudaMemsetAsync(c->buf[0], 0, bytes, c->stream));
   WAVE_TRY_CUDA(cudaMemsetAsync(c->buf[1], 0, bytes, c->stream));
   WAVE_TRY_CUDA(cudaMemsetAsync(
@@ -1149,9 +1156,12 @@ int gradient_impl(wave_ctx *c, const wave_shot *shot, int N,
   WAVE_TRY_CUDA(cudaMemcpyAsync(&errs[1], &dadj->error, 4, cudaMemcpyDeviceToHost, st));
   WAVE_TRY_CUDA(cudaStreamSynchronize(st));
   if (misfit && !data_is_resid) *misfit = hm;
+  // errors of the forward run (a timeout, or NaN in its traces), read before
+  // the reset clears them
+  const int ferr = read_device_error(c);
   if ((e = wave_reset(c))) return e;
-  if ((e = read_device_error(c))) return e;
-  if (errs[0] || errs[1]) return WAVE_ETIMEOUT;
+  if (ferr) return ferr;
+  if (errs[0] || errs[1]) return device_error_status(errs[0] ? errs[0] : errs[1]);
   return WAVE_OK;
 }
 
@@ -1417,11 +1427,15 @@ extern "C" int wave_propagate_noalloc(const wave_grid *g, const wave_spacing *h,
         halo[cur], tile[cur ^ 1], vmap, a);
   }
   WAVE_TRY_CUDA(cudaGetLastError());
+  if (nrec > 0) {  // NaN / infinity in the traces: WAVE_ENAN
+    finite_check_kernel<<<nd->sms * 4, 256, 0, cs>>>(traces, (long long)nsteps * nrec,
+                                                     &a.desc->error);
+    WAVE_TRY_CUDA(cudaGetLastError());
+  }
   int err = 0;
   WAVE_TRY_CUDA(cudaMemcpyAsync(&err, &a.desc->error, sizeof(int),
                                 cudaMemcpyDeviceToHost, cs));
   WAVE_TRY_CUDA(cudaStreamSynchronize(cs));
   *newest = nsteps & 1;
-  if (err == kErrTimeout) return WAVE_ETIMEOUT;
-  return err ? WAVE_ECUDA : WAVE_OK;
+  return device_error_status(err);
 }
