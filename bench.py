@@ -544,7 +544,10 @@ def main():
     ms = replica_max(ev0.elapsed_time(ev1), "cuda")
     clocks = sampler.summary(tw0, tw1)
     value = replica_value(npts, K, ms * 1e-3, world)
-    launches = (K // GRAPH_STEPS) * (GRAPH_STEPS + 1) + ((K % GRAPH_STEPS) + 1 if K % GRAPH_STEPS else 0)
+    # graph chunks of GRAPH_STEPS sweeps + a step-counter node, the remainder
+    # as direct sweeps + one counter kernel, and the final check of the traces
+    launches = (K // GRAPH_STEPS) * (GRAPH_STEPS + 1) + \
+        ((K % GRAPH_STEPS) + 1 if K % GRAPH_STEPS else 0) + (1 if nrec else 0)
     tr_ok = bool(torch.isfinite(traces_d[:K]).all().item())
     solver.close()
     del traces_d
