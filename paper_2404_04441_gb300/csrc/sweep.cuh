@@ -386,6 +386,27 @@ __device__ __forceinline__ void sweep_cta(const CUtensorMap *tm_u,
     for (int k = 0; k < 9; ++k) q[v][k] = make_float4(0.f, 0.f, 0.f, 0.f);
 
   const int col = 4 * tx + C::HX;  // smem column of this thread's first point
+
+  // kModeGradAcc: D and the (hi, lo) partial of the next plane to finish,
+  // loaded one plane ahead so that their latency overlaps a plane's work
+  // instead of stalling its epilogue.
+  float4 gd[C::VY], gh[C::VY], gl[C::VY];
+  auto grad_load = [&](int jj) {
+#pragma unroll
+    for (int v = 0; v < C::VY; ++v) {
+      const int y = y0 + ty * C::VY + v;
+      const int x = x0 + 4 * tx;
+      gd[v] = gh[v] = gl[v] = make_float4(0.f, 0.f, 0.f, 0.f);
+      if (jj < ze && y < a.ny && x < a.px) {
+        const size_t idx = ((size_t)jj * a.ny + y) * a.px + x;
+        gd[v] = __ldcs(reinterpret_cast<const float4 *>(a.dsrc + idx));
+        gh[v] = *reinterpret_cast<const float4 *>(a.ghi + idx);
+        gl[v] = *reinterpret_cast<const float4 *>(a.glo + idx);
+      }
+    }
+  };
+  if constexpr ((kMode & kModeGradAcc) != 0) grad_load(zb);
+
   int s = 0;
   for (int s0 = 0; s0 < NS; s0 += 9) {
 #pragma unroll
@@ -593,19 +614,18 @@ __device__ __forceinline__ void sweep_cta(const CUtensorMap *tm_u,
             // double-float partial; the host folds it into the FP64 time
             // sum at fixed step boundaries.
             const float4 uc4 = q[v][(p + 5) % 9];
-            const float4 d4 = __ldcs(reinterpret_cast<const float4 *>(a.dsrc + idx));
-            float4 *gh = reinterpret_cast<float4 *>(a.ghi + idx);
-            float4 *gl = reinterpret_cast<float4 *>(a.glo + idx);
-            float4 h = *gh, l = *gl;
+            const float4 d4 = gd[v];
+            float4 h = gh[v], l = gl[v];
             acc_exact(h.x, l.x, uc4.x, d4.x);
             acc_exact(h.y, l.y, uc4.y, d4.y);
             acc_exact(h.z, l.z, uc4.z, d4.z);
             acc_exact(h.w, l.w, uc4.w, d4.w);
-            *gh = h;
-            *gl = l;
+            *reinterpret_cast<float4 *>(a.ghi + idx) = h;
+            *reinterpret_cast<float4 *>(a.glo + idx) = l;
           }
         }
       }
+      if constexpr ((kMode & kModeGradAcc) != 0) grad_load(j + 1);
 
       // Receivers on this plane: stage the plane, then one thread per entry.
       if (j == rz) {
