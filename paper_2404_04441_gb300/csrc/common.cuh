@@ -12,6 +12,7 @@
 #include <cstdint>
 #include <cstring>
 #include <functional>
+#include <queue>
 #include <vector>
 
 #include "../../include/wave.h"
@@ -224,25 +225,47 @@ CUtensorMapDataType field_dtype(int storage) {
   return CU_TENSOR_MAP_DATA_TYPE_FLOAT32;
 }
 
-// Makespan of one launch in plane units: CTAs start in launch order (layer
-// by layer, tiles within a layer) on the earliest free of `slots` resident
-// slots and take (planes + kPreRoll) each; kPreRoll prices the 8 u-only
-// stages that refill the register queue at the start of every CTA.
+// Makespan of one launch, in units of one CTA stage (one plane) run alone.
+// CTAs start in launch order (layer by layer, tiles within a layer) as soon
+// as one of the `slots` resident places is free, and each takes planes +
+// kPreRoll stages: the 8 u-only stages that refill the register queue move
+// about 40 % of the bytes of a full stage and count as 4. All resident CTAs
+// advance together, one stage per 1 + C / slots units while C are resident:
+// a CTA alone is bound by load latency, and CTAs that share the GPU share its
+// HBM bandwidth. On GB300 a stage takes 0.37 us with few CTAs resident and
+// 0.72 us with all 608 places busy. Measured on 128^3 .. 448^3 and
+// 1024 x 1024 x 512, this model picks the fastest plan tried on all but
+// 384^3 (2.6 % slower than its best); counting time per CTA as fixed left
+// small grids with a third of the places idle (128^3: 106 against 174
+// Gpts/s, 192^3: 203 against 316).
 double layer_makespan(const std::vector<int> &chunks, long long ntiles,
                       long long slots) {
   constexpr double kPreRoll = 4.0;
-  std::vector<double> heap((size_t)std::min<long long>(slots, 1 << 20), 0.0);
-  double end = 0.0;
-  for (int c : chunks) {
-    for (long long t = 0; t < ntiles; ++t) {
-      std::pop_heap(heap.begin(), heap.end(), std::greater<double>());
-      const double e = heap.back() + c + kPreRoll;
-      heap.back() = e;
-      std::push_heap(heap.begin(), heap.end(), std::greater<double>());
-      end = std::max(end, e);
+  // finish points of the resident CTAs, in stages of common progress
+  std::priority_queue<double, std::vector<double>, std::greater<double>> live;
+  size_t layer = 0;
+  long long tile = 0;
+  auto next = [&](double &len) {
+    if (layer >= chunks.size()) return false;
+    len = chunks[layer] + kPreRoll;
+    if (++tile == ntiles) {
+      tile = 0;
+      ++layer;
+    }
+    return true;
+  };
+  double t = 0.0, prog = 0.0, len = 0.0;
+  while ((long long)live.size() < slots && next(len)) live.push(prog + len);
+  while (!live.empty()) {
+    const double nxt = live.top();
+    t += (nxt - prog) * (1.0 + (double)live.size() / (double)slots);
+    prog = nxt;
+    while (!live.empty() && live.top() <= prog) {
+      live.pop();
+      if (next(len)) live.push(prog + len);
     }
   }
-  return end;
+  return t;
 }
 
 // Split nz into at most kMaxLayers z layers: uniform splits and "k equal
@@ -278,11 +301,16 @@ std::vector<int> plan_layers(int nz, long long ntiles, long long slots) {
     score.push_back({w * ntiles / (double)slots + waves, i});
   }
   std::sort(score.begin(), score.end());
-  size_t best = score[0].second;
+  // Simulate the best few by that score and every uniform split (the first
+  // candidates): the score counts work, not idle places.
+  const size_t nuni = (size_t)std::min(nz, kMaxLayers);
+  std::vector<size_t> sim;
+  for (size_t i = 0; i < nuni; ++i) sim.push_back(i);
+  for (size_t r = 0; r < std::min<size_t>(score.size(), 48); ++r)
+    if (score[r].second >= nuni) sim.push_back(score[r].second);
+  size_t best = 0;
   double best_m = 1e300;
-  const size_t nsim = std::min<size_t>(score.size(), 48);
-  for (size_t r = 0; r < nsim; ++r) {
-    const size_t i = score[r].second;
+  for (size_t i : sim) {
     const double m = layer_makespan(cands[i], ntiles, slots);
     if (m < best_m - 1e-9) {
       best_m = m;
