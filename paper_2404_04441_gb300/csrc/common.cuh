@@ -228,8 +228,12 @@ CUtensorMapDataType field_dtype(int storage) {
 // Makespan of one launch, in units of one CTA stage (one plane) run alone.
 // CTAs start in launch order (layer by layer, tiles within a layer) as soon
 // as one of the `slots` resident places is free, and each takes planes +
-// kPreRoll stages: the 8 u-only stages that refill the register queue move
-// about 40 % of the bytes of a full stage and count as 4. All resident CTAs
+// preroll stages. For the FP32 sweep the 8 u-only stages that refill the
+// register queue move about 40 % of the bytes of a full stage and count as
+// 4. The 16-bit sweeps, bound by instruction issue and with a longer CTA
+// prologue (the scale state), run fastest with fewer, longer CTAs; a
+// preroll of 8 picks those plans (1024 x 1024 x 512: 448/64 against
+// 272/216/24, FP16 477 against 470 Gpts/s, BF16 487 against 481). All resident CTAs
 // advance together, one stage per 1 + C / slots units while C are resident:
 // a CTA alone is bound by load latency, and CTAs that share the GPU share its
 // HBM bandwidth. On GB300 a stage takes 0.37 us with few CTAs resident and
@@ -239,15 +243,14 @@ CUtensorMapDataType field_dtype(int storage) {
 // small grids with a third of the places idle (128^3: 106 against 174
 // Gpts/s, 192^3: 203 against 316).
 double layer_makespan(const std::vector<int> &chunks, long long ntiles,
-                      long long slots) {
-  constexpr double kPreRoll = 4.0;
+                      long long slots, double preroll = 4.0) {
   // finish points of the resident CTAs, in stages of common progress
   std::priority_queue<double, std::vector<double>, std::greater<double>> live;
   size_t layer = 0;
   long long tile = 0;
   auto next = [&](double &len) {
     if (layer >= chunks.size()) return false;
-    len = chunks[layer] + kPreRoll;
+    len = chunks[layer] + preroll;
     if (++tile == ntiles) {
       tile = 0;
       ++layer;
@@ -270,7 +273,8 @@ double layer_makespan(const std::vector<int> &chunks, long long ntiles,
 
 // Split nz into at most kMaxLayers z layers: uniform splits and "k equal
 // chunks then a tail of small chunks", scored by layer_makespan.
-std::vector<int> plan_layers(int nz, long long ntiles, long long slots) {
+std::vector<int> plan_layers(int nz, long long ntiles, long long slots,
+                             double preroll = 4.0) {
   std::vector<std::vector<int>> cands;
   for (int k = 1; k <= std::min(nz, kMaxLayers); ++k) {
     const int zc = (nz + k - 1) / k;
@@ -311,7 +315,7 @@ std::vector<int> plan_layers(int nz, long long ntiles, long long slots) {
   size_t best = 0;
   double best_m = 1e300;
   for (size_t i : sim) {
-    const double m = layer_makespan(cands[i], ntiles, slots);
+    const double m = layer_makespan(cands[i], ntiles, slots, preroll);
     if (m < best_m - 1e-9) {
       best_m = m;
       best = i;

@@ -417,7 +417,8 @@ static int create_impl(wave_ctx *c, const float *velocity) {
   const int nty = (c->ny + c->var.ty - 1) / c->var.ty;
   c->ntiles = ntx * nty;
   const std::vector<int> layers = plan_layers(
-      c->nz, (long long)c->ntiles, (long long)sms * c->ctas_per_sm);
+      c->nz, (long long)c->ntiles, (long long)sms * c->ctas_per_sm,
+      c->storage == WAVE_STORAGE_F32 ? 4.0 : 8.0);
   c->zchunk = *std::max_element(layers.begin(), layers.end());
   c->grid = dim3(ntx, nty, (unsigned)layers.size());
   if (c->grid.y > 65535) return WAVE_EINVAL;

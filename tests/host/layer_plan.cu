@@ -1,7 +1,7 @@
 // Host-only driver for the z-layer planner of the sweep (no GPU needed):
-// reads "nz ntiles slots" lines on stdin and prints the chosen plan and its
-// modelled makespan, or "makespan ntiles slots c1 c2 ..." lines and prints
-// the model's value for that plan.
+// reads "nz ntiles slots [preroll]" lines on stdin and prints the chosen
+// plan and its modelled makespan, or "makespan ntiles slots c1 c2 ..." lines
+// and prints the model's value for that plan (preroll 4).
 #include <cstdio>
 #include <cstring>
 #include <vector>
@@ -26,9 +26,10 @@ int main() {
     } else {
       int nz = 0;
       long long ntiles = 0, slots = 0;
-      if (std::sscanf(line, "%d %lld %lld", &nz, &ntiles, &slots) != 3) continue;
-      const std::vector<int> ch = plan_layers(nz, ntiles, slots);
-      std::printf("%.17g", layer_makespan(ch, ntiles, slots));
+      double pre = 4.0;
+      if (std::sscanf(line, "%d %lld %lld %lf", &nz, &ntiles, &slots, &pre) < 3) continue;
+      const std::vector<int> ch = plan_layers(nz, ntiles, slots, pre);
+      std::printf("%.17g", layer_makespan(ch, ntiles, slots, pre));
       for (int v : ch) std::printf(" %d", v);
       std::printf("\n");
     }

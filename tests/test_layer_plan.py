@@ -3,7 +3,7 @@ from the library's own source calls plan_layers and layer_makespan.
 
 A sweep launch gives each CTA an xy tile and a range of z planes (a layer).
 The planner splits nz into at most 16 layers by a makespan model in which a
-CTA runs planes + 4 stages and every resident CTA advances one stage per
+CTA runs planes + 4 stages (8 for the 16-bit sweeps) and every resident CTA advances one stage per
 1 + C / slots time units while C CTAs are resident (latency bound alone,
 sharing HBM bandwidth when many run). The fixed plans below are the ones
 measured fastest on GB300 among the plans timed for each grid (FP32, 32 x 16
@@ -58,6 +58,18 @@ def plan_of(planner, nx, ny, nz, slots=SLOTS):
 ])
 def test_plans_measured_fastest(planner, dims, expected):
     assert plan_of(planner, *dims)[1] == expected
+
+
+@pytest.mark.parametrize("dims,expected", [
+    ((1024, 1024, 512), [448, 64]),
+    ((512, 512, 512), [448, 64]),
+])
+def test_plans_16bit(planner, dims, expected):
+    # the 16-bit sweeps (64 x 8 tiles, same tile counts) plan with preroll 8
+    nx, ny, nz = dims
+    nt = -(-nx // 64) * -(-ny // 8)
+    line = planner(["%d %d %d 8" % (nz, nt, SLOTS)])[0].split()
+    assert [int(v) for v in line[1:]] == expected
 
 
 @pytest.mark.parametrize("nz", [1, 2, 7, 16, 17, 100, 255, 1040, 4096])
