@@ -1023,6 +1023,17 @@ int gradient_impl(wave_ctx *c, const wave_shot *shot, int N,
     WAVE_TRY_CUDA(cudaFuncSetAttribute(
         f, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)Cfg0::SMEM_BYTES));
 
+  // Receivers on the host once: each segment's wave_propagate would
+  // otherwise copy device-resident ones back and wait for the stream.
+  std::vector<int32_t> hrec;
+  if (nrec > 0 && is_device_ptr(rec_xyz)) {
+    hrec.resize((size_t)nrec * 3);
+    WAVE_TRY_CUDA(cudaMemcpyAsync(hrec.data(), rec_xyz, hrec.size() * 4,
+                                  cudaMemcpyDeviceToHost, st));
+    WAVE_TRY_CUDA(cudaStreamSynchronize(st));
+    rec_xyz = hrec.data();
+  }
+
   // Forward run from rest with a checkpoint (u^{sK}, u^{sK-1}) per segment.
   if ((e = wave_reset(c))) return e;
   for (int sgm = 0; sgm < ncp; ++sgm) {
