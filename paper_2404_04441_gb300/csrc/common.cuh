@@ -228,20 +228,23 @@ CUtensorMapDataType field_dtype(int storage) {
 // Makespan of one launch, in units of one CTA stage (one plane) run alone.
 // CTAs start in launch order (layer by layer, tiles within a layer) as soon
 // as one of the `slots` resident places is free, and each takes planes +
-// preroll stages. For the FP32 sweep the 8 u-only stages that refill the
-// register queue move about 40 % of the bytes of a full stage and count as
-// 4. The 16-bit sweeps, bound by instruction issue and with a longer CTA
-// prologue (the scale state), run fastest with fewer, longer CTAs; a
-// preroll of 8 picks those plans (1024 x 1024 x 512: 448/64 against
-// 272/216/24, FP16 477 against 470 Gpts/s, BF16 487 against 481). All resident CTAs
-// advance together, one stage per 1 + C / slots units while C are resident:
-// a CTA alone is bound by load latency, and CTAs that share the GPU share its
-// HBM bandwidth. On GB300 a stage takes 0.37 us with few CTAs resident and
-// 0.72 us with all 608 places busy. Measured on 128^3 .. 448^3 and
-// 1024 x 1024 x 512, this model picks the fastest plan tried on all but
-// 384^3 (2.6 % slower than its best); counting time per CTA as fixed left
-// small grids with a third of the places idle (128^3: 106 against 174
-// Gpts/s, 192^3: 203 against 316).
+// preroll stages. All resident CTAs advance together, one stage per
+// 1 + C / slots units while C are resident: a CTA alone is bound by load
+// latency, and CTAs that share the GPU share its HBM bandwidth. On GB300 a
+// stage takes 0.37 us with few CTAs resident and 0.72 us with all 608
+// places busy.
+//
+// preroll: for the FP32 sweep the 8 u-only stages that refill the register
+// queue move about 40 % of the bytes of a full stage and count as 4. The
+// 16-bit sweeps, bound by instruction issue and with a longer CTA prologue
+// (the scale state), run fastest with fewer, longer CTAs; a preroll of 8
+// picks those plans (1024 x 1024 x 512: 448/64 against 272/216/24, FP16 477
+// against 470 Gpts/s, BF16 487 against 481).
+//
+// Measured on 128^3 .. 448^3 and 1024 x 1024 x 512, this model picks the
+// fastest plan tried on all but 384^3 (2.6 % slower than its best).
+// Counting each CTA's time as fixed left small grids with a third of the
+// places idle (128^3: 106 against 174 Gpts/s, 192^3: 203 against 316).
 double layer_makespan(const std::vector<int> &chunks, long long ntiles,
                       long long slots, double preroll = 4.0) {
   // finish points of the resident CTAs, in stages of common progress
