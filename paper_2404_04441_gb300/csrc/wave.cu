@@ -51,6 +51,28 @@ struct Variant {
                  const CUtensorMap &, const SweepArgs &);
 };
 
+// Launch with programmatic dependent launch allowed: the grid's CTAs may
+// become resident while the previous kernel in the stream finishes, and wait
+// in the kernel (griddepcontrol.wait) for its completion before reading
+// anything. Used for the adjoint-gradient sweeps, issued back to back
+// without graphs (wave_gradient at 256^3: 0.186 against 0.189 s). Kernels of
+// other kinds in the stream (folds, copies) keep full stream ordering.
+template <class K, class... Args>
+void launch_pdl(K kernel, dim3 grid, int threads, size_t smem, cudaStream_t st,
+                const Args &...args) {
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = grid;
+  cfg.blockDim = dim3(threads);
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = st;
+  cudaLaunchAttribute at[1];
+  at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  at[0].val.programmaticStreamSerializationAllowed = 1;
+  cfg.attrs = at;
+  cfg.numAttrs = 1;
+  cudaLaunchKernelEx(&cfg, kernel, args...);
+}
+
 template <class C>
 void launch_sweep(dim3 grid, cudaStream_t st, const CUtensorMap &tu,
                   const CUtensorMap &tup, const CUtensorMap &tc,
@@ -909,9 +931,8 @@ namespace {
 template <int kMode>
 void launch_mode(const wave_ctx *c, const CUtensorMap &tu,
                  const CUtensorMap &tup, const SweepArgs &a) {
-  wave_sweep_kernel<Cfg0, false, kMode>
-      <<<c->grid, Cfg0::THREADS, Cfg0::SMEM_BYTES, c->stream>>>(tu, tup,
-                                                                 c->tm_c, a);
+  launch_pdl(wave_sweep_kernel<Cfg0, false, kMode>, c->grid, Cfg0::THREADS,
+             Cfg0::SMEM_BYTES, c->stream, tu, tup, c->tm_c, a);
 }
 
 // r = traces - observed; misfit += 1/2 sum r^2 in FP64.
