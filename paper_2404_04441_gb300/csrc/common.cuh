@@ -362,13 +362,17 @@ int encode_map(CUtensorMap *m, const void *base, int nx, int ny, int nz,
 }
 
 // Receivers (x, y, z) on the host -> entries {z, local index in tile, id,
-// tile} sorted by (tile, z, id) and per-tile start offsets (ntiles + 1).
-// Returns WAVE_EINVAL for a receiver outside the nx*ny*nz interior.
-int build_receiver_table(const int32_t *xyz, int nrec, int nx, int ny, int nz,
-                         int tx, int ty, int ntx, int ntiles,
-                         std::vector<int4> &entries, std::vector<int> &start) {
-  entries.resize(nrec);
-  start.assign((size_t)ntiles + 1, 0);
+// tile} sorted by (tile, z, id) and per-tile start offsets (ntiles + 1), in
+// caller-provided arrays of nrec and ntiles + 1 elements (no allocation:
+// the allocation-free entry point fills its fixed scratch image with it).
+// A tile is tx x ty points, tiles numbered y-major (tile = ty_index * ntx +
+// tx_index); the local index is (y mod ty) * tx + (x mod tx). Returns
+// WAVE_EINVAL for a receiver outside the nx*ny*nz interior (the arrays are
+// then unspecified).
+int fill_receiver_table(const int32_t *xyz, int nrec, int nx, int ny, int nz,
+                        int tx, int ty, int ntx, int ntiles, int4 *entries,
+                        int *start) {
+  std::fill(start, start + (size_t)ntiles + 1, 0);
   for (int r = 0; r < nrec; ++r) {
     const int x = xyz[3 * r], y = xyz[3 * r + 1], z = xyz[3 * r + 2];
     if (x < 0 || x >= nx || y < 0 || y >= ny || z < 0 || z >= nz)
@@ -377,13 +381,22 @@ int build_receiver_table(const int32_t *xyz, int nrec, int nx, int ny, int nz,
     entries[r] = make_int4(z, (y % ty) * tx + (x % tx), r, t);
     start[t + 1]++;
   }
-  std::sort(entries.begin(), entries.end(), [](const int4 &a, const int4 &b) {
+  std::sort(entries, entries + nrec, [](const int4 &a, const int4 &b) {
     if (a.w != b.w) return a.w < b.w;
     if (a.x != b.x) return a.x < b.x;
     return a.z < b.z;
   });
   for (int t = 0; t < ntiles; ++t) start[t + 1] += start[t];
   return WAVE_OK;
+}
+
+int build_receiver_table(const int32_t *xyz, int nrec, int nx, int ny, int nz,
+                         int tx, int ty, int ntx, int ntiles,
+                         std::vector<int4> &entries, std::vector<int> &start) {
+  entries.resize(nrec);
+  start.resize((size_t)ntiles + 1);
+  return fill_receiver_table(xyz, nrec, nx, ny, nz, tx, ty, ntx, ntiles,
+                             entries.data(), start.data());
 }
 
 }  // namespace

@@ -537,26 +537,10 @@ int wave_propagate(wave_ctx *c, const wave_shot *shot, int nsteps,
       std::memcpy(hrec.data(), rec_xyz, hrec.size() * 4);
     }
   }
-  const int tx = c->var.tx, ty = c->var.ty, ntx = (int)c->grid.x;
-  c->h_rec.resize(nrec);
-  c->h_rec_start.assign(c->ntiles + 1, 0);
-  std::vector<int> tile_of(nrec);
-  for (int r = 0; r < nrec; ++r) {
-    const int x = hrec[3 * r], y = hrec[3 * r + 1], z = hrec[3 * r + 2];
-    if (x < 0 || x >= c->nx || y < 0 || y >= c->ny || z < 0 || z >= c->nz)
-      return WAVE_EINVAL;
-    const int t = (y / ty) * ntx + (x / tx);
-    tile_of[r] = t;
-    c->h_rec[r] = make_int4(z, (y % ty) * tx + (x % tx), r, t);
-  }
-  std::sort(c->h_rec.begin(), c->h_rec.end(), [](const int4 &a, const int4 &b) {
-    if (a.w != b.w) return a.w < b.w;
-    if (a.x != b.x) return a.x < b.x;
-    return a.z < b.z;
-  });
-  for (int r = 0; r < nrec; ++r) c->h_rec_start[tile_of[r] + 1]++;
-  for (int t = 0; t < c->ntiles; ++t)
-    c->h_rec_start[t + 1] += c->h_rec_start[t];
+  if (build_receiver_table(hrec.data(), nrec, c->nx, c->ny, c->nz, c->var.tx,
+                           c->var.ty, (int)c->grid.x, c->ntiles, c->h_rec,
+                           c->h_rec_start))
+    return WAVE_EINVAL;
 
   // Source wavelet for this call's steps, FP64 on the host, stored FP32.
   StepDesc &d = c->host_desc;
@@ -1397,20 +1381,9 @@ extern "C" int wave_propagate_noalloc(const wave_grid *g, const wave_spacing *h,
   if (nrec > 0) {
     int *rs = reinterpret_cast<int *>(g_noalloc_image + off_rs);
     int4 *re = reinterpret_cast<int4 *>(g_noalloc_image + off_r);
-    std::memset(rs, 0, (ntiles + 1) * 4);
-    for (int r = 0; r < nrec; ++r) {
-      const int x = g_noalloc_rec_raw[3 * r], y = g_noalloc_rec_raw[3 * r + 1],
-                z = g_noalloc_rec_raw[3 * r + 2];
-      const int t = (y / C::TY) * ntx + (x / C::TX);
-      re[r] = make_int4(z, (y % C::TY) * C::TX + (x % C::TX), r, t);
-      rs[t + 1]++;
-    }
-    std::sort(re, re + nrec, [](const int4 &a, const int4 &b) {
-      if (a.w != b.w) return a.w < b.w;
-      if (a.x != b.x) return a.x < b.x;
-      return a.z < b.z;
-    });
-    for (size_t t = 0; t < ntiles; ++t) rs[t + 1] += rs[t];
+    if (fill_receiver_table(g_noalloc_rec_raw, nrec, nx, ny, nz, C::TX, C::TY,
+                            (int)ntx, (int)ntiles, re, rs))
+      return WAVE_EINVAL;
     d.traces = traces;
     d.rec = reinterpret_cast<const int4 *>(scr + off_r);
     d.rec_start = reinterpret_cast<const int *>(scr + off_rs);
