@@ -39,6 +39,7 @@ STORAGE = {"f32": 0, "bf16": 1, "f16": 2}
 WORKLOADS = {"1024x1024x512": wl.CFG_1024, "512cube": wl.CFG_512, "64cube": wl.CFG_SMALL}
 KERNEL_SOURCES = ["paper_2404_04441_gb300/csrc/sweep.cuh", "paper_2404_04441_gb300/csrc/ptx.cuh"]
 TRAFFIC_FILE = "profiles/sweep_f32_traffic.txt"
+TRAFFIC_FILE_16 = "profiles/sweep_16bit_traffic.txt"
 GRAPH_STEPS = 32
 
 
@@ -50,21 +51,25 @@ def kernel_hash():
     return h.hexdigest()[:16]
 
 
-def read_traffic(workload_name):
-    """Per-launch DRAM bytes of the sweep kernel from the committed ncu summary,
-    or None if absent or taken on different kernel sources."""
-    path = os.path.join(ROOT, TRAFFIC_FILE)
+def read_traffic(workload_name, path=TRAFFIC_FILE, prefix=""):
+    """Per-launch DRAM bytes of the sweep kernel from a committed ncu summary
+    (prefix "bf16:" / "f16:" selects a storage form in the 16-bit file), or
+    None if absent, unreadable or taken on different kernel sources."""
+    path = os.path.join(ROOT, path)
     if not os.path.exists(path):
         return None
     vals = {}
     for line in open(path):
         if ":" in line and not line.startswith("#"):
-            k, v = line.split(":", 1)
+            k, v = line.rsplit(":", 1)
             vals[k.strip()] = v.strip()
     if vals.get("kernel_source_sha256_16") != kernel_hash():
         return None
-    key = "dram_bytes_per_launch[%s]" % workload_name
-    return float(vals[key]) if key in vals else None
+    key = "dram_bytes_per_launch[%s%s]" % (prefix, workload_name)
+    try:
+        return float(vals[key]) if key in vals else None
+    except ValueError:
+        return None
 
 
 def measured_peaks():
@@ -616,6 +621,8 @@ def main():
                                "roofline": {"bound": "hbm", "achieved": ach,
                                             "peak": peaks["hbm_gbs"], "unit": "GB/s",
                                             "frac": ach / peaks["hbm_gbs"],
+                                            "traffic": read_traffic(cfg["name"], TRAFFIC_FILE_16,
+                                                                    name + ":"),
                                             "algorithmic_bytes_per_point": BYTES_PER_POINT_16}}
         if rank == 0:
             err = precision_errors(gw, torch)
