@@ -120,6 +120,36 @@ int wave_create(const wave_grid *g, const wave_spacing *h, double dt,
                 const float *velocity, int storage, void *stream,
                 wave_ctx **out);
 
+/*
+ * As wave_create, but the call returns before the velocity model has been
+ * read. Reading it, validating it and converting it to v^2 dt^2 run on a
+ * stream of the context's own in 32 depth slabs, overlapped with the first
+ * steps of a propagation from rest: on a host model the transfer (bound by
+ * the host link) is then hidden behind the stepping instead of preceding it.
+ *  - While the context is still at rest (zero fields, nothing stepped, no
+ *    wave_set_state), a wave_propagate with a source waits before its step k
+ *    only for the slabs that reach depth sz + 4k: the stencil of Eq. 1 moves
+ *    the field by at most R = 4 planes per step (Sec. 4.1), so every deeper
+ *    plane still holds zero and computes zero whatever its v^2 dt^2 (which
+ *    starts at zero). Any other call that steps or needs the model waits
+ *    for all of it first. Results are identical to those of wave_create.
+ *  - The caller's velocity buffer must stay valid and unchanged until a
+ *    synchronizing call on this context has returned (wave_synchronize, a
+ *    wave_propagate or wave_get_field with a host destination, wave_set_cpml,
+ *    wave_adjoint, wave_gradient) or the context is destroyed.
+ *  - Velocities that are not finite and positive (WAVE_EINVAL) and a dt
+ *    above the stability limit (WAVE_EUNSTABLE) are reported by that
+ *    synchronizing call and by every later synchronizing call (wave_reset
+ *    does not clear them); what was computed before is meaningless.
+ *  - The deferral applies to FP32 storage when the GPU can read the model
+ *    where it lies: device memory, pinned host memory, or pageable host
+ *    memory on systems whose GPU uses the host's page tables. Otherwise the
+ *    call behaves exactly like wave_create.
+ */
+int wave_create_async(const wave_grid *g, const wave_spacing *h, double dt,
+                      const float *velocity, int storage, void *stream,
+                      wave_ctx **out);
+
 /* Advance nsteps (>= 0) leapfrog steps with no source and no receivers. */
 int wave_step(wave_ctx *ctx, int nsteps);
 

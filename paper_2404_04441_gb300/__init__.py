@@ -18,7 +18,7 @@ __all__ = [
     "wave_synchronize", "wave_destroy", "wave_strerror", "wave_get_launch_info",
     "wave_selftest_wait", "wave_propagate_noalloc", "WaveSolver", "library_path",
     "ShotServer", "wave_adjoint", "wave_gradient", "WaveTraces", "wave_traces",
-    "wave_set_cpml",
+    "wave_set_cpml", "wave_create_async",
 ]
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
@@ -94,6 +94,7 @@ def load(path=None):
     lib.wave_cfl_dt.restype = ctypes.c_double
     lib.wave_create.argtypes = [ctypes.POINTER(_Grid), ctypes.POINTER(_Spacing),
                                 ctypes.c_double, vp, ip, vp, ctypes.POINTER(vp)]
+    lib.wave_create_async.argtypes = lib.wave_create.argtypes
     lib.wave_step.argtypes = [vp, ip]
     lib.wave_propagate.argtypes = [vp, ctypes.POINTER(_Shot), ip, vp, ip, vp]
     lib.wave_get_field.argtypes = [vp, ip, vp]
@@ -125,7 +126,7 @@ def load(path=None):
     lib.wave_propagate_noalloc.argtypes = [
         ctypes.POINTER(_Grid), ctypes.POINTER(_Spacing), ctypes.c_double, vp, vp, vp,
         ctypes.POINTER(_Shot), ctypes.c_int64, ip, vp, ip, vp, vp, ctypes.POINTER(ip)]
-    for name in ("wave_create", "wave_step", "wave_propagate", "wave_get_field",
+    for name in ("wave_create", "wave_create_async", "wave_step", "wave_propagate", "wave_get_field",
                  "wave_set_state", "wave_get_step", "wave_reset", "wave_synchronize",
                  "wave_get_launch_info", "wave_selftest_wait", "wave_propagate_noalloc",
                  "wave_set_cpml"):
@@ -180,8 +181,13 @@ def wave_cfl_dt(spacing, vmax):
     return lib.wave_cfl_dt(ctypes.byref(_Spacing(*map(float, spacing))), float(vmax))
 
 
-def wave_create(grid, spacing, dt, velocity, storage=0, stream=None):
-    """Create a context; ``grid`` = (nx, ny, nz); velocity has nx*ny*nz float32."""
+def wave_create(grid, spacing, dt, velocity, storage=0, stream=None, defer=False):
+    """Create a context; ``grid`` = (nx, ny, nz); velocity has nx*ny*nz float32.
+
+    ``defer=True`` calls wave_create_async: the model is read on the GPU after
+    the call returns (keep ``velocity`` alive and unchanged until the next
+    synchronizing call); errors in it are raised by that call.
+    """
     lib = load()
     nx, ny, nz = map(int, grid)
     g = _Grid(nx, ny, nz)
@@ -189,8 +195,9 @@ def wave_create(grid, spacing, dt, velocity, storage=0, stream=None):
     vptr = _ptr(velocity, "float32", nx * ny * nz, "velocity")
     out = ctypes.c_void_p()
     st = _default_stream() if stream is None else int(stream)
-    _check(lib.wave_create(ctypes.byref(g), ctypes.byref(h), float(dt), vptr, int(storage),
-                           st, ctypes.byref(out)), "wave_create")
+    fn = lib.wave_create_async if defer else lib.wave_create
+    _check(fn(ctypes.byref(g), ctypes.byref(h), float(dt), vptr, int(storage),
+              st, ctypes.byref(out)), "wave_create_async" if defer else "wave_create")
     return out
 
 
@@ -337,12 +344,15 @@ def wave_get_launch_info(ctx):
 class WaveSolver:
     """Owning wrapper of one context (destroyed with the object)."""
 
-    def __init__(self, grid, spacing, dt, velocity, storage=0, stream=None):
+    def __init__(self, grid, spacing, dt, velocity, storage=0, stream=None, defer=False):
         self.grid = tuple(int(v) for v in grid)
         self.spacing = tuple(float(v) for v in spacing)
         self.dt = float(dt)
         self.count = self.grid[0] * self.grid[1] * self.grid[2]
-        self.ctx = wave_create(self.grid, self.spacing, self.dt, velocity, storage, stream)
+        self.ctx = wave_create(self.grid, self.spacing, self.dt, velocity, storage, stream,
+                               defer)
+        # a deferred creation reads the model later: keep it alive until close
+        self._velocity = velocity if defer else None
 
     def step(self, nsteps):
         wave_step(self.ctx, nsteps)
@@ -385,6 +395,7 @@ class WaveSolver:
         if getattr(self, "ctx", None):
             wave_destroy(self.ctx)
             self.ctx = None
+        self._velocity = None
 
     def __del__(self):
         try:

@@ -12,7 +12,6 @@
 #include <cstdint>
 #include <cstring>
 #include <functional>
-#include <queue>
 #include <vector>
 
 #include "../../include/wave.h"
@@ -28,8 +27,10 @@ constexpr double kW[5] = {-205.0 / 72.0, 8.0 / 5.0, -1.0 / 5.0, 8.0 / 315.0,
 // 8th-order central first-derivative weights (index 1..4), for the CPML.
 constexpr double kW1[5] = {0.0, 4.0 / 5.0, -1.0 / 5.0, 4.0 / 105.0, -1.0 / 280.0};
 
-// Device error word value: a receiver trace holds a NaN or an infinity.
+// Device error word values: a receiver trace holds a NaN or an infinity; a
+// device-resident receiver point lies outside the interior.
 constexpr int kErrNonFinite = 2;
+constexpr int kErrBadReceiver = 3;
 
 // Records kErrNonFinite in *err (if no error is recorded yet) when any of the
 // n values is not finite.
@@ -46,6 +47,7 @@ inline int device_error_status(int err) {
   if (err == 0) return WAVE_OK;
   if (err == kErrTimeout) return WAVE_ETIMEOUT;
   if (err == kErrNonFinite) return WAVE_ENAN;
+  if (err == kErrBadReceiver) return WAVE_EINVAL;
   return WAVE_ECUDA;
 }
 
@@ -78,28 +80,123 @@ __global__ void scan_velocity_kernel(const float *v, int nx, int px,
   }
 }
 
-// c = v^2 dt^2 in place, in FP32 arithmetic (FP64 runs at a small fraction
-// of the FP32 rate on this part): v^2 = p + e exactly (TwoProduct with an
-// FMA, Ogita, Rump and Oishi 2005), dt^2 = dh + dl (the FP64 value split
-// into two floats), c = p dh + (p dl + e dh), small terms first: within
-// about one unit in the last place of the exact product, and the same on
-// every path. n is a multiple of 4 and c is 16-byte aligned (pitched field).
+// c = v^2 dt^2 in FP32 arithmetic (FP64 runs at a small fraction of the
+// FP32 rate on this part): v^2 = p + e exactly (TwoProduct with an FMA,
+// Ogita, Rump and Oishi 2005), dt^2 = dh + dl (the FP64 value split into two
+// floats), c = p dh + (p dl + e dh), small terms first: within about one unit
+// in the last place of the exact product, and the same on every path.
+__device__ __forceinline__ float v2dt2(float v, float dh, float dl) {
+  const float p = v * v;
+  const float e = fmaf(v, v, -p);
+  return fmaf(p, dh, fmaf(p, dl, e * dh));
+}
+
+// v2dt2 in place over a field; n is a multiple of 4 and c is 16-byte aligned
+// (pitched field).
 __global__ void velocity_to_c_kernel(float *c, long long n, float dh, float dl) {
   float4 *c4 = reinterpret_cast<float4 *>(c);
   const long long n4 = n / 4;
-  auto conv = [&](float v) {
-    const float p = v * v;
-    const float e = fmaf(v, v, -p);
-    return fmaf(p, dh, fmaf(p, dl, e * dh));
-  };
   for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n4;
        i += (long long)gridDim.x * blockDim.x) {
     float4 t = c4[i];
-    t.x = conv(t.x);
-    t.y = conv(t.y);
-    t.z = conv(t.z);
-    t.w = conv(t.w);
+    t.x = v2dt2(t.x, dh, dl);
+    t.y = v2dt2(t.y, dh, dl);
+    t.z = v2dt2(t.z, dh, dl);
+    t.w = v2dt2(t.w, dh, dl);
     c4[i] = t;
+  }
+}
+
+// One pass over a velocity model: c = v2dt2(v) into the pitched field (its
+// pitch columns [nx, px) written as zero), the largest velocity (float bits)
+// and the count of values that are not finite and positive. Rows of src are
+// sx floats apart: nx for a caller's dense array (device memory, or host
+// memory the GPU can read), px when converting a staged copy in place.
+// Blocks take whole rows; each thread loads four columns a block-width apart
+// before it stores any (more loads in flight on the host link).
+__global__ void __launch_bounds__(256, 4)
+    velocity_to_c_checked_kernel(const float *src, long long sx, float *c,
+                                 int nx, int px, long long rows, float dh,
+                                 float dl, unsigned *vmax_bits,
+                                 unsigned long long *nbad) {
+  unsigned local_max = 0;
+  unsigned long long local_bad = 0;
+  const int bw = blockDim.x;
+  for (long long r = blockIdx.x; r < rows; r += gridDim.x) {
+    const float *row = src + r * sx;
+    float *out = c + r * px;
+    for (int x0 = threadIdx.x; x0 < px; x0 += 4 * bw) {
+      float v[4];
+#pragma unroll
+      for (int j = 0; j < 4; ++j) {
+        const int x = x0 + j * bw;
+        v[j] = x < nx ? row[x] : 0.f;
+      }
+#pragma unroll
+      for (int j = 0; j < 4; ++j) {
+        const int x = x0 + j * bw;
+        if (x < nx) {
+          if (!(v[j] > 0.f) || !isfinite(v[j]))
+            ++local_bad;
+          else
+            local_max = max(local_max, __float_as_uint(v[j]));
+        }
+        if (x < px) out[x] = x < nx ? v2dt2(v[j], dh, dl) : 0.f;
+      }
+    }
+  }
+  for (int o = 16; o > 0; o >>= 1) {
+    local_max = max(local_max, __shfl_xor_sync(0xffffffffu, local_max, o));
+    local_bad += __shfl_xor_sync(0xffffffffu, local_bad, o);
+  }
+  if ((threadIdx.x & 31) == 0) {
+    atomicMax(vmax_bits, local_max);
+    if (local_bad) atomicAdd(nbad, local_bad);
+  }
+}
+
+// The velocity pass over a slab stored without row padding (px == nx): one
+// contiguous run of n4 float4 in src and in c (both 16-byte aligned). Each
+// thread keeps four 16-byte loads in flight, so a few blocks saturate the
+// host link when src is host memory the GPU reads directly.
+__global__ void __launch_bounds__(256, 4)
+    velocity_to_c_dense_kernel(const float4 *src, float4 *c, long long n4,
+                               float dh, float dl, unsigned *vmax_bits,
+                               unsigned long long *nbad) {
+  unsigned local_max = 0;
+  unsigned long long local_bad = 0;
+  const long long stride = (long long)gridDim.x * blockDim.x;
+  for (long long i0 = blockIdx.x * (long long)blockDim.x + threadIdx.x; i0 < n4;
+       i0 += 4 * stride) {
+    float4 v[4];
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+      const long long i = i0 + j * stride;
+      v[j] = i < n4 ? src[i] : make_float4(1.f, 1.f, 1.f, 1.f);
+    }
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+      const long long i = i0 + j * stride;
+      if (i >= n4) continue;
+      const float e[4] = {v[j].x, v[j].y, v[j].z, v[j].w};
+#pragma unroll
+      for (int k = 0; k < 4; ++k) {
+        if (!(e[k] > 0.f) || !isfinite(e[k]))
+          ++local_bad;
+        else
+          local_max = max(local_max, __float_as_uint(e[k]));
+      }
+      c[i] = make_float4(v2dt2(e[0], dh, dl), v2dt2(e[1], dh, dl),
+                         v2dt2(e[2], dh, dl), v2dt2(e[3], dh, dl));
+    }
+  }
+  for (int o = 16; o > 0; o >>= 1) {
+    local_max = max(local_max, __shfl_xor_sync(0xffffffffu, local_max, o));
+    local_bad += __shfl_xor_sync(0xffffffffu, local_bad, o);
+  }
+  if ((threadIdx.x & 31) == 0) {
+    atomicMax(vmax_bits, local_max);
+    if (local_bad) atomicAdd(nbad, local_bad);
   }
 }
 
@@ -245,86 +342,181 @@ CUtensorMapDataType field_dtype(int storage) {
 // fastest plan tried on all but 384^3 (2.6 % slower than its best).
 // Counting each CTA's time as fixed left small grids with a third of the
 // places idle (128^3: 106 against 174 Gpts/s, 192^3: 203 against 316).
-double layer_makespan(const std::vector<int> &chunks, long long ntiles,
+//
+// The simulation keeps the resident CTAs as groups that finish at the same
+// time (CTAs started together with the same layer length), so its cost
+// grows with the number of distinct finish times, not with the number of
+// CTAs; it uses fixed storage only. Returns a huge value if the groups
+// outgrow that storage (the plan is then never chosen).
+constexpr int kPlanGroups = 1024;
+
+double layer_makespan(const int *chunks, int nchunks, long long ntiles,
                       long long slots, double preroll = 4.0) {
-  // finish points of the resident CTAs, in stages of common progress
-  std::priority_queue<double, std::vector<double>, std::greater<double>> live;
-  size_t layer = 0;
-  long long tile = 0;
-  auto next = [&](double &len) {
-    if (layer >= chunks.size()) return false;
-    len = chunks[layer] + preroll;
-    if (++tile == ntiles) {
-      tile = 0;
-      ++layer;
+  double fin[kPlanGroups];
+  long long cnt[kPlanGroups];
+  int ng = 0;
+  int layer = 0;
+  long long tile = 0;  // next tile of `layer` to start
+  long long live = 0;  // resident CTAs
+  bool overflow = false;
+  // start k CTAs at progress point p, in launch order
+  auto start = [&](long long k, double p) {
+    while (k > 0 && layer < nchunks) {
+      const long long m = std::min(k, ntiles - tile);
+      const double f = p + (chunks[layer] + preroll);
+      int g = 0;
+      while (g < ng && fin[g] != f) ++g;
+      if (g == ng) {
+        if (ng == kPlanGroups) {
+          overflow = true;
+          return;
+        }
+        fin[ng] = f;
+        cnt[ng++] = 0;
+      }
+      cnt[g] += m;
+      live += m;
+      k -= m;
+      tile += m;
+      if (tile == ntiles) {
+        tile = 0;
+        ++layer;
+      }
     }
-    return true;
   };
-  double t = 0.0, prog = 0.0, len = 0.0;
-  while ((long long)live.size() < slots && next(len)) live.push(prog + len);
-  while (!live.empty()) {
-    const double nxt = live.top();
-    t += (nxt - prog) * (1.0 + (double)live.size() / (double)slots);
+  double t = 0.0, prog = 0.0;
+  start(slots, 0.0);
+  while (ng > 0 && !overflow) {
+    double nxt = fin[0];
+    for (int g = 1; g < ng; ++g) nxt = std::min(nxt, fin[g]);
+    t += (nxt - prog) * (1.0 + (double)live / (double)slots);
     prog = nxt;
-    while (!live.empty() && live.top() <= prog) {
-      live.pop();
-      if (next(len)) live.push(prog + len);
+    long long freed = 0;
+    for (int g = 0; g < ng;) {
+      if (fin[g] <= prog) {
+        freed += cnt[g];
+        fin[g] = fin[ng - 1];
+        cnt[g] = cnt[ng - 1];
+        --ng;
+      } else {
+        ++g;
+      }
     }
+    live -= freed;
+    start(freed, prog);
   }
-  return t;
+  return overflow ? 1e300 : t;
 }
 
-// Split nz into at most kMaxLayers z layers: uniform splits and "k equal
-// chunks then a tail of small chunks", scored by layer_makespan.
-std::vector<int> plan_layers(int nz, long long ntiles, long long slots,
-                             double preroll = 4.0) {
-  std::vector<std::vector<int>> cands;
-  for (int k = 1; k <= std::min(nz, kMaxLayers); ++k) {
-    const int zc = (nz + k - 1) / k;
-    std::vector<int> ch;
-    for (int z = 0; z < nz; z += zc) ch.push_back(std::min(zc, nz - z));
-    cands.push_back(ch);
+double layer_makespan(const std::vector<int> &chunks, long long ntiles,
+                      long long slots, double preroll = 4.0) {
+  return layer_makespan(chunks.data(), (int)chunks.size(), ntiles, slots,
+                        preroll);
+}
+
+// Candidate plans for plan_layers, numbered in a fixed order: first the
+// uniform splits into k = 1..min(nz, 16) layers, then "layers of a planes,
+// the rest, then `tail` layers of b planes" for a = 16, 24, .. < nz, b in
+// {8, 16, 24, 32, 48, 64} below a, tail = 1..4, keeping those of at most 16
+// layers. Writes candidate `idx` to out and returns its layer count (0 when
+// idx is past the last candidate).
+struct PlanCandidate {
+  int a, b, tail;  // a = 0: uniform split into b layers
+};
+
+int plan_candidate_chunks(int nz, const PlanCandidate &pc, int *out) {
+  int n = 0;
+  if (pc.a == 0) {
+    const int zc = (nz + pc.b - 1) / pc.b;
+    for (int z = 0; z < nz; z += zc) out[n++] = std::min(zc, nz - z);
+    return n;
   }
-  for (int a = 16; a < nz; a += 8) {
-    for (int b : {8, 16, 24, 32, 48, 64}) {
+  int rest = nz - pc.tail * pc.b;
+  const int full = rest / pc.a;
+  if (full + (rest % pc.a > 0) + pc.tail > kMaxLayers) return 0;
+  while (rest >= pc.a) {
+    out[n++] = pc.a;
+    rest -= pc.a;
+  }
+  if (rest > 0) out[n++] = rest;
+  for (int t = 0; t < pc.tail; ++t) out[n++] = pc.b;
+  return n;
+}
+
+// Split nz into at most kMaxLayers z layers, chosen by layer_makespan: a
+// cheap score (work plus waves) ranks all candidates; every uniform split
+// and the best-ranked others (among the 48 best scores) are simulated, and
+// the first plan with the smallest makespan wins. Writes the plan to out and
+// returns its layer count. Fixed storage only (no allocation).
+int plan_layers(int nz, long long ntiles, long long slots, double preroll,
+                int out[kMaxLayers]) {
+  constexpr int kTop = 48;
+  static const int kTail[6] = {8, 16, 24, 32, 48, 64};
+  const int nuni = std::min(nz, kMaxLayers);
+  // the kTop best (score, index) pairs, ascending
+  double tscore[kTop] = {};
+  int tidx[kTop] = {};
+  PlanCandidate tcand[kTop] = {};
+  int ntop = 0;
+  int idx = 0;
+  int ch[kMaxLayers];
+  auto consider = [&](const PlanCandidate &pc) {
+    const int n = plan_candidate_chunks(nz, pc, ch);
+    if (n == 0) return;
+    double w = 0;
+    for (int i = 0; i < n; ++i) w += ch[i] + 4.0;
+    const double waves = (double)ntiles * n / (double)slots;
+    const double sc = w * ntiles / (double)slots + waves;
+    const int my = idx++;
+    if (ntop == kTop && !(sc < tscore[kTop - 1])) return;
+    int pos = ntop < kTop ? ntop++ : kTop - 1;
+    while (pos > 0 && sc < tscore[pos - 1]) {
+      tscore[pos] = tscore[pos - 1];
+      tidx[pos] = tidx[pos - 1];
+      tcand[pos] = tcand[pos - 1];
+      --pos;
+    }
+    tscore[pos] = sc;
+    tidx[pos] = my;
+    tcand[pos] = pc;
+  };
+  for (int k = 1; k <= nuni; ++k) consider({0, k, 0});
+  for (int a = 16; a < nz; a += 8)
+    for (int b : kTail) {
       if (b >= a) continue;
       for (int tail = 1; tail <= 4; ++tail) {
         if (a + tail * b > nz) break;
-        std::vector<int> ch;
-        int rest = nz - tail * b;
-        while (rest >= a) { ch.push_back(a); rest -= a; }
-        if (rest > 0) ch.push_back(rest);
-        for (int t = 0; t < tail; ++t) ch.push_back(b);
-        if ((int)ch.size() <= kMaxLayers) cands.push_back(ch);
+        consider({a, b, tail});
       }
     }
-  }
-  // Cheap pre-filter by a wave model, then simulate the best few.
-  std::vector<std::pair<double, size_t>> score;
-  for (size_t i = 0; i < cands.size(); ++i) {
-    double w = 0;
-    for (int c : cands[i]) w += c + 4.0;
-    const double waves = (double)ntiles * cands[i].size() / (double)slots;
-    score.push_back({w * ntiles / (double)slots + waves, i});
-  }
-  std::sort(score.begin(), score.end());
-  // Simulate the best few by that score and every uniform split (the first
-  // candidates): the score counts work, not idle places.
-  const size_t nuni = (size_t)std::min(nz, kMaxLayers);
-  std::vector<size_t> sim;
-  for (size_t i = 0; i < nuni; ++i) sim.push_back(i);
-  for (size_t r = 0; r < std::min<size_t>(score.size(), 48); ++r)
-    if (score[r].second >= nuni) sim.push_back(score[r].second);
-  size_t best = 0;
   double best_m = 1e300;
-  for (size_t i : sim) {
-    const double m = layer_makespan(cands[i], ntiles, slots, preroll);
+  int best_n = 0;
+  auto simulate = [&](const PlanCandidate &pc) {
+    const int n = plan_candidate_chunks(nz, pc, ch);
+    const double m = layer_makespan(ch, n, ntiles, slots, preroll);
     if (m < best_m - 1e-9) {
       best_m = m;
-      best = i;
+      best_n = n;
+      std::copy(ch, ch + n, out);
     }
-  }
-  return cands[best];
+  };
+  for (int k = 1; k <= nuni; ++k) simulate({0, k, 0});
+  for (int r = 0; r < ntop; ++r)
+    if (tidx[r] >= nuni) simulate(tcand[r]);
+  return best_n;
+}
+
+std::vector<int> plan_layers(int nz, long long ntiles, long long slots,
+                             double preroll = 4.0) {
+  int out[kMaxLayers];
+  const int n = plan_layers(nz, ntiles, slots, preroll, out);
+  return std::vector<int>(out, out + n);
+}
+
+void set_layers(SweepArgs &a, const int *ch, int n) {
+  a.nlayers = n;
+  a.zl[0] = 0;
+  for (int l = 0; l < n; ++l) a.zl[l + 1] = a.zl[l] + ch[l];
 }
 
 void set_layers(SweepArgs &a, const std::vector<int> &ch) {
@@ -397,6 +589,182 @@ int build_receiver_table(const int32_t *xyz, int nrec, int nx, int ny, int nz,
   start.resize((size_t)ntiles + 1);
   return fill_receiver_table(xyz, nrec, nx, ny, nz, tx, ty, ntx, ntiles,
                              entries.data(), start.data());
+}
+
+// ---------------------------------------------------------------------------
+// Receiver table built on the device: the same entries {z, local, id, tile},
+// sorted by (tile, z, id), and per-tile starts as fill_receiver_table, from
+// receivers in device memory, with no copy to the host and no stream
+// synchronisation. Receivers outside the interior are left out of the table
+// and recorded as kErrBadReceiver in the error word. Four launches:
+// per-tile counts, their exclusive scan, a scatter of the keys (z << 32 | id)
+// into the tiles' segments, and a sort of each segment (one block per tile).
+struct RecGeom {
+  int nx, ny, nz;   // interior
+  int tx, ty, ntx;  // tile size and tiles along x
+  int ntiles;
+};
+
+constexpr int kRecScanThreads = 1024;
+constexpr int kRecSortThreads = 256;
+constexpr int kRecSortShared = 2048;  // segments up to this size sort in shared memory
+
+__device__ __forceinline__ bool rec_point(const int32_t *xyz, long long r,
+                                          const RecGeom &g, int &x, int &y,
+                                          int &z) {
+  x = xyz[3 * r];
+  y = xyz[3 * r + 1];
+  z = xyz[3 * r + 2];
+  return x >= 0 && x < g.nx && y >= 0 && y < g.ny && z >= 0 && z < g.nz;
+}
+
+__global__ void rec_count_kernel(const int32_t *xyz, int nrec, RecGeom g,
+                                 int *cnt, int *err) {
+  for (long long r = blockIdx.x * (long long)blockDim.x + threadIdx.x; r < nrec;
+       r += (long long)gridDim.x * blockDim.x) {
+    int x, y, z;
+    if (!rec_point(xyz, r, g, x, y, z)) {
+      atomicCAS(err, 0, kErrBadReceiver);
+      continue;
+    }
+    atomicAdd(&cnt[(y / g.ty) * g.ntx + x / g.tx], 1);
+  }
+}
+
+// One block: start[t] = sum of cnt[0..t), start[ntiles] = total; cnt[t] is
+// overwritten with start[t] (the scatter's cursor).
+__global__ void __launch_bounds__(kRecScanThreads)
+    rec_scan_kernel(int *cnt, int *start, int ntiles) {
+  __shared__ int warp_sum[kRecScanThreads / 32];
+  const int tid = threadIdx.x;
+  const long long per = ((long long)ntiles + kRecScanThreads - 1) / kRecScanThreads;
+  const long long b = tid * per;
+  const long long e = b + per < (long long)ntiles ? b + per : (long long)ntiles;
+  int sum = 0;
+  for (long long i = b; i < e; ++i) sum += cnt[i];
+  // exclusive scan of the per-thread sums
+  int v = sum;
+  for (int o = 1; o < 32; o <<= 1) {
+    const int n = __shfl_up_sync(0xffffffffu, v, o);
+    if ((tid & 31) >= o) v += n;
+  }
+  if ((tid & 31) == 31) warp_sum[tid >> 5] = v;
+  __syncthreads();
+  if (tid < 32) {
+    int w = warp_sum[tid];
+    for (int o = 1; o < 32; o <<= 1) {
+      const int n = __shfl_up_sync(0xffffffffu, w, o);
+      if (tid >= o) w += n;
+    }
+    warp_sum[tid] = w;
+  }
+  __syncthreads();
+  int run = v - sum + ((tid >> 5) > 0 ? warp_sum[(tid >> 5) - 1] : 0);
+  for (long long i = b; i < e; ++i) {
+    const int c = cnt[i];
+    start[i] = run;
+    cnt[i] = run;
+    run += c;
+  }
+  if (tid == kRecScanThreads - 1) start[ntiles] = warp_sum[31];
+}
+
+__global__ void rec_scatter_kernel(const int32_t *xyz, int nrec, RecGeom g,
+                                   int *cursor, unsigned long long *keys) {
+  for (long long r = blockIdx.x * (long long)blockDim.x + threadIdx.x; r < nrec;
+       r += (long long)gridDim.x * blockDim.x) {
+    int x, y, z;
+    if (!rec_point(xyz, r, g, x, y, z)) continue;
+    const int pos = atomicAdd(&cursor[(y / g.ty) * g.ntx + x / g.tx], 1);
+    keys[pos] = ((unsigned long long)(unsigned)z << 32) | (unsigned long long)r;
+  }
+}
+
+// Ascending bitonic sort of a[0, n) by one block, for any n: the network of
+// the padded power-of-two size N in the form whose every comparator puts the
+// smaller key at the lower index (the first stage of each merge compares
+// mirror positions), so the padding, +infinity at [n, N), never moves and
+// comparators that reach it are skipped.
+__device__ void block_bitonic_sort(unsigned long long *a, long long n) {
+  long long N = 1;
+  while (N < n) N <<= 1;
+  for (long long k = 2; k <= N; k <<= 1) {
+    for (long long j = k >> 1; j > 0; j >>= 1) {
+      for (long long i = threadIdx.x; i < N / 2; i += blockDim.x) {
+        const long long blk = i / j, off = i - blk * j;
+        long long lo, hi;
+        if (j == (k >> 1)) {  // mirror stage of a merge of size k
+          lo = blk * k + off;
+          hi = blk * k + k - 1 - off;
+        } else {
+          lo = blk * 2 * j + off;
+          hi = lo + j;
+        }
+        if (hi < n) {
+          const unsigned long long p = a[lo], q = a[hi];
+          if (q < p) {
+            a[lo] = q;
+            a[hi] = p;
+          }
+        }
+      }
+      __syncthreads();
+    }
+  }
+}
+
+__global__ void __launch_bounds__(kRecSortThreads)
+    rec_sort_kernel(const int32_t *xyz, RecGeom g, const int *start,
+                    unsigned long long *keys, int4 *entries) {
+  __shared__ unsigned long long sk[kRecSortShared];
+  for (int t = blockIdx.x; t < g.ntiles; t += gridDim.x) {
+    const int s0 = start[t], n = start[t + 1] - s0;
+    if (n == 0) continue;
+    unsigned long long *a = keys + s0;
+    if (n <= kRecSortShared) {
+      for (int i = threadIdx.x; i < n; i += blockDim.x) sk[i] = a[i];
+      __syncthreads();
+      a = sk;
+    }
+    if (n > 1) block_bitonic_sort(a, n);
+    for (int i = threadIdx.x; i < n; i += blockDim.x) {
+      const unsigned long long k = a[i];
+      const int r = (int)(k & 0xffffffffu);
+      const int x = xyz[3 * (long long)r], y = xyz[3 * (long long)r + 1];
+      entries[s0 + i] = make_int4((int)(k >> 32), (y % g.ty) * g.tx + (x % g.tx), r, t);
+    }
+    __syncthreads();  // sk is reused by the block's next tile
+  }
+}
+
+// Enqueue the four launches on st. cnt and start hold ntiles + 1 ints, keys
+// nrec, entries nrec; err is the device error word. Requires nrec >= 1.
+int build_receiver_table_device(const int32_t *xyz, int nrec, const RecGeom &g,
+                                int *cnt, int *start, unsigned long long *keys,
+                                int4 *entries, int *err, int sms,
+                                cudaStream_t st) {
+  WAVE_TRY_CUDA(cudaMemsetAsync(cnt, 0, ((size_t)g.ntiles + 1) * sizeof(int), st));
+  const int blocks = (int)std::min<long long>(((long long)nrec + 255) / 256, 4ll * sms);
+  rec_count_kernel<<<blocks, 256, 0, st>>>(xyz, nrec, g, cnt, err);
+  rec_scan_kernel<<<1, kRecScanThreads, 0, st>>>(cnt, start, g.ntiles);
+  rec_scatter_kernel<<<blocks, 256, 0, st>>>(xyz, nrec, g, cnt, keys);
+  rec_sort_kernel<<<(int)std::min<long long>(g.ntiles, 16ll * sms), kRecSortThreads, 0,
+                    st>>>(xyz, g, start, keys, entries);
+  WAVE_TRY_CUDA(cudaGetLastError());
+  return WAVE_OK;
+}
+
+// Receivers within w cells of a face (the CPML shell), as {x, y, z, id} in
+// any order, counted in *count (zeroed by the caller).
+__global__ void rec_shell_kernel(const int32_t *xyz, int nrec, RecGeom g, int w,
+                                 int4 *out, int *count) {
+  for (long long r = blockIdx.x * (long long)blockDim.x + threadIdx.x; r < nrec;
+       r += (long long)gridDim.x * blockDim.x) {
+    int x, y, z;
+    if (!rec_point(xyz, r, g, x, y, z)) continue;
+    if (x < w || x >= g.nx - w || y < w || y >= g.ny - w || z < w || z >= g.nz - w)
+      out[atomicAdd(count, 1)] = make_int4(x, y, z, (int)r);
+  }
 }
 
 }  // namespace

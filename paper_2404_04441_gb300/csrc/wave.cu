@@ -12,6 +12,7 @@
 #include <cstdlib>
 #include <cstring>
 #include <functional>
+#include <mutex>
 #include <new>
 #include <vector>
 
@@ -128,6 +129,8 @@ __global__ void selftest_wait_kernel(uint64_t limit_ns, int *out) {
 
 }  // namespace
 
+constexpr int kUploadChunks = 32;  // z slabs of the deferred velocity pass
+
 struct wave_ctx {
   int nx = 0, ny = 0, nz = 0;
   int px = 0;       // row pitch of the v^2 dt^2 field (floats, multiple of 4)
@@ -139,8 +142,21 @@ struct wave_ctx {
   cudaStream_t stream = nullptr;
   cudaStream_t capture_stream = nullptr;
   int device = 0;
+  void *base = nullptr;  // one allocation: both wavefields, c, desc, scratch
   void *buf[2] = {nullptr, nullptr};  // buf[cur] = u, buf[cur ^ 1] = u_prev
   float *c = nullptr;
+  cudaEvent_t ev_aux = nullptr;  // joins work of capture_stream into stream
+  // Deferred velocity pass (wave_create_async).
+  cudaStream_t upload_stream = nullptr;
+  cudaEvent_t ev_upload_start = nullptr;
+  cudaEvent_t chunk_ev[kUploadChunks] = {};
+  int chunk_z0[kUploadChunks] = {};
+  int nchunks = 0;
+  int chunk_next = 0;           // first slab the main stream has not waited for
+  bool upload_pending = false;  // the main stream has not waited for every slab
+  bool model_checked = true;    // the host holds the velocity pass's verdict
+  int model_status = WAVE_OK;   // that verdict (WAVE_EINVAL, WAVE_EUNSTABLE)
+  bool at_rest = true;          // zero fields since creation or reset
   int cur = 0;
   int64_t step = 0;
   StepDesc *d_desc = nullptr;
@@ -150,12 +166,17 @@ struct wave_ctx {
   dim3 grid;
   int zchunk = 0, ctas_per_sm = 0, ntiles = 0;
   SweepArgs args{};
-  DeviceBuf wavelet, rec, rec_start, traces;
+  // Per-call tables in one device buffer (one cudaFree at destroy): the
+  // source wavelet, the receiver table and its build arrays, staged host
+  // receivers, and staged traces for a host destination.
+  DeviceBuf tables;
+  float *d_wavelet = nullptr;
+  int4 *d_rec = nullptr;            // receiver table, sorted by (tile, z)
+  int *d_rec_start = nullptr;       // per-tile starts (ntiles + 1)
   cudaGraphExec_t graph[2] = {nullptr, nullptr};
   int graph_steps = 32;
   StepDesc host_desc{};
-  std::vector<int4> h_rec;
-  std::vector<int> h_rec_start;
+  std::vector<int32_t> h_rec_raw;  // host receivers, staged for upload
   std::vector<float> h_wavelet;
   unsigned char scale_image[32];  // host staging of the 16-bit scale state
   // CPML layer (wave_set_cpml).
@@ -164,11 +185,11 @@ struct wave_ctx {
   std::vector<void *> cpml_mem;
   DeviceBuf srec;            // receivers within w of a face: {x, y, z, id}
   int *d_nsrec = nullptr;    // their count (device: graphs stay valid)
-  std::vector<int4> h_srec;
-  int cpml_nsrec_host = 0;
 };
 
 namespace {
+
+size_t round_up256(size_t x) { return (x + 255) & ~size_t(255); }
 
 int make_map(CUtensorMap *m, const void *base, const wave_ctx *c, int box_x,
              int box_y, CUtensorMapDataType dtype, int pitch, int esize) {
@@ -257,13 +278,6 @@ int zero_cpml(wave_ctx *c) {
   return WAVE_OK;
 }
 
-// A point whose update carries a layer term: within w = npml + 4 of a face.
-bool cpml_in_shell(const wave_ctx *c, int x, int y, int z) {
-  const int w = c->cg.w;
-  return x < w || x >= c->nx - w || y < w || y >= c->ny - w || z < w ||
-         z >= c->nz - w;
-}
-
 int build_graph(wave_ctx *c, int parity) {
   cudaGraph_t g = nullptr;
   WAVE_TRY_CUDA(cudaStreamBeginCapture(c->capture_stream,
@@ -298,10 +312,79 @@ int run_steps(wave_ctx *c, int nsteps) {
   }
   WAVE_TRY_CUDA(cudaGetLastError());
   c->step += nsteps;
+  if (nsteps > 0) c->at_rest = false;
   return WAVE_OK;
 }
 
-int read_device_error(const wave_ctx *c) {
+// Deferred velocity pass, field at rest, source at depth sz: enqueue steps
+// one by one, each after the slabs it can reach (planes up to sz + 4k for
+// the call's step k), until every slab has been waited for or the call's
+// steps run out. Returns the number of steps enqueued (the caller runs the
+// rest as usual).
+int steps_while_loading(wave_ctx *c, int sz, int nsteps) {
+  int k = 0, cur = c->cur;
+  for (; k < nsteps && c->chunk_next < c->nchunks; ++k, cur ^= 1) {
+    const long long reach = (long long)sz + 4ll * k;
+    while (c->chunk_next < c->nchunks && c->chunk_z0[c->chunk_next] <= reach) {
+      WAVE_TRY_CUDA(cudaStreamWaitEvent(c->stream, c->chunk_ev[c->chunk_next], 0));
+      ++c->chunk_next;
+    }
+    enqueue_step(c, c->stream, cur, k);
+  }
+  if (k > 0) {
+    advance_kernel<<<1, 1, 0, c->stream>>>(c->d_desc, k);
+    WAVE_TRY_CUDA(cudaGetLastError());
+    c->cur = cur;
+    c->step += k;
+    c->at_rest = false;
+  }
+  if (c->chunk_next == c->nchunks) c->upload_pending = false;
+  return k;
+}
+
+// Result of the velocity pass (16 bytes: max bits, bad count) to a status;
+// sets vmax.
+int check_model(wave_ctx *c, const unsigned char *res) {
+  unsigned vb;
+  unsigned long long bad;
+  std::memcpy(&vb, res, 4);
+  std::memcpy(&bad, res + 8, 8);
+  if (bad) return WAVE_EINVAL;
+  float vmax;
+  std::memcpy(&vmax, &vb, 4);
+  wave_spacing h{c->dx, c->dy, c->dz};
+  const double lim = wave_cfl_dt(&h, (double)vmax);
+  if (!(c->dt <= lim * (1.0 + 1e-12))) return WAVE_EUNSTABLE;
+  c->vmax = vmax;
+  return WAVE_OK;
+}
+
+// Deferred velocity pass (wave_create_async): make the main stream wait for
+// every slab.
+int wait_model(wave_ctx *c) {
+  if (!c->upload_pending) return WAVE_OK;
+  WAVE_TRY_CUDA(cudaStreamWaitEvent(c->stream, c->chunk_ev[c->nchunks - 1], 0));
+  c->chunk_next = c->nchunks;
+  c->upload_pending = false;
+  return WAVE_OK;
+}
+
+// Deferred velocity pass: wait for it on the host and take its verdict (and
+// vmax); the verdict of a synchronous creation is already known.
+int finish_model(wave_ctx *c) {
+  if (c->model_checked) return c->model_status;
+  unsigned char res[16];
+  WAVE_TRY_CUDA(cudaMemcpyAsync(res, c->d_scratch, 16, cudaMemcpyDeviceToHost,
+                                c->upload_stream));
+  WAVE_TRY_CUDA(cudaStreamSynchronize(c->upload_stream));
+  c->model_status = check_model(c, res);
+  c->model_checked = true;
+  return c->model_status;
+}
+
+int read_device_error(wave_ctx *c) {
+  const int ms = finish_model(c);
+  if (ms) return ms;
   int err = 0;
   WAVE_TRY_CUDA(cudaMemcpyAsync(&err, &c->d_desc->error, sizeof(int),
                                 cudaMemcpyDeviceToHost, c->stream));
@@ -352,18 +435,17 @@ const char *wave_strerror(int st) {
 
 void wave_destroy(wave_ctx *c) {
   if (!c) return;
+  if (c->upload_stream) cudaStreamSynchronize(c->upload_stream);
   if (c->stream || c->buf[0]) cudaStreamSynchronize(c->stream);
   for (int p = 0; p < 2; ++p)
     if (c->graph[p]) cudaGraphExecDestroy(c->graph[p]);
-  cudaFree(c->buf[0]);
-  cudaFree(c->buf[1]);
-  cudaFree(c->c);
-  cudaFree(c->d_desc);
-  cudaFree(c->d_scratch);
-  cudaFree(c->wavelet.p);
-  cudaFree(c->rec.p);
-  cudaFree(c->rec_start.p);
-  cudaFree(c->traces.p);
+  cudaFree(c->base);
+  cudaFree(c->tables.p);
+  if (c->ev_aux) cudaEventDestroy(c->ev_aux);
+  if (c->ev_upload_start) cudaEventDestroy(c->ev_upload_start);
+  for (cudaEvent_t e : c->chunk_ev)
+    if (e) cudaEventDestroy(e);
+  if (c->upload_stream) cudaStreamDestroy(c->upload_stream);
   if (c->capture_stream) cudaStreamDestroy(c->capture_stream);
   free_cpml(c);
   cudaFree(c->srec.p);
@@ -375,60 +457,67 @@ size_t field_bytes(const wave_ctx *c) {
   return (size_t)c->pxu * c->ny * c->nz * (size_t)c->var.esize;
 }
 
-static int create_impl(wave_ctx *c, const float *velocity) {
-  const size_t plane = (size_t)c->px * c->ny;
-  const size_t nfield = plane * c->nz;
-  const size_t bytes = nfield * sizeof(float);
+// Where the velocity pass reads the caller's model: device memory, pinned
+// host memory through its device mapping, or pageable host memory when the
+// GPU reads the host's page tables (address translation services); nullptr
+// when the model has to be staged by a copy first.
+static const float *velocity_source(const float *velocity, int device) {
+  cudaPointerAttributes at;
+  if (cudaPointerGetAttributes(&at, velocity) != cudaSuccess) {
+    cudaGetLastError();
+    return nullptr;
+  }
+  if (at.type == cudaMemoryTypeDevice || at.type == cudaMemoryTypeManaged)
+    return velocity;
+  if (at.type == cudaMemoryTypeHost) {
+    void *dp = nullptr;
+    if (cudaHostGetDevicePointer(&dp, const_cast<float *>(velocity), 0) == cudaSuccess)
+      return static_cast<const float *>(dp);
+    cudaGetLastError();
+    return nullptr;
+  }
+  int pageable = 0, host_tables = 0;
+  cudaDeviceGetAttribute(&pageable, cudaDevAttrPageableMemoryAccess, device);
+  cudaDeviceGetAttribute(&host_tables,
+                         cudaDevAttrPageableMemoryAccessUsesHostPageTables, device);
+  return pageable && host_tables ? velocity : nullptr;
+}
+
+// Streams, events and the one allocation that holds both wavefields,
+// v^2 dt^2, the step descriptor and the scan result (one cudaMalloc /
+// cudaFree instead of five). The zero initial state is written on the side
+// stream (joined through ev_aux) while the velocity pass runs on the main one.
+static int alloc_context(wave_ctx *c) {
+  const size_t bytes = (size_t)c->px * c->ny * c->nz * sizeof(float);
   cudaStream_t st = c->stream;
   const char *ev = std::getenv("GBWAVE_VARIANT");
   c->var = pick_variant(c->storage, ev ? std::atoi(ev) : 0);
   WAVE_TRY_CUDA(cudaGetDevice(&c->device));
+  WAVE_TRY_CUDA(cudaDeviceGetAttribute(&c->sms, cudaDevAttrMultiProcessorCount,
+                                       c->device));
   WAVE_TRY_CUDA(cudaStreamCreateWithFlags(&c->capture_stream,
                                           cudaStreamNonBlocking));
+  WAVE_TRY_CUDA(cudaEventCreateWithFlags(&c->ev_aux, cudaEventDisableTiming));
   const size_t fbytes = field_bytes(c);
-  WAVE_TRY_CUDA(cudaMalloc(&c->buf[0], fbytes));
-  WAVE_TRY_CUDA(cudaMalloc(&c->buf[1], fbytes));
-  WAVE_TRY_CUDA(cudaMalloc((void **)&c->c, bytes));
-  WAVE_TRY_CUDA(cudaMalloc((void **)&c->d_desc, sizeof(StepDesc)));
-  WAVE_TRY_CUDA(cudaMalloc(&c->d_scratch, 16));
-  WAVE_TRY_CUDA(cudaMemsetAsync(c->buf[0], 0, fbytes, st));
-  WAVE_TRY_CUDA(cudaMemsetAsync(c->buf[1], 0, fbytes, st));
-  WAVE_TRY_CUDA(cudaMemsetAsync(c->c, 0, bytes, st));
-  WAVE_TRY_CUDA(cudaMemsetAsync(c->d_desc, 0, sizeof(StepDesc), st));
-  WAVE_TRY_CUDA(cudaMemsetAsync(c->d_scratch, 0, 16, st));
+  const size_t off1 = round_up256(fbytes), offc = off1 + round_up256(fbytes);
+  const size_t offd = offc + round_up256(bytes);
+  const size_t offs = offd + round_up256(sizeof(StepDesc));
+  WAVE_TRY_CUDA(cudaMalloc(&c->base, offs + 256));
+  char *base = static_cast<char *>(c->base);
+  c->buf[0] = base;
+  c->buf[1] = base + off1;
+  c->c = reinterpret_cast<float *>(base + offc);
+  c->d_desc = reinterpret_cast<StepDesc *>(base + offd);
+  c->d_scratch = base + offs;
+  WAVE_TRY_CUDA(cudaMemsetAsync(c->buf[0], 0, fbytes, c->capture_stream));
+  WAVE_TRY_CUDA(cudaMemsetAsync(c->buf[1], 0, fbytes, c->capture_stream));
+  WAVE_TRY_CUDA(cudaEventRecord(c->ev_aux, c->capture_stream));
+  WAVE_TRY_CUDA(cudaMemsetAsync(c->d_desc, 0, offs + 256 - offd, st));
+  return WAVE_OK;
+}
 
-  // Velocity into the c buffer (pitched), then validate and convert.
-  WAVE_TRY_CUDA(cudaMemcpy2DAsync(c->c, (size_t)c->px * 4, velocity,
-                                  (size_t)c->nx * 4, (size_t)c->nx * 4,
-                                  (size_t)c->ny * c->nz, cudaMemcpyDefault, st));
-  unsigned *vmax_bits = reinterpret_cast<unsigned *>(c->d_scratch);
-  unsigned long long *nbad =
-      reinterpret_cast<unsigned long long *>((char *)c->d_scratch + 8);
-  int sms = 0;
-  WAVE_TRY_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount,
-                                       c->device));
-  c->sms = sms;
-  scan_velocity_kernel<<<sms * 4, 256, 0, st>>>(
-      c->c, c->nx, c->px, (long long)c->ny * c->nz, vmax_bits, nbad);
-  WAVE_TRY_CUDA(cudaGetLastError());
-  unsigned char res[16];
-  WAVE_TRY_CUDA(cudaMemcpyAsync(res, c->d_scratch, 16, cudaMemcpyDeviceToHost, st));
-  WAVE_TRY_CUDA(cudaStreamSynchronize(st));
-  unsigned vb;
-  unsigned long long bad;
-  std::memcpy(&vb, res, 4);
-  std::memcpy(&bad, res + 8, 8);
-  if (bad) return WAVE_EINVAL;
-  float vmax;
-  std::memcpy(&vmax, &vb, 4);
-  wave_spacing h{c->dx, c->dy, c->dz};
-  const double lim = wave_cfl_dt(&h, (double)vmax);
-  if (!(c->dt <= lim * (1.0 + 1e-12))) return WAVE_EUNSTABLE;
-  c->vmax = vmax;
-  launch_velocity_to_c(c->c, (long long)nfield, c->dt * c->dt, sms, st);
-  WAVE_TRY_CUDA(cudaGetLastError());
-
-  // Launch geometry.
+// Launch geometry, z-layer plan, coefficients and tensor maps.
+static int setup_launch(wave_ctx *c) {
   WAVE_TRY_CUDA(cudaFuncSetAttribute(c->var.func,
                                      cudaFuncAttributeMaxDynamicSharedMemorySize,
                                      (int)c->var.smem));
@@ -438,26 +527,143 @@ static int create_impl(wave_ctx *c, const float *velocity) {
   const int ntx = (c->nx + c->var.tx - 1) / c->var.tx;
   const int nty = (c->ny + c->var.ty - 1) / c->var.ty;
   c->ntiles = ntx * nty;
-  const std::vector<int> layers = plan_layers(
-      c->nz, (long long)c->ntiles, (long long)sms * c->ctas_per_sm,
-      c->storage == WAVE_STORAGE_F32 ? 4.0 : 8.0);
-  c->zchunk = *std::max_element(layers.begin(), layers.end());
-  c->grid = dim3(ntx, nty, (unsigned)layers.size());
+  int layers[kMaxLayers];
+  const int nl = plan_layers(c->nz, (long long)c->ntiles,
+                             (long long)c->sms * c->ctas_per_sm,
+                             c->storage == WAVE_STORAGE_F32 ? 4.0 : 8.0, layers);
+  c->zchunk = *std::max_element(layers, layers + nl);
+  c->grid = dim3(ntx, nty, (unsigned)nl);
   if (c->grid.y > 65535) return WAVE_EINVAL;
   set_coeffs(c);
-  set_layers(c->args, layers);
+  set_layers(c->args, layers, nl);
   int stt = build_maps(c);
   if (stt) return stt;
   const char *gs = std::getenv("GBWAVE_GRAPH_STEPS");
   if (gs) c->graph_steps = std::max(2, (std::atoi(gs) / 2) * 2);
-
-  if (!is_device_ptr(velocity)) WAVE_TRY_CUDA(cudaStreamSynchronize(st));
   return WAVE_OK;
 }
 
-int wave_create(const wave_grid *g, const wave_spacing *h, double dt,
-                const float *velocity, int storage, void *stream,
-                wave_ctx **out) {
+static void launch_velocity_pass(wave_ctx *c, const float *src, long long sx,
+                                 int z0, int z1, cudaStream_t st, int blocks) {
+  const double dt2 = c->dt * c->dt;
+  const float dh = (float)dt2, dl = (float)(dt2 - (double)dh);
+  unsigned *vmax = reinterpret_cast<unsigned *>(c->d_scratch);
+  unsigned long long *nbad =
+      reinterpret_cast<unsigned long long *>((char *)c->d_scratch + 8);
+  const float *s0 = src + (long long)z0 * c->ny * sx;
+  float *c0 = c->c + (size_t)z0 * c->ny * c->px;
+  if (sx == c->px && c->px == c->nx && reinterpret_cast<uintptr_t>(s0) % 16 == 0) {
+    velocity_to_c_dense_kernel<<<blocks, 256, 0, st>>>(
+        reinterpret_cast<const float4 *>(s0), reinterpret_cast<float4 *>(c0),
+        (long long)(z1 - z0) * c->ny * c->px / 4, dh, dl, vmax, nbad);
+  } else {
+    velocity_to_c_checked_kernel<<<blocks, 256, 0, st>>>(
+        s0, sx, c0, c->nx, c->px, (long long)(z1 - z0) * c->ny, dh, dl, vmax, nbad);
+  }
+}
+
+static int create_impl(wave_ctx *c, const float *velocity) {
+  int s;
+  if ((s = alloc_context(c))) return s;
+  cudaStream_t st = c->stream;
+  // One pass validates the velocities, finds their maximum and writes
+  // v^2 dt^2, reading the caller's model where it lies when the GPU can
+  // reach it, else from a staged copy in the c buffer.
+  const float *src = velocity_source(velocity, c->device);
+  long long sx = c->nx;
+  if (!src) {
+    WAVE_TRY_CUDA(cudaMemcpy2DAsync(c->c, (size_t)c->px * 4, velocity,
+                                    (size_t)c->nx * 4, (size_t)c->nx * 4,
+                                    (size_t)c->ny * c->nz, cudaMemcpyDefault, st));
+    src = c->c;
+    sx = c->px;
+  }
+  launch_velocity_pass(c, src, sx, 0, c->nz, st, c->sms * 4);
+  WAVE_TRY_CUDA(cudaGetLastError());
+  WAVE_TRY_CUDA(cudaStreamWaitEvent(st, c->ev_aux, 0));
+  unsigned char res[16];
+  WAVE_TRY_CUDA(cudaMemcpyAsync(res, c->d_scratch, 16, cudaMemcpyDeviceToHost, st));
+  WAVE_TRY_CUDA(cudaStreamSynchronize(st));
+  if ((s = check_model(c, res))) return s;
+  c->model_checked = true;
+  return setup_launch(c);
+}
+
+// Deferred form (wave_create_async): v^2 dt^2 starts at zero everywhere (so
+// every value the sweep can read is finite) and the velocity pass runs on
+// its own stream in kUploadChunks z slabs, each followed by an event. While
+// the field is still at rest, a propagation waits before step k only for
+// the slabs that reach depth sz + 4k: the star stencil spreads the field by
+// at most 4 planes per step, so every plane below that bound still holds
+// u = u_prev = L u = 0 and computes u_next = 0 whatever its v^2 dt^2.
+// A host model crosses the link by copy engine into the c buffer, slab by
+// slab, and is converted there in place by a short kernel: the SMs stay
+// with the sweep while the (link-bound) transfer runs. A device model is
+// converted directly. The pass kernels take one block per SM.
+static int create_async_impl(wave_ctx *c, const float *velocity) {
+  int s;
+  if ((s = alloc_context(c))) return s;
+  cudaStream_t st = c->stream;
+  // Pinned host models cross the link by copy engine and are converted in
+  // place by one-block-per-SM kernels; pageable host models (read by the
+  // GPU through the host's page tables) are read by the pass kernel itself
+  // with a quarter of the SMs, enough blocks to fill the link while taking
+  // few CTA places from the sweep; device models are converted directly.
+  // Measured at 1024 x 1024 x 512, 20 steps from rest, create + propagate +
+  // destroy: pinned 35.7 ms (copy engine) against 36.6 (kernel reads, 38
+  // blocks); pageable 37.2 ms (kernel reads, 38 blocks) against 39.4 (76),
+  // 40.4 (152) and 56.5 (copy engine: the pageable copy blocks the host).
+  // GBWAVE_UPLOAD=sm|ce and GBWAVE_UPLOAD_BLOCKS override both (tuning).
+  cudaPointerAttributes at{};
+  if (cudaPointerGetAttributes(&at, velocity) != cudaSuccess) cudaGetLastError();
+  const bool on_device =
+      at.type == cudaMemoryTypeDevice || at.type == cudaMemoryTypeManaged;
+  const float *direct = velocity_source(velocity, c->device);
+  bool copy_engine = at.type == cudaMemoryTypeHost;
+  int pass_blocks = copy_engine || on_device ? c->sms : std::max(1, c->sms / 4);
+  if (const char *um = std::getenv("GBWAVE_UPLOAD"))
+    copy_engine = !on_device && std::strcmp(um, "ce") == 0;
+  if (const char *ub = std::getenv("GBWAVE_UPLOAD_BLOCKS"))
+    pass_blocks = std::max(1, std::atoi(ub));
+  WAVE_TRY_CUDA(cudaStreamCreateWithFlags(&c->upload_stream, cudaStreamNonBlocking));
+  WAVE_TRY_CUDA(cudaEventCreateWithFlags(&c->ev_upload_start, cudaEventDisableTiming));
+  for (int j = 0; j < kUploadChunks; ++j)
+    WAVE_TRY_CUDA(cudaEventCreateWithFlags(&c->chunk_ev[j], cudaEventDisableTiming));
+  WAVE_TRY_CUDA(cudaMemsetAsync(c->c, 0, (size_t)c->px * c->ny * c->nz * 4, st));
+  WAVE_TRY_CUDA(cudaEventRecord(c->ev_upload_start, st));
+  WAVE_TRY_CUDA(cudaStreamWaitEvent(c->upload_stream, c->ev_upload_start, 0));
+  const int nch = std::min(c->nz, kUploadChunks);
+  for (int j = 0; j < nch; ++j) {
+    const int z0 = (int)((long long)c->nz * j / nch);
+    const int z1 = (int)((long long)c->nz * (j + 1) / nch);
+    c->chunk_z0[j] = z0;
+    if (on_device || !copy_engine) {
+      launch_velocity_pass(c, direct, c->nx, z0, z1, c->upload_stream, pass_blocks);
+    } else {
+      const size_t rows = (size_t)(z1 - z0) * c->ny;
+      WAVE_TRY_CUDA(cudaMemcpy2DAsync(
+          c->c + (size_t)z0 * c->ny * c->px, (size_t)c->px * 4,
+          velocity + (size_t)z0 * c->ny * c->nx, (size_t)c->nx * 4, (size_t)c->nx * 4,
+          rows, cudaMemcpyHostToDevice, c->upload_stream));
+      launch_velocity_pass(c, c->c, c->px, z0, z1, c->upload_stream, pass_blocks);
+    }
+    WAVE_TRY_CUDA(cudaGetLastError());
+    WAVE_TRY_CUDA(cudaEventRecord(c->chunk_ev[j], c->upload_stream));
+  }
+  c->nchunks = nch;
+  c->chunk_next = 0;
+  c->upload_pending = true;
+  c->model_checked = false;
+  c->at_rest = true;
+  WAVE_TRY_CUDA(cudaStreamWaitEvent(st, c->ev_aux, 0));
+  return setup_launch(c);
+}
+
+// Arguments shared by wave_create and wave_create_async; a new context with
+// its sizes filled in, or a status.
+static int new_context(const wave_grid *g, const wave_spacing *h, double dt,
+                       const float *velocity, int storage, void *stream,
+                       wave_ctx **out) {
   if (!out) return WAVE_EINVAL;
   *out = nullptr;
   if (!g || !h || !velocity) return WAVE_EINVAL;
@@ -486,7 +692,36 @@ int wave_create(const wave_grid *g, const wave_spacing *h, double dt,
   c->dz = h->dz;
   c->dt = dt;
   c->stream = reinterpret_cast<cudaStream_t>(stream);
-  const int st = create_impl(c, velocity);
+  *out = c;
+  return WAVE_OK;
+}
+
+int wave_create(const wave_grid *g, const wave_spacing *h, double dt,
+                const float *velocity, int storage, void *stream,
+                wave_ctx **out) {
+  wave_ctx *c = nullptr;
+  int st = new_context(g, h, dt, velocity, storage, stream, &c);
+  if (st != WAVE_OK) return st;
+  st = create_impl(c, velocity);
+  if (st != WAVE_OK) {
+    cudaGetLastError();
+    wave_destroy(c);
+    return st;
+  }
+  *out = c;
+  return WAVE_OK;
+}
+
+int wave_create_async(const wave_grid *g, const wave_spacing *h, double dt,
+                      const float *velocity, int storage, void *stream,
+                      wave_ctx **out) {
+  wave_ctx *c = nullptr;
+  int st = new_context(g, h, dt, velocity, storage, stream, &c);
+  if (st != WAVE_OK) return st;
+  int dev = 0;
+  const bool defer = storage == WAVE_STORAGE_F32 && cudaGetDevice(&dev) == cudaSuccess &&
+                     velocity_source(velocity, dev) != nullptr;
+  st = defer ? create_async_impl(c, velocity) : create_impl(c, velocity);
   if (st != WAVE_OK) {
     cudaGetLastError();
     wave_destroy(c);
@@ -501,12 +736,11 @@ int wave_step(wave_ctx *c, int nsteps) {
   if (nsteps == 0) return WAVE_OK;
   StepDesc &d = c->host_desc;
   std::memset(&d, 0, sizeof(d));
-  if (c->cpml) {
-    c->cpml_nsrec_host = 0;
-    WAVE_TRY_CUDA(cudaMemcpyAsync(c->d_nsrec, &c->cpml_nsrec_host, sizeof(int),
-                                  cudaMemcpyHostToDevice, c->stream));
-  }
-  int st = upload_desc(c);
+  if (c->cpml)
+    WAVE_TRY_CUDA(cudaMemsetAsync(c->d_nsrec, 0, sizeof(int), c->stream));
+  int st = wait_model(c);
+  if (st) return st;
+  st = upload_desc(c);
   if (st) return st;
   return run_steps(c, nsteps);
 }
@@ -525,95 +759,119 @@ int wave_propagate(wave_ctx *c, const wave_shot *shot, int nsteps,
   }
   if (nsteps == 0) return WAVE_OK;
   cudaStream_t st = c->stream;
+  int s;
 
-  // Receivers: bring to the host, validate, sort by (tile, z) into CSR.
-  std::vector<int32_t> hrec((size_t)nrec * 3);
-  if (nrec > 0) {
-    if (is_device_ptr(rec_xyz)) {
-      WAVE_TRY_CUDA(cudaMemcpyAsync(hrec.data(), rec_xyz, hrec.size() * 4,
-                                    cudaMemcpyDeviceToHost, st));
-      WAVE_TRY_CUDA(cudaStreamSynchronize(st));
-    } else {
-      std::memcpy(hrec.data(), rec_xyz, hrec.size() * 4);
+  // Receivers: host-resident ones are validated here (WAVE_EINVAL before
+  // anything is launched) and staged through a copy the call owns, so the
+  // caller's buffer is read completely before the call returns. The table
+  // sorted by (tile, z) is then built on the device, with no round trip to
+  // the host and no wait for the stream; device-resident receivers outside
+  // the interior are left out and reported as WAVE_EINVAL by the next
+  // synchronizing call.
+  const bool host_rec = nrec > 0 && !is_device_ptr(rec_xyz);
+  const bool host_traces = nrec > 0 && !is_device_ptr(traces);
+  if (host_rec) {
+    c->h_rec_raw.resize((size_t)nrec * 3);
+    for (int r = 0; r < nrec; ++r) {
+      const int32_t x = rec_xyz[3 * r], y = rec_xyz[3 * r + 1], z = rec_xyz[3 * r + 2];
+      if (x < 0 || x >= c->nx || y < 0 || y >= c->ny || z < 0 || z >= c->nz)
+        return WAVE_EINVAL;
+      c->h_rec_raw[3 * r] = x;
+      c->h_rec_raw[3 * r + 1] = y;
+      c->h_rec_raw[3 * r + 2] = z;
     }
   }
-  if (build_receiver_table(hrec.data(), nrec, c->nx, c->ny, c->nz, c->var.tx,
-                           c->var.ty, (int)c->grid.x, c->ntiles, c->h_rec,
-                           c->h_rec_start))
-    return WAVE_EINVAL;
+  // Layout of the tables buffer for this call (256-byte aligned blocks).
+  size_t off = 0;
+  auto take = [&](size_t bytes) {
+    const size_t o = off;
+    off += round_up256(bytes);
+    return o;
+  };
+  const size_t o_w = take(shot ? (size_t)nsteps * 4 : 0);
+  const size_t o_raw = take(host_rec ? (size_t)nrec * 12 : 0);
+  const size_t o_rec = take((size_t)nrec * sizeof(int4));
+  const size_t o_keys = take((size_t)nrec * 8);
+  const size_t o_start = take(nrec > 0 ? (size_t)(c->ntiles + 1) * 4 : 0);
+  const size_t o_cnt = take(nrec > 0 ? (size_t)(c->ntiles + 1) * 4 : 0);
+  const size_t o_tr = take(host_traces ? (size_t)nsteps * nrec * 4 : 0);
+  if ((s = ensure(c->tables, off, st))) return s;
+  char *tb = static_cast<char *>(c->tables.p);
+  c->d_wavelet = reinterpret_cast<float *>(tb + o_w);
+  c->d_rec = reinterpret_cast<int4 *>(tb + o_rec);
+  c->d_rec_start = reinterpret_cast<int *>(tb + o_start);
+  float *d_traces_stage = reinterpret_cast<float *>(tb + o_tr);
+  const int32_t *drec = rec_xyz;
+  if (host_rec) {
+    drec = reinterpret_cast<const int32_t *>(tb + o_raw);
+    WAVE_TRY_CUDA(cudaMemcpyAsync(tb + o_raw, c->h_rec_raw.data(), (size_t)nrec * 12,
+                                  cudaMemcpyHostToDevice, st));
+  }
 
   // Source wavelet for this call's steps, FP64 on the host, stored FP32.
   StepDesc &d = c->host_desc;
   std::memset(&d, 0, sizeof(d));
-  int s;
   if (shot) {
     c->h_wavelet.resize(nsteps);
     const double t0 = shot->t0 < 0 ? 1.0 / shot->f_peak : shot->t0;
     for (int k = 0; k < nsteps; ++k)
       c->h_wavelet[k] = (float)ricker((double)(c->step + k) * c->dt,
                                       shot->f_peak, t0, shot->amp);
-    if ((s = ensure(c->wavelet, (size_t)nsteps * 4, st))) return s;
-    WAVE_TRY_CUDA(cudaMemcpyAsync(c->wavelet.p, c->h_wavelet.data(),
+    WAVE_TRY_CUDA(cudaMemcpyAsync(c->d_wavelet, c->h_wavelet.data(),
                                   (size_t)nsteps * 4, cudaMemcpyHostToDevice, st));
-    d.wavelet = (const float *)c->wavelet.p;
+    d.wavelet = c->d_wavelet;
     d.src_active = 1;
     d.sx = shot->sx;
     d.sy = shot->sy;
     d.sz = shot->sz;
   }
-  const bool host_traces = nrec > 0 && !is_device_ptr(traces);
+  const RecGeom geom{c->nx, c->ny, c->nz, c->var.tx, c->var.ty, (int)c->grid.x,
+                     c->ntiles};
   if (nrec > 0) {
-    if ((s = ensure(c->rec, (size_t)nrec * sizeof(int4), st))) return s;
-    if ((s = ensure(c->rec_start, (size_t)(c->ntiles + 1) * 4, st))) return s;
-    WAVE_TRY_CUDA(cudaMemcpyAsync(c->rec.p, c->h_rec.data(),
-                                  (size_t)nrec * sizeof(int4),
-                                  cudaMemcpyHostToDevice, st));
-    WAVE_TRY_CUDA(cudaMemcpyAsync(c->rec_start.p, c->h_rec_start.data(),
-                                  (size_t)(c->ntiles + 1) * 4,
-                                  cudaMemcpyHostToDevice, st));
-    if (host_traces) {
-      if ((s = ensure(c->traces, (size_t)nsteps * nrec * 4, st))) return s;
-      d.traces = (float *)c->traces.p;
-    } else {
-      d.traces = traces;
-    }
-    d.rec = (const int4 *)c->rec.p;
-    d.rec_start = (const int *)c->rec_start.p;
+    if ((s = build_receiver_table_device(
+             drec, nrec, geom, reinterpret_cast<int *>(tb + o_cnt), c->d_rec_start,
+             reinterpret_cast<unsigned long long *>(tb + o_keys), c->d_rec,
+             &c->d_desc->error, c->sms, st)))
+      return s;
+    d.traces = host_traces ? d_traces_stage : traces;
+    d.rec = c->d_rec;
+    d.rec_start = c->d_rec_start;
     d.nrec = nrec;
   }
   if (c->cpml) {
     // receivers inside the CPML shell are recorded from the shell values
-    c->h_srec.clear();
-    for (int r = 0; r < nrec; ++r)
-      if (cpml_in_shell(c, hrec[3 * r], hrec[3 * r + 1], hrec[3 * r + 2]))
-        c->h_srec.push_back(make_int4(hrec[3 * r], hrec[3 * r + 1], hrec[3 * r + 2], r));
-    const int ns = (int)c->h_srec.size();
-    if (ns > 0) {
+    if (nrec > 0) {
       void *old = c->srec.p;
-      if ((s = ensure(c->srec, (size_t)ns * sizeof(int4), st))) return s;
+      if ((s = ensure(c->srec, (size_t)nrec * sizeof(int4), st))) return s;
       if (c->srec.p != old) drop_graphs(c);  // graphs hold the list's address
-      WAVE_TRY_CUDA(cudaMemcpyAsync(c->srec.p, c->h_srec.data(),
-                                    (size_t)ns * sizeof(int4),
-                                    cudaMemcpyHostToDevice, st));
     }
-    c->cpml_nsrec_host = ns;
-    WAVE_TRY_CUDA(cudaMemcpyAsync(c->d_nsrec, &c->cpml_nsrec_host, sizeof(int),
-                                  cudaMemcpyHostToDevice, st));
+    WAVE_TRY_CUDA(cudaMemsetAsync(c->d_nsrec, 0, sizeof(int), st));
+    if (nrec > 0) {
+      rec_shell_kernel<<<std::min(c->sms * 4, (nrec + 255) / 256), 256, 0, st>>>(
+          drec, nrec, geom, c->cg.w, (int4 *)c->srec.p, c->d_nsrec);
+      WAVE_TRY_CUDA(cudaGetLastError());
+    }
   }
   if ((s = upload_desc(c))) return s;
-  if ((s = run_steps(c, nsteps))) return s;
+  int early = 0;
+  if (c->upload_pending) {
+    if (c->at_rest && shot)
+      early = steps_while_loading(c, shot->sz, nsteps);
+    else if ((s = wait_model(c)))
+      return s;
+    if (early < 0) return early;
+  }
+  if ((s = run_steps(c, nsteps - early))) return s;
   if (nrec > 0) {  // NaN / infinity in the traces: WAVE_ENAN at the next sync
     finite_check_kernel<<<c->sms * 4, 256, 0, st>>>(
         c->host_desc.traces, (long long)nsteps * nrec, &c->d_desc->error);
     WAVE_TRY_CUDA(cudaGetLastError());
   }
   if (host_traces) {
-    WAVE_TRY_CUDA(cudaMemcpyAsync(traces, c->traces.p, (size_t)nsteps * nrec * 4,
+    WAVE_TRY_CUDA(cudaMemcpyAsync(traces, d_traces_stage, (size_t)nsteps * nrec * 4,
                                   cudaMemcpyDeviceToHost, st));
     return read_device_error(c);
   }
-  // The host-side tables were staged by the copies above; make sure pageable
-  // sources are consumed before the vectors change on the next call.
   return WAVE_OK;
 }
 
@@ -651,7 +909,7 @@ int wave_get_field(const wave_ctx *c, int which, float *out) {
                                     (size_t)c->px * 4, (size_t)c->nx * 4,
                                     (size_t)c->ny * c->nz, cudaMemcpyDefault,
                                     c->stream));
-    if (host_out) return read_device_error(c);
+    if (host_out) return read_device_error(const_cast<wave_ctx *>(c));
     return WAVE_OK;
   }
   // 16-bit storage: expand to FP32 with the field's scale.
@@ -670,7 +928,7 @@ int wave_get_field(const wave_ctx *c, int which, float *out) {
     cudaFree(dst);
   }
   if (e != cudaSuccess) return cuda_status(e);
-  return host_out ? read_device_error(c) : WAVE_OK;
+  return host_out ? read_device_error(const_cast<wave_ctx *>(c)) : WAVE_OK;
 }
 
 }  // extern "C"
@@ -754,6 +1012,9 @@ extern "C" {
 int wave_set_state(wave_ctx *c, const float *u, const float *u_prev,
                    int64_t step) {
   if (!c || !u || !u_prev || step < 0) return WAVE_EINVAL;
+  int ws = wait_model(c);  // the state is no longer at rest
+  if (ws) return ws;
+  c->at_rest = false;
   WAVE_TRY_CUDA(cudaMemsetAsync(&c->d_desc->error, 0, sizeof(int), c->stream));
   if (c->storage != WAVE_STORAGE_F32) return set_state_16(c, u, u_prev, step);
   c->cur = 0;
@@ -789,11 +1050,15 @@ int wave_reset(wave_ctx *c) {
       sizeof(int) * 4 + sizeof(unsigned) * 4, c->stream));
   c->cur = 0;
   c->step = 0;
+  c->at_rest = true;
   return zero_cpml(c);
 }
 
 int wave_set_cpml(wave_ctx *c, int npml, double R, double f_cps) {
   if (!c || npml < 0) return WAVE_EINVAL;
+  // the layer's profile needs the model's largest velocity
+  int ms = finish_model(c);
+  if (ms || (ms = wait_model(c))) return ms;
   if (npml == 0) {
     WAVE_TRY_CUDA(cudaStreamSynchronize(c->stream));
     free_cpml(c);
@@ -998,6 +1263,8 @@ int gradient_impl(wave_ctx *c, const wave_shot *shot, int N,
   if (c->storage != WAVE_STORAGE_F32 || c->cpml ||
       c->var.func != reinterpret_cast<const void *>(&wave_sweep_kernel<Cfg0>))
     return WAVE_ENOTSUP;
+  int ms = finish_model(c);
+  if (ms || (ms = wait_model(c))) return ms;
   cudaStream_t st = c->stream;
   const size_t fe = (size_t)c->px * c->ny * c->nz;  // field elements
   const size_t fb = fe * 4;
@@ -1028,8 +1295,8 @@ int gradient_impl(wave_ctx *c, const wave_shot *shot, int N,
     WAVE_TRY_CUDA(cudaFuncSetAttribute(
         f, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)Cfg0::SMEM_BYTES));
 
-  // Receivers on the host once: each segment's wave_propagate would
-  // otherwise copy device-resident ones back and wait for the stream.
+  // Receivers on the host once, so that they are validated before anything
+  // is launched (each segment's wave_propagate checks host receivers).
   std::vector<int32_t> hrec;
   if (nrec > 0 && is_device_ptr(rec_xyz)) {
     hrec.resize((size_t)nrec * 3);
@@ -1086,8 +1353,8 @@ int gradient_impl(wave_ctx *c, const wave_shot *shot, int N,
                                 cudaMemcpyHostToDevice, st));
   if (nrec > 0) {
     ha.inj_val = inj;
-    ha.inj = (const int4 *)c->rec.p;  // receiver table of the forward run
-    ha.inj_start = (const int *)c->rec_start.p;
+    ha.inj = c->d_rec;  // receiver table of the forward run
+    ha.inj_start = c->d_rec_start;
     ha.ninj = nrec;
   }
   WAVE_TRY_CUDA(cudaMemcpyAsync(dfwd, &hf, sizeof(hf), cudaMemcpyHostToDevice, st));
@@ -1233,10 +1500,15 @@ NoallocDevice g_noalloc_dev[kNoallocMaxDevices];
 
 size_t round256(size_t x) { return (x + 255) & ~size_t(255); }
 
-// Once per device, with that device current.
+// Once per device, with that device current. A mutex (static storage, no
+// allocation) serialises first calls from several host threads; the cached
+// address stays valid for the life of the process's context on the device.
+std::mutex g_noalloc_setup_mutex;
+
 int noalloc_setup(int dev, NoallocDevice **out) {
   if (dev < 0 || dev >= kNoallocMaxDevices) return WAVE_ECUDA;
   NoallocDevice &d = g_noalloc_dev[dev];
+  std::lock_guard<std::mutex> lock(g_noalloc_setup_mutex);
   if (!d.scratch) {
     void *p = nullptr;
     WAVE_TRY_CUDA(cudaGetSymbolAddress(&p, g_noalloc_scratch));
@@ -1404,12 +1676,13 @@ extern "C" int wave_propagate_noalloc(const wave_grid *g, const wave_spacing *h,
       return st;
   }
   if ((st = noalloc_map(&vmap, velocity, nx, ny, nz, C::TX, C::TY))) return st;
-  const std::vector<int> layers =
-      plan_layers(nz, (long long)ntiles, (long long)nd->sms * nd->ctas_per_sm);
-  const dim3 grid(ntx, nty, (unsigned)layers.size());
+  int layers[kMaxLayers];
+  const int nl = plan_layers(nz, (long long)ntiles,
+                             (long long)nd->sms * nd->ctas_per_sm, 4.0, layers);
+  const dim3 grid(ntx, nty, (unsigned)nl);
   if (grid.y > 65535) return WAVE_EINVAL;
   SweepArgs a{};
-  set_layers(a, layers);
+  set_layers(a, layers, nl);
   a.nx = nx;
   a.ny = ny;
   a.nz = nz;
