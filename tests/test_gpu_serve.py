@@ -75,6 +75,30 @@ def test_alone_and_in_the_mix_are_identical(wave_lib):
         assert np.abs(tr_mix).max() > 0
 
 
+def test_served_shots_match_the_oracle(wave_lib, oracle_mod):
+    """Each shot of a served mix against the FP64 oracle on that shot's own
+    model, source, receivers and time step: the batched launch (per-shot
+    tensor maps, CTA-to-shot search, step offsets) computes the Eq. 1
+    leapfrog update of every resident shot. Ragged sizes (nx not a multiple
+    of 4, grids smaller than a tile in some axis), FP32 and FP16 in one mix.
+    FP32: relative L2 <= 1e-5, the FP32 parity bar. FP16: every step rounds
+    u_next to 11 significant bits (relative 2^-11) and the leapfrog carries
+    the errors forward undamped, so the traces stay within 6 * 2^-11 *
+    sqrt(steps), the bound of the 16-bit short-run parity tests."""
+    specs = [((45, 37, 29), 0, 40, 51), ((70, 33, 41), 2, 35, 52),
+             ((33, 50, 20), 0, 30, 53), ((61, 27, 35), 0, 37, 54),
+             ((21, 9, 44), 2, 28, 55)]
+    mix, res, stats = _serve(wave_lib, specs, slots=8)
+    assert stats["completed"] == len(specs) and stats["resident_peak"] >= 3
+    for (grid, storage, nsteps, seed), tr, r in zip(specs, mix, res):
+        vel, rec, shot = _inputs(grid, seed)
+        _, _, otr = oracle_mod.propagate(vel.cpu().numpy(), (10.0, 10.0, 10.0), r["dt"],
+                                         nsteps, source=shot, receivers=rec.cpu().numpy())
+        err = float(np.linalg.norm(tr.astype(np.float64) - otr) / np.linalg.norm(otr))
+        tol = 1e-5 if storage == 0 else 6 * 2.0 ** -11 * np.sqrt(nsteps)
+        assert err <= tol, (grid, storage, err, tol)
+
+
 def test_stream_sized_shots_alone_and_in_the_mix(wave_lib):
     """Shots of the serving stream's sizes (up to 512 per axis; nz > 256 is
     split into two z layers per CTA column), FP32 and FP16 in one mix with a

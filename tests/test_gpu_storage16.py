@@ -122,8 +122,12 @@ def test_precision_workload_128cube_500_steps(wave_lib, oracle_mod, mode, record
     record_property("rel_l2_field", e_u)
     record_property("rel_l2_traces", e_t)
     print("\nstorage %s: 128^3 x 500 steps rel-L2 field %.3e traces %.3e" % (mode, e_u, e_t))
-    bound = {"f32": 1e-4, "bf16": 1.0, "f16": 2e-2}[mode]
-    assert e_u <= bound and e_t <= bound
+    # (field, traces) bounds: FP16 storage is held to the 1e-2 trace error the
+    # 16-bit forms are stated at (measured 8.9e-3, field 1.5e-2); BF16 storage
+    # misses that bound (measured 0.36 on both), held just above its value
+    # so that a regression shows; FP32 after 500 steps (3.8e-5 / 1.0e-5).
+    bound_u, bound_t = {"f32": (1e-4, 1e-4), "bf16": (0.5, 0.5), "f16": (2e-2, 1e-2)}[mode]
+    assert e_u <= bound_u and e_t <= bound_t
 
 
 _ORACLE_CACHE = {}

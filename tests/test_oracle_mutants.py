@@ -62,7 +62,16 @@ MUTANTS = {
         [pins.test_adjoint_gradient_matches_finite_differences]),
     "CPML damping profile linear": (
         "const double d = d0 * xi * xi;", "const double d = d0 * xi;",
-        [cpml_pins.test_profile]),
+        [cpml_pins.test_profile_integral_meets_the_reflection_target]),
+    "CPML d0 without the cell size": (
+        "const double L = npml * h;", "const double L = npml;",
+        [cpml_pins.test_profile_integral_meets_the_reflection_target]),
+    "CPML d0 without the profile's factor 3/2": (
+        "3.0 * vmax * log(1.0 / R) / (2.0 * L)", "vmax * log(1.0 / R) / L",
+        [cpml_pins.test_profile_integral_meets_the_reflection_target]),
+    "CPML frequency shift largest at the wall": (
+        "const double al = pi * fcps * (1.0 - xi);", "const double al = pi * fcps * xi;",
+        [cpml_pins.test_frequency_shift_vanishes_at_the_wall]),
     "CPML convolution weight with the wrong sign": (
         "a[i] = (d + al > 0.0) ? d / (d + al) * (b[i] - 1.0) : 0.0;",
         "a[i] = (d + al > 0.0) ? d / (d + al) * (1.0 - b[i]) : 0.0;",
