@@ -99,6 +99,8 @@ typedef struct {
  * dt_max = 2 / (vmax sqrt(S (1/dx^2 + 1/dy^2 + 1/dz^2))), S = |w0| + 2 sum |w_m|
  * (von Neumann analysis of the leapfrog recurrence on the highest mode of
  * Eq. 1). Returns a negative value for invalid arguments.
+ * Defined by: Eq. 1 (the stencil) with the second-order time update of the
+ * wave equation of Sec. 2.
  */
 double wave_cfl_dt(const wave_spacing *h, double vmax);
 
@@ -115,10 +117,22 @@ double wave_cfl_dt(const wave_spacing *h, double vmax);
  *   out       receives the new context (NULL on failure)
  * The wavefields start at zero, step counter 0. Returns WAVE_EINVAL,
  * WAVE_EUNSTABLE, WAVE_ENOMEM, WAVE_ENOTSUP or WAVE_ECUDA on failure.
+ * Defined by: Sec. 2 (the acoustic isotropic medium the stencil is applied
+ * to) and Sec. 4.1 (the grid as one flat array, x innermost).
  */
 int wave_create(const wave_grid *g, const wave_spacing *h, double dt,
                 const float *velocity, int storage, void *stream,
                 wave_ctx **out);
+
+/*
+ * As wave_create, with the model given as the squared velocity m = v^2
+ * (m^2/s^2, nx*ny*nz float32, every value finite and > 0): the variable
+ * wave_adjoint / wave_gradient differentiate with respect to. The context
+ * keeps c = m dt^2 (one product, no square root taken and squared again),
+ * and the stability limit uses vmax = sqrt(max m).
+ */
+int wave_create_m(const wave_grid *g, const wave_spacing *h, double dt,
+                  const float *m, int storage, void *stream, wave_ctx **out);
 
 /*
  * As wave_create, but the call returns before the velocity model has been
@@ -150,7 +164,11 @@ int wave_create_async(const wave_grid *g, const wave_spacing *h, double dt,
                       const float *velocity, int storage, void *stream,
                       wave_ctx **out);
 
-/* Advance nsteps (>= 0) leapfrog steps with no source and no receivers. */
+/*
+ * Advance nsteps (>= 0) leapfrog steps with no source and no receivers.
+ * Defined by: Eq. 1 applied at every interior point once per time step
+ * (Sec. 2), the update u_next = 2u - u_prev + v^2 dt^2 L u.
+ */
 int wave_step(wave_ctx *ctx, int nsteps);
 
 /*
@@ -162,6 +180,10 @@ int wave_step(wave_ctx *ctx, int nsteps);
  *            the receivers after step n of this call (time (step0+n+1) dt,
  *            step0 = the context's step counter at entry)
  * The source time of the call's step n is t = (step0 + n) dt.
+ * Defined by: Eq. 1 and the per-step update of Sec. 2; the paper does not
+ * state the source or the receivers: a Ricker point source injected after
+ * each update and receivers recording the updated field are the readings
+ * taken here.
  */
 int wave_propagate(wave_ctx *ctx, const wave_shot *shot, int nsteps,
                    const int32_t *rec_xyz, int nrec, float *traces);
@@ -171,6 +193,7 @@ int wave_propagate(wave_ctx *ctx, const wave_shot *shot, int nsteps,
  *   which  0 = u at the current step, 1 = u at the previous step
  * 16-bit storage: the values are expanded to FP32 with the field's scale (a
  * host destination is staged through a temporary device buffer).
+ * Defined by: the wavefield of Sec. 2 in the layout of Sec. 4.1.
  */
 int wave_get_field(const wave_ctx *ctx, int which, float *out);
 
@@ -181,14 +204,16 @@ int wave_get_field(const wave_ctx *ctx, int which, float *out);
  * power-of-two scale that maps its largest magnitude to at most 2^14
  * (host inputs are staged through temporary device buffers; the call
  * synchronizes). Non-finite values return WAVE_EINVAL.
+ * Defined by: the two time levels the leapfrog update of Sec. 2 carries.
  */
 int wave_set_state(wave_ctx *ctx, const float *u, const float *u_prev,
                    int64_t step);
 
-/* Current step counter (number of steps taken since creation/reset/set_state). */
+/* Current step counter (number of steps taken since creation/reset/set_state;
+ * the iteration count of the time loop of Sec. 2). */
 int wave_get_step(const wave_ctx *ctx, int64_t *step);
 
-/* Zero both wavefields and the step counter. */
+/* Zero both wavefields and the step counter (the time loop of Sec. 2 from rest). */
 int wave_reset(wave_ctx *ctx);
 
 /*
@@ -216,19 +241,22 @@ int wave_reset(wave_ctx *ctx);
  */
 int wave_set_cpml(wave_ctx *ctx, int npml, double reflection, double f_cps);
 
-/* Wait for the context's stream; return any error a kernel recorded. */
+/* Wait for the context's stream; return any error a kernel recorded. No
+ * counterpart in the paper (error reporting of this library). */
 int wave_synchronize(wave_ctx *ctx);
 
-/* Free everything the context owns (waits for its stream first). NULL is a no-op. */
+/* Free everything the context owns (waits for its stream first). NULL is a
+ * no-op. No counterpart in the paper. */
 void wave_destroy(wave_ctx *ctx);
 
-/* Static message for a status code. */
+/* Static message for a status code. No counterpart in the paper. */
 const char *wave_strerror(int status);
 
 /*
  * Launch geometry of the stencil sweep for this context (for reports and
  * benchmarks): CTA tile in x and y, z planes per CTA, grid size, resident
- * CTAs per SM. Any output pointer may be NULL.
+ * CTAs per SM. Any output pointer may be NULL. The blocking itself follows
+ * the 2.5D streaming scheme of Sec. 4.1 (xy tile plus halo, z streamed).
  */
 int wave_get_launch_info(const wave_ctx *ctx, int *tile_x, int *tile_y,
                          int *z_chunk, int *grid_ctas, int *ctas_per_sm);
@@ -239,6 +267,7 @@ int wave_get_launch_info(const wave_ctx *ctx, int *tile_x, int *tile_y,
  * arrives on, with a limit of limit_ns nanoseconds (clamped to 1 ms .. 10 s).
  * Synchronizes the stream. Returns WAVE_ETIMEOUT when the wait gave up as
  * designed, WAVE_ECUDA if it reported completion or a CUDA call failed.
+ * No counterpart in the paper (failure detection of this library).
  */
 int wave_selftest_wait(int64_t limit_ns, void *stream);
 
@@ -267,6 +296,9 @@ int wave_selftest_wait(int64_t limit_ns, void *stream);
  *   traces       optional nsteps*nrec float32 output of the forward traces
  * FP32 storage and the default kernel variant only (else WAVE_ENOTSUP). The
  * call synchronizes; it leaves the context reset (zero fields, step 0).
+ * Defined by: the discrete adjoint of the update of Eq. 1 and Sec. 2 (the
+ * paper computes no gradient; this is the exact derivative of the discrete
+ * forward map).
  */
 int wave_adjoint(wave_ctx *ctx, const wave_shot *shot, int nsteps,
                  const int32_t *rec_xyz, int nrec, const float *resid,
@@ -277,6 +309,7 @@ int wave_adjoint(wave_ctx *ctx, const wave_shot *shot, int nsteps,
  * from rest and its gradient dJ/d(v^2) (wave_adjoint with resid = d -
  * observed). The residual and the misfit sum are formed on the GPU, the sum
  * in FP64. observed: nsteps*nrec float32, host or device; misfit: host.
+ * Defined by: as wave_adjoint.
  */
 int wave_gradient(wave_ctx *ctx, const wave_shot *shot, int nsteps,
                   const int32_t *rec_xyz, int nrec, const float *observed,
@@ -294,7 +327,10 @@ int wave_gradient(wave_ctx *ctx, const wave_shot *shot, int nsteps,
  * table, source wavelet) in one fixed array of WAVE_NOALLOC_SCRATCH_BYTES
  * that the library declares statically: every GPU that loads the library
  * holds that array until the process exits. It calls no cudaMalloc, no
- * cudaFree and no allocating library routine, and allocates no host heap.
+ * cudaFree and no allocating library routine; its own host-side work (the
+ * z-layer plan, the table image, staged host receivers) uses fixed static
+ * storage, so the call allocates no host heap either (the CUDA runtime's
+ * internal bookkeeping aside).
  *
  *   g, h, dt     as for wave_create; nx must be a multiple of 4 (rows of the
  *                caller's dense arrays must start on 16-byte boundaries)
@@ -316,7 +352,10 @@ int wave_gradient(wave_ctx *ctx, const wave_shot *shot, int nsteps,
  *
  * The first call on each device finds the array's device address
  * (cudaGetSymbolAddress) and sets the kernel's shared-memory limit, with that
- * device current; make that first call before any stream capture. Every
+ * device current; make that first call before any stream capture. First
+ * calls from several host threads are serialised by a lock. The address is
+ * kept for the life of the process: after cudaDeviceReset the library has
+ * to be unloaded and loaded again before this entry point is used. Every
  * call shares the one array and overwrites what the last call left there;
  * calls whose work overlaps on the GPU (other streams, other host threads)
  * race on it, so serialize them. The call validates the velocities

@@ -55,7 +55,7 @@ typedef struct {
 
 typedef struct {
   int status;       /* WAVE_OK, WAVE_EBUSY (queued or running), or an error */
-  int64_t ticket;
+  uint64_t ticket;
   double submit_s;  /* times in seconds since serve_create (steady clock) */
   double start_s;   /* admitted (-1 if not yet) */
   double done_s;    /* completed (-1 if not yet) */
@@ -91,17 +91,17 @@ int serve_create(size_t hbm_budget_bytes, int max_slots, void *stream,
  * values fail the request (status WAVE_EINVAL or WAVE_EUNSTABLE).
  *   ticket  receives the request's id (> 0)
  */
-int serve_submit(serve_ctx *s, const wave_request *req, int64_t *ticket);
+int serve_submit(serve_ctx *s, const wave_request *req, uint64_t *ticket);
 
 /*
  * State of a request without waiting: WAVE_EBUSY while queued or running,
  * otherwise the request's final status; *out (if not NULL) is filled either
  * way. WAVE_EINVAL for an unknown ticket.
  */
-int serve_poll(serve_ctx *s, int64_t ticket, wave_result *out);
+int serve_poll(serve_ctx *s, uint64_t ticket, wave_result *out);
 
 /* As serve_poll, but waits up to timeout_s seconds (< 0: no limit). */
-int serve_wait(serve_ctx *s, int64_t ticket, double timeout_s, wave_result *out);
+int serve_wait(serve_ctx *s, uint64_t ticket, double timeout_s, wave_result *out);
 
 int serve_get_stats(serve_ctx *s, serve_stats_t *out);
 

@@ -18,7 +18,7 @@ __all__ = [
     "wave_synchronize", "wave_destroy", "wave_strerror", "wave_get_launch_info",
     "wave_selftest_wait", "wave_propagate_noalloc", "WaveSolver", "library_path",
     "ShotServer", "wave_adjoint", "wave_gradient", "WaveTraces", "wave_traces",
-    "wave_set_cpml", "wave_create_async",
+    "wave_set_cpml", "wave_create_async", "wave_create_m",
 ]
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
@@ -59,7 +59,7 @@ class _Request(ctypes.Structure):
 
 
 class _Result(ctypes.Structure):
-    _fields_ = [("status", ctypes.c_int), ("ticket", ctypes.c_int64),
+    _fields_ = [("status", ctypes.c_int), ("ticket", ctypes.c_uint64),
                 ("submit_s", ctypes.c_double), ("start_s", ctypes.c_double),
                 ("done_s", ctypes.c_double), ("dt", ctypes.c_double),
                 ("steps_done", ctypes.c_int64)]
@@ -95,6 +95,7 @@ def load(path=None):
     lib.wave_create.argtypes = [ctypes.POINTER(_Grid), ctypes.POINTER(_Spacing),
                                 ctypes.c_double, vp, ip, vp, ctypes.POINTER(vp)]
     lib.wave_create_async.argtypes = lib.wave_create.argtypes
+    lib.wave_create_m.argtypes = lib.wave_create.argtypes
     lib.wave_step.argtypes = [vp, ip]
     lib.wave_propagate.argtypes = [vp, ctypes.POINTER(_Shot), ip, vp, ip, vp]
     lib.wave_get_field.argtypes = [vp, ip, vp]
@@ -115,9 +116,9 @@ def load(path=None):
     lib.wave_adjoint.restype = ctypes.c_int
     lib.wave_gradient.restype = ctypes.c_int
     lib.serve_create.argtypes = [ctypes.c_size_t, ip, vp, ctypes.POINTER(vp)]
-    lib.serve_submit.argtypes = [vp, ctypes.POINTER(_Request), ctypes.POINTER(ctypes.c_int64)]
-    lib.serve_poll.argtypes = [vp, ctypes.c_int64, ctypes.POINTER(_Result)]
-    lib.serve_wait.argtypes = [vp, ctypes.c_int64, ctypes.c_double, ctypes.POINTER(_Result)]
+    lib.serve_submit.argtypes = [vp, ctypes.POINTER(_Request), ctypes.POINTER(ctypes.c_uint64)]
+    lib.serve_poll.argtypes = [vp, ctypes.c_uint64, ctypes.POINTER(_Result)]
+    lib.serve_wait.argtypes = [vp, ctypes.c_uint64, ctypes.c_double, ctypes.POINTER(_Result)]
     lib.serve_get_stats.argtypes = [vp, ctypes.POINTER(_Stats)]
     lib.serve_destroy.argtypes = [vp]
     lib.serve_destroy.restype = None
@@ -126,7 +127,7 @@ def load(path=None):
     lib.wave_propagate_noalloc.argtypes = [
         ctypes.POINTER(_Grid), ctypes.POINTER(_Spacing), ctypes.c_double, vp, vp, vp,
         ctypes.POINTER(_Shot), ctypes.c_int64, ip, vp, ip, vp, vp, ctypes.POINTER(ip)]
-    for name in ("wave_create", "wave_create_async", "wave_step", "wave_propagate", "wave_get_field",
+    for name in ("wave_create", "wave_create_async", "wave_create_m", "wave_step", "wave_propagate", "wave_get_field",
                  "wave_set_state", "wave_get_step", "wave_reset", "wave_synchronize",
                  "wave_get_launch_info", "wave_selftest_wait", "wave_propagate_noalloc",
                  "wave_set_cpml"):
@@ -181,12 +182,14 @@ def wave_cfl_dt(spacing, vmax):
     return lib.wave_cfl_dt(ctypes.byref(_Spacing(*map(float, spacing))), float(vmax))
 
 
-def wave_create(grid, spacing, dt, velocity, storage=0, stream=None, defer=False):
+def wave_create(grid, spacing, dt, velocity, storage=0, stream=None, defer=False,
+                squared=False):
     """Create a context; ``grid`` = (nx, ny, nz); velocity has nx*ny*nz float32.
 
     ``defer=True`` calls wave_create_async: the model is read on the GPU after
     the call returns (keep ``velocity`` alive and unchanged until the next
     synchronizing call); errors in it are raised by that call.
+    ``squared=True`` calls wave_create_m: ``velocity`` holds m = v^2.
     """
     lib = load()
     nx, ny, nz = map(int, grid)
@@ -195,9 +198,11 @@ def wave_create(grid, spacing, dt, velocity, storage=0, stream=None, defer=False
     vptr = _ptr(velocity, "float32", nx * ny * nz, "velocity")
     out = ctypes.c_void_p()
     st = _default_stream() if stream is None else int(stream)
-    fn = lib.wave_create_async if defer else lib.wave_create
-    _check(fn(ctypes.byref(g), ctypes.byref(h), float(dt), vptr, int(storage),
-              st, ctypes.byref(out)), "wave_create_async" if defer else "wave_create")
+    if squared and defer:
+        raise ValueError("squared and defer cannot be combined")
+    name = "wave_create_m" if squared else ("wave_create_async" if defer else "wave_create")
+    _check(getattr(lib, name)(ctypes.byref(g), ctypes.byref(h), float(dt), vptr, int(storage),
+                              st, ctypes.byref(out)), name)
     return out
 
 
@@ -344,13 +349,14 @@ def wave_get_launch_info(ctx):
 class WaveSolver:
     """Owning wrapper of one context (destroyed with the object)."""
 
-    def __init__(self, grid, spacing, dt, velocity, storage=0, stream=None, defer=False):
+    def __init__(self, grid, spacing, dt, velocity, storage=0, stream=None, defer=False,
+                 squared=False):
         self.grid = tuple(int(v) for v in grid)
         self.spacing = tuple(float(v) for v in spacing)
         self.dt = float(dt)
         self.count = self.grid[0] * self.grid[1] * self.grid[2]
         self.ctx = wave_create(self.grid, self.spacing, self.dt, velocity, storage, stream,
-                               defer)
+                               defer, squared)
         # a deferred creation reads the model later: keep it alive until close
         self._velocity = velocity if defer else None
 
@@ -445,7 +451,7 @@ class ShotServer:
                   float(amp)),
             int(nsteps), _ptr(rec, "int32", 3 * nrec, "rec") if nrec else None, nrec,
             _ptr(traces, "float32", int(nsteps) * nrec, "traces") if nrec else None)
-        ticket = ctypes.c_int64()
+        ticket = ctypes.c_uint64()
         _check(load().serve_submit(self.handle, ctypes.byref(req), ctypes.byref(ticket)),
                "serve_submit")
         self._keep[ticket.value] = (velocity, rec, traces)
@@ -494,14 +500,14 @@ def _make_traces_function():
         (wave_propagate). backward: the discrete adjoint (wave_adjoint) with
         the incoming gradient as dJ/dtraces, checkpointing every ``ckpt_every``
         steps. dt stays fixed, so the map m -> traces is a fixed discrete
-        function; the model used is v = sqrt(m) rounded to FP32.
+        function; the library takes m itself (wave_create_m: v^2 dt^2 = m dt^2).
         """
 
         @staticmethod
         def forward(fctx, m, spacing, dt, shot, nsteps, rec, ckpt_every=40):
             nz, ny, nx = m.shape
-            vel = torch.sqrt(m.detach()).to(torch.float32).contiguous()
-            solver = WaveSolver((nx, ny, nz), spacing, dt, vel)
+            solver = WaveSolver((nx, ny, nz), spacing, dt,
+                                m.detach().to(torch.float32).contiguous(), squared=True)
             traces = torch.zeros((nsteps, rec.shape[0]), dtype=torch.float32, device=m.device)
             solver.propagate(shot, nsteps, rec, traces)
             solver.synchronize()

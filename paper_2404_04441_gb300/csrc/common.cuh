@@ -91,6 +91,13 @@ __device__ __forceinline__ float v2dt2(float v, float dh, float dl) {
   return fmaf(p, dh, fmaf(p, dl, e * dh));
 }
 
+// The model value to v^2 dt^2: a velocity v (sq = 0) through v2dt2, or a
+// squared velocity m = v^2 (sq = 1) as m dh + m dl, again within about one
+// unit in the last place of the exact m dt^2.
+__device__ __forceinline__ float model_to_c(float x, int sq, float dh, float dl) {
+  return sq ? fmaf(x, dh, x * dl) : v2dt2(x, dh, dl);
+}
+
 // v2dt2 in place over a field; n is a multiple of 4 and c is 16-byte aligned
 // (pitched field).
 __global__ void velocity_to_c_kernel(float *c, long long n, float dh, float dl) {
@@ -109,7 +116,8 @@ __global__ void velocity_to_c_kernel(float *c, long long n, float dh, float dl) 
 
 // One pass over a velocity model: c = v2dt2(v) into the pitched field (its
 // pitch columns [nx, px) written as zero), the largest velocity (float bits)
-// and the count of values that are not finite and positive. Rows of src are
+// and the count of values that are not finite and positive. With sq = 1 the
+// model holds m = v^2 instead (c = m dt^2, largest m). Rows of src are
 // sx floats apart: nx for a caller's dense array (device memory, or host
 // memory the GPU can read), px when converting a staged copy in place.
 // Blocks take whole rows; each thread loads four columns a block-width apart
@@ -117,7 +125,7 @@ __global__ void velocity_to_c_kernel(float *c, long long n, float dh, float dl) 
 __global__ void __launch_bounds__(256, 4)
     velocity_to_c_checked_kernel(const float *src, long long sx, float *c,
                                  int nx, int px, long long rows, float dh,
-                                 float dl, unsigned *vmax_bits,
+                                 float dl, int sq, unsigned *vmax_bits,
                                  unsigned long long *nbad) {
   unsigned local_max = 0;
   unsigned long long local_bad = 0;
@@ -141,7 +149,7 @@ __global__ void __launch_bounds__(256, 4)
           else
             local_max = max(local_max, __float_as_uint(v[j]));
         }
-        if (x < px) out[x] = x < nx ? v2dt2(v[j], dh, dl) : 0.f;
+        if (x < px) out[x] = x < nx ? model_to_c(v[j], sq, dh, dl) : 0.f;
       }
     }
   }
@@ -161,7 +169,7 @@ __global__ void __launch_bounds__(256, 4)
 // host link when src is host memory the GPU reads directly.
 __global__ void __launch_bounds__(256, 4)
     velocity_to_c_dense_kernel(const float4 *src, float4 *c, long long n4,
-                               float dh, float dl, unsigned *vmax_bits,
+                               float dh, float dl, int sq, unsigned *vmax_bits,
                                unsigned long long *nbad) {
   unsigned local_max = 0;
   unsigned long long local_bad = 0;
@@ -186,8 +194,8 @@ __global__ void __launch_bounds__(256, 4)
         else
           local_max = max(local_max, __float_as_uint(e[k]));
       }
-      c[i] = make_float4(v2dt2(e[0], dh, dl), v2dt2(e[1], dh, dl),
-                         v2dt2(e[2], dh, dl), v2dt2(e[3], dh, dl));
+      c[i] = make_float4(model_to_c(e[0], sq, dh, dl), model_to_c(e[1], sq, dh, dl),
+                         model_to_c(e[2], sq, dh, dl), model_to_c(e[3], sq, dh, dl));
     }
   }
   for (int o = 16; o > 0; o >>= 1) {

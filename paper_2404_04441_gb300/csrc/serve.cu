@@ -77,7 +77,7 @@ const Kind &kind_of(int storage) {
 size_t round_up(size_t x, size_t a) { return (x + a - 1) / a * a; }
 
 struct Request {
-  int64_t ticket = 0;
+  uint64_t ticket = 0;
   wave_request r{};
   int status = WAVE_EBUSY;
   double t_submit = 0, t_start = -1, t_done = -1, dt = 0;
@@ -141,8 +141,8 @@ struct serve_ctx {
   std::mutex mu;
   std::condition_variable cv_engine, cv_done;
   std::deque<Request *> queue;
-  std::unordered_map<int64_t, std::unique_ptr<Request>> all;
-  int64_t next_ticket = 1;
+  std::unordered_map<uint64_t, std::unique_ptr<Request>> all;
+  uint64_t next_ticket = 1;
   bool stopping = false;
   serve_stats_t st{};
   std::thread engine;
@@ -600,7 +600,7 @@ int serve_create(size_t hbm_budget_bytes, int max_slots, void *stream,
   return WAVE_OK;
 }
 
-int serve_submit(serve_ctx *s, const wave_request *req, int64_t *ticket) {
+int serve_submit(serve_ctx *s, const wave_request *req, uint64_t *ticket) {
   if (!s || !ticket) return WAVE_EINVAL;
   *ticket = 0;
   const int v = validate_request(req);
@@ -625,7 +625,7 @@ int serve_submit(serve_ctx *s, const wave_request *req, int64_t *ticket) {
   return WAVE_OK;
 }
 
-int serve_poll(serve_ctx *s, int64_t ticket, wave_result *out) {
+int serve_poll(serve_ctx *s, uint64_t ticket, wave_result *out) {
   if (!s) return WAVE_EINVAL;
   std::lock_guard<std::mutex> lk(s->mu);
   auto it = s->all.find(ticket);
@@ -634,7 +634,7 @@ int serve_poll(serve_ctx *s, int64_t ticket, wave_result *out) {
   return it->second->status;
 }
 
-int serve_wait(serve_ctx *s, int64_t ticket, double timeout_s,
+int serve_wait(serve_ctx *s, uint64_t ticket, double timeout_s,
                wave_result *out) {
   if (!s) return WAVE_EINVAL;
   std::unique_lock<std::mutex> lk(s->mu);

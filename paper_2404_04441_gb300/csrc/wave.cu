@@ -157,6 +157,7 @@ struct wave_ctx {
   bool model_checked = true;    // the host holds the velocity pass's verdict
   int model_status = WAVE_OK;   // that verdict (WAVE_EINVAL, WAVE_EUNSTABLE)
   bool at_rest = true;          // zero fields since creation or reset
+  int model_m = 0;              // the model was given as m = v^2 (wave_create_m)
   int cur = 0;
   int64_t step = 0;
   StepDesc *d_desc = nullptr;
@@ -350,10 +351,11 @@ int check_model(wave_ctx *c, const unsigned char *res) {
   std::memcpy(&vb, res, 4);
   std::memcpy(&bad, res + 8, 8);
   if (bad) return WAVE_EINVAL;
-  float vmax;
-  std::memcpy(&vmax, &vb, 4);
+  float top;
+  std::memcpy(&top, &vb, 4);
+  const double vmax = c->model_m ? std::sqrt((double)top) : (double)top;
   wave_spacing h{c->dx, c->dy, c->dz};
-  const double lim = wave_cfl_dt(&h, (double)vmax);
+  const double lim = wave_cfl_dt(&h, vmax);
   if (!(c->dt <= lim * (1.0 + 1e-12))) return WAVE_EUNSTABLE;
   c->vmax = vmax;
   return WAVE_OK;
@@ -555,10 +557,11 @@ static void launch_velocity_pass(wave_ctx *c, const float *src, long long sx,
   if (sx == c->px && c->px == c->nx && reinterpret_cast<uintptr_t>(s0) % 16 == 0) {
     velocity_to_c_dense_kernel<<<blocks, 256, 0, st>>>(
         reinterpret_cast<const float4 *>(s0), reinterpret_cast<float4 *>(c0),
-        (long long)(z1 - z0) * c->ny * c->px / 4, dh, dl, vmax, nbad);
+        (long long)(z1 - z0) * c->ny * c->px / 4, dh, dl, c->model_m, vmax, nbad);
   } else {
     velocity_to_c_checked_kernel<<<blocks, 256, 0, st>>>(
-        s0, sx, c0, c->nx, c->px, (long long)(z1 - z0) * c->ny, dh, dl, vmax, nbad);
+        s0, sx, c0, c->nx, c->px, (long long)(z1 - z0) * c->ny, dh, dl, c->model_m,
+        vmax, nbad);
   }
 }
 
@@ -703,6 +706,22 @@ int wave_create(const wave_grid *g, const wave_spacing *h, double dt,
   int st = new_context(g, h, dt, velocity, storage, stream, &c);
   if (st != WAVE_OK) return st;
   st = create_impl(c, velocity);
+  if (st != WAVE_OK) {
+    cudaGetLastError();
+    wave_destroy(c);
+    return st;
+  }
+  *out = c;
+  return WAVE_OK;
+}
+
+int wave_create_m(const wave_grid *g, const wave_spacing *h, double dt,
+                  const float *m, int storage, void *stream, wave_ctx **out) {
+  wave_ctx *c = nullptr;
+  int st = new_context(g, h, dt, m, storage, stream, &c);
+  if (st != WAVE_OK) return st;
+  c->model_m = 1;
+  st = create_impl(c, m);
   if (st != WAVE_OK) {
     cudaGetLastError();
     wave_destroy(c);

@@ -35,10 +35,11 @@ def _dt(pkg, cfg, *models):
     return 0.5 * pkg.wave_cfl_dt(cfg["spacing"], max(float(m.max()) for m in models) * 1.02)
 
 
-def _gpu_gradient(pkg, vel, cfg, dt, shot, rec, obs, ckpt):
+def _gpu_gradient(pkg, vel, cfg, dt, shot, rec, obs, ckpt, squared=False):
     import torch
     nx, ny, nz = cfg["shape"]
-    s = pkg.WaveSolver((nx, ny, nz), cfg["spacing"], dt, torch.from_numpy(vel).cuda())
+    s = pkg.WaveSolver((nx, ny, nz), cfg["spacing"], dt, torch.from_numpy(vel).cuda(),
+                       squared=squared)
     g = torch.empty((nz, ny, nx), device="cuda")
     tr = torch.empty((cfg["nsteps"], rec.shape[0]), device="cuda")
     mis = s.gradient(shot, cfg["nsteps"], torch.from_numpy(rec).cuda(),
@@ -123,10 +124,16 @@ def test_autograd_matches_wave_gradient(wave_lib, oracle_mod):
                               ckpt_every=7)
     loss = 0.5 * ((tr.double() - obs32.double()) ** 2).sum()
     (gm,) = torch.autograd.grad(loss, m)
-    v = torch.sqrt(m.detach()).float().cpu().numpy()
-    mis, g, _ = _gpu_gradient(wave_lib, v, cfg, dt, shot, rec, obs.astype(np.float32), 7)
+    # the same model given as m = v^2 to wave_create_m: the same arithmetic
+    mis, g, _ = _gpu_gradient(wave_lib, m.detach().cpu().numpy(), cfg, dt, shot, rec,
+                              obs.astype(np.float32), 7, squared=True)
     assert float(loss.detach()) == pytest.approx(mis, rel=1e-6)
     assert rel_l2(gm.cpu().numpy(), g) <= 1e-5
+    # and as velocities v = sqrt(m): v^2 dt^2 within an ulp or two of m dt^2
+    v = torch.sqrt(m.detach()).float().cpu().numpy()
+    mis_v, g_v, _ = _gpu_gradient(wave_lib, v, cfg, dt, shot, rec, obs.astype(np.float32), 7)
+    assert mis_v == pytest.approx(mis, rel=1e-5)
+    assert rel_l2(g_v, g) <= 1e-4
 
 
 def test_host_buffers_and_unsupported_storage(wave_lib, oracle_mod):

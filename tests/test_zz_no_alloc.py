@@ -91,3 +91,48 @@ def test_noalloc_refuses_requests_beyond_its_array(wave_lib):
                                         rec, tr)
     assert ei.value.code == -9
     assert float(u.abs().max()) == 0.0 and float(tr.abs().max()) == 0.0
+
+
+def test_noalloc_host_receivers_no_source_and_zero_steps(wave_lib):
+    """The branches the first test does not reach: receivers in host memory
+    (staged through the library's static buffer), no source (no wavelet
+    block, so the tables start earlier), and nsteps = 0 (validation only,
+    the buffers left as they were). A warm call also leaves the device's
+    free memory unchanged: it allocates nothing."""
+    import torch
+    nx, ny, nz = 40, 28, 22
+    sp = (10.0, 10.0, 10.0)
+    rng = np.random.default_rng(31)
+    vel = rng.uniform(1500.0, 3500.0, size=(nz, ny, nx)).astype(np.float32)
+    u0, up0 = wl.random_state((nz, ny, nx), seed=32)
+    dt = 0.45 * wave_lib.wave_cfl_dt(sp, float(vel.max()))
+    rec = wl.random_receivers(nx, ny, nz, 25, seed=33)
+    n = 9
+
+    ref = wave_lib.WaveSolver((nx, ny, nz), sp, dt, torch.from_numpy(vel).cuda())
+    ref.set_state(u0, up0, 0)
+    rtr = np.zeros((n, rec.shape[0]), dtype=np.float32)
+    ref.propagate(None, n, rec, rtr)
+    ru = np.empty((nz, ny, nx), dtype=np.float32)
+    ref.get_field(0, ru)
+    ref.close()
+
+    vel_d = torch.from_numpy(vel).cuda()
+    bufs = [torch.from_numpy(u0).cuda(), torch.from_numpy(up0).cuda()]
+    # nsteps = 0: nothing moves
+    newest = wave_lib.wave_propagate_noalloc((nx, ny, nz), sp, dt, vel_d, bufs[0], bufs[1],
+                                             None, 0, 0)
+    assert newest == 0
+    assert np.array_equal(bufs[0].cpu().numpy(), u0)
+    assert np.array_equal(bufs[1].cpu().numpy(), up0)
+    tr = torch.zeros((n, rec.shape[0]), dtype=torch.float32, device="cuda")
+    torch.cuda.synchronize()
+    free0, _ = torch.cuda.mem_get_info()
+    newest = wave_lib.wave_propagate_noalloc((nx, ny, nz), sp, dt, vel_d, bufs[0], bufs[1],
+                                             None, 0, n, rec, tr)
+    torch.cuda.synchronize()
+    free1, _ = torch.cuda.mem_get_info()
+    assert free1 == free0
+    got = bufs[newest].cpu().numpy()
+    assert rel_l2(got, ru) <= TOL
+    assert rel_l2(tr.cpu().numpy(), rtr) <= TOL
