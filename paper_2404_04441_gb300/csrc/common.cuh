@@ -226,10 +226,6 @@ template <>
 __device__ __forceinline__ __half from_f32(float v) {
   return __float2half_rn(v);
 }
-__device__ __forceinline__ float to_f32(__nv_bfloat16 v) {
-  return __bfloat162float(v);
-}
-__device__ __forceinline__ float to_f32(__half v) { return __half2float(v); }
 
 // Dense FP32 (x fastest) -> pitched 16-bit field with scale 2^exps[slot].
 template <class T>
@@ -519,6 +515,21 @@ std::vector<int> plan_layers(int nz, long long ntiles, long long slots,
   int out[kMaxLayers];
   const int n = plan_layers(nz, ntiles, slots, preroll, out);
   return std::vector<int>(out, out + n);
+}
+
+// Eq. 1 coefficients of one grid spacing (kernel parameters).
+StencilCoefs make_coefs(double dx, double dy, double dz) {
+  StencilCoefs k{};
+  const double ix = 1.0 / (dx * dx), iy = 1.0 / (dy * dy), iz = 1.0 / (dz * dz);
+  k.c0 = (float)(kW[0] * (ix + iy + iz));
+  for (int m = 1; m <= 4; ++m) {
+    k.cx[m - 1] = (float)(kW[m] * ix);
+    k.cy[m - 1] = (float)(kW[m] * iy);
+    k.cz[m - 1] = (float)(kW[m] * iz);
+  }
+  k.sxi = (float)(ix / 5040.0);
+  k.syi = (float)(iy / 5040.0);
+  return k;
 }
 
 void set_layers(SweepArgs &a, const int *ch, int n) {

@@ -20,10 +20,11 @@ using namespace gbw;
 namespace {
 
 // One kernel configuration per storage type (index = WAVE_STORAGE_*), the
-// same tiles as the single-grid defaults.
+// single-grid defaults: FP32 32 x 16 tiles of 4 warps, 16-bit on the tensor
+// cores with 64 x 16 tiles of 8 warps.
 using ServeF32 = SweepCfg<32, 16, 1, 4, 4>;
-using ServeB16 = SweepCfg<64, 8, 1, 4, 4, __nv_bfloat16>;
-using ServeH16 = SweepCfg<64, 8, 1, 4, 4, __half>;
+using ServeB16 = TcCfg<64, 4, 2, __nv_bfloat16>;
+using ServeH16 = TcCfg<64, 4, 2, __half>;
 constexpr int kKinds = 3;
 constexpr int kMaxGroup = 16;     // batch steps between two engine checks
 constexpr int kLayerPlanes = 256; // target z planes per CTA for batched shots
@@ -37,6 +38,7 @@ constexpr int kTargetWaves = 6;
 
 struct Kind {
   int tx, ty, hx, esize, threads;
+  int box_u, box_p;  // TMA box widths: u plane with halo, u_prev / c tiles
   size_t smem;
   const void *func;
   void (*launch)(int, cudaStream_t, const BatchShot *, int, long long,
@@ -63,6 +65,8 @@ Kind make_kind() {
               C::HX,
               (int)sizeof(typename C::T),
               C::THREADS,
+              C::BOX_U,
+              C::BOX_P,
               C::SMEM_BYTES,
               reinterpret_cast<const void *>(&wave_sweep_batched_kernel<C>),
               &launch_batch<C>};
@@ -110,6 +114,12 @@ int request_ctas(const wave_request &r) {
   return ntiles * request_layers(r.grid.nz);
 }
 
+// The same in CTA places of 128 threads (an FP32 CTA; a 16-bit CTA of 8
+// warps takes two), the unit of the admission's CTA target.
+int request_places(const wave_request &r) {
+  return request_ctas(r) * (kind_of(r.storage).threads / 128);
+}
+
 size_t request_bytes(const wave_request &r) {
   const Kind &k = kind_of(r.storage);
   const size_t nx = r.grid.nx, ny = r.grid.ny, nz = r.grid.nz;
@@ -149,7 +159,8 @@ struct serve_ctx {
   // Engine thread only.
   std::vector<Request *> resident;
   size_t bytes = 0;
-  long long ctas = 0;         // CTAs of one batched step over the resident shots
+  long long ctas = 0;         // CTA places (128 threads) of one batched step
+                              // over the resident shots
   long long target_ctas = 0;  // admission adds no shot beyond this (kTargetWaves)
   long long k = 0;  // batch steps taken
   BatchShot *d_table[kKinds] = {nullptr, nullptr, nullptr};
@@ -300,14 +311,14 @@ int admit(serve_ctx *s, Request *q) {
   const CUtensorMapDataType dtf = field_dtype(r.storage);
   for (int i = 0; i < 2; ++i) {
     if ((e = encode_map(&b.halo[i], q->buf[i], nx, ny, nz, pxu, kd.esize, dtf,
-                        kd.tx + 2 * kd.hx, kd.ty + 2 * kR)))
+                        kd.box_u, kd.ty + 2 * kR)))
       return e;
     if ((e = encode_map(&b.tile[i], q->buf[i], nx, ny, nz, pxu, kd.esize, dtf,
-                        kd.tx, kd.ty)))
+                        kd.box_p, kd.ty)))
       return e;
   }
   if ((e = encode_map(&b.cmap, q->c, nx, ny, nz, px, 4,
-                      CU_TENSOR_MAP_DATA_TYPE_FLOAT32, kd.tx, kd.ty)))
+                      CU_TENSOR_MAP_DATA_TYPE_FLOAT32, kd.box_p, kd.ty)))
     return e;
   SweepArgs &a = b.args;
   a.nx = nx;
@@ -320,15 +331,7 @@ int admit(serve_ctx *s, Request *q) {
   for (int z = 0; z < nz; z += zc) layers.push_back(std::min(zc, nz - z));
   set_layers(a, layers);
   a.ntx = ntx;
-  const double ix = 1.0 / (r.spacing.dx * r.spacing.dx),
-               iy = 1.0 / (r.spacing.dy * r.spacing.dy),
-               iz = 1.0 / (r.spacing.dz * r.spacing.dz);
-  a.k.c0 = (float)(kW[0] * (ix + iy + iz));
-  for (int m = 1; m <= 4; ++m) {
-    a.k.cx[m - 1] = (float)(kW[m] * ix);
-    a.k.cy[m - 1] = (float)(kW[m] * iy);
-    a.k.cz[m - 1] = (float)(kW[m] * iz);
-  }
+  a.k = make_coefs(r.spacing.dx, r.spacing.dy, r.spacing.dz);
   a.desc = q->desc;
   a.cmax = (float)((double)vmax * vmax * dt * dt);
   b.buf[0] = q->buf[0];
@@ -419,7 +422,7 @@ void engine_main(serve_ctx *s) {
         if (!s->queue.empty() && (int)s->resident.size() < s->max_slots &&
             s->bytes + s->queue.front()->bytes <= s->budget &&
             (s->resident.empty() ||
-             s->ctas + request_ctas(s->queue.front()->r) <= s->target_ctas)) {
+             s->ctas + request_places(s->queue.front()->r) <= s->target_ctas)) {
           q = s->queue.front();
           s->queue.pop_front();
           s->st.queued--;
@@ -439,7 +442,7 @@ void engine_main(serve_ctx *s) {
         q->t_start = s->now();
         s->resident.push_back(q);
         s->bytes += q->bytes;
-        s->ctas += q->ctas;
+        s->ctas += request_places(q->r);
         s->st.resident = (int64_t)s->resident.size();
         s->st.bytes_resident = s->bytes;
         s->st.bytes_peak = std::max(s->st.bytes_peak, s->bytes);
@@ -496,7 +499,7 @@ void engine_main(serve_ctx *s) {
         continue;
       }
       s->bytes -= q->bytes;
-      s->ctas -= q->ctas;
+      s->ctas -= request_places(q->r);
       s->dirty = true;
     }
     std::lock_guard<std::mutex> lk(s->mu);

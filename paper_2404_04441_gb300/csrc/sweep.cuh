@@ -29,6 +29,7 @@
 #include <cuda_bf16.h>
 #include <cuda_fp16.h>
 #include <cstdint>
+#include <type_traits>
 
 #include "ptx.cuh"
 
@@ -75,7 +76,15 @@ constexpr int kModeGradAcc = 4;  // (a.ghi, a.glo) += u * a.dsrc, per point
 struct StencilCoefs {
   float c0;                   // w0 * (1/dx^2 + 1/dy^2 + 1/dz^2)
   float cx[4], cy[4], cz[4];  // w_m / h_a^2 for m = 1..4
+  float sxi, syi;             // 1 / (5040 h_a^2), a = x, y: scale of the
+                              // integer weights 5040 w_m (tensor-core sweep)
 };
+
+// Eq. 1's off-centre weights times 5040 (the least common multiple of their
+// denominators): 8064, -1008, 128, -9. Each is exact in FP16 and in BF16 (at
+// most 6 significant bits), so the 16-bit tensor-core sweep multiplies the
+// stored wavefield by exact weights and scales the FP32 sums once.
+constexpr float kWInt[5] = {0.f, 8064.f, -1008.f, 128.f, -9.f};
 
 struct SweepArgs {
   int nx, ny, nz, px;  // interior sizes; px = row pitch in elements (16 B rows)
@@ -200,6 +209,7 @@ struct SweepCfg {
   using T = T_;
   static constexpr int TX = TX_, TY = TY_, VY = VY_, PF = PF_, MINB = MINB_;
   static constexpr bool kScaled = sizeof(T) == 2;
+  static constexpr bool kTensor = false;
   static constexpr int HX = Elem<T>::kHaloX;  // box columns left of the tile
   static constexpr int NTX = TX / 4;          // threads along x (4 points each)
   static constexpr int NTY = TY / VY;         // threads along y (VY rows each)
@@ -209,6 +219,8 @@ struct SweepCfg {
   static constexpr int NB = PF + 1;           // one barrier per in-flight stage
   static constexpr int UW = TX + 2 * HX;      // u slot row length (elements)
   static constexpr int UH = TY + 2 * kR;
+  static constexpr int BOX_U = UW;            // TMA box widths: u with halo,
+  static constexpr int BOX_P = TX;            // u_prev and v^2 dt^2 tiles
   static constexpr int U_SLOT = UW * UH;      // elements
   static constexpr int P_SLOT = TX * TY;      // elements
   static constexpr uint32_t U_BYTES = U_SLOT * sizeof(T);
@@ -226,6 +238,46 @@ struct SweepCfg {
                     C_BYTES % 128 == 0,
                 "slot alignment");
   static_assert(UW <= 256 && UH <= 256, "TMA box limit");
+};
+
+
+// 16-bit storage on the tensor cores: TX x 16 tiles (TX = 32, 64 or 128), one
+// warp per block of 8 x-columns by all 16 rows. Same rings as SweepCfg (u
+// planes with the halo, u_prev and v^2 dt^2 tiles, a staging plane, one
+// barrier per stage in flight), with wider TMA boxes so that the warps'
+// shared-memory accesses fall in distinct banks: u rows of TX + 24 elements
+// (112, 176 or 304 bytes: the 8 rows of an ldmatrix land on 8 disjoint
+// groups of 4 banks), u_prev and v^2 dt^2 rows of TX + 8 (the extra columns
+// are the next tile's, read from L2).
+template <int TX_, int PF_, int MINB_, class T_>
+struct TcCfg {
+  using T = T_;
+  static_assert(sizeof(T) == 2, "16-bit storage only");
+  static_assert(TX_ == 32 || TX_ == 64 || TX_ == 128, "tile width");
+  static constexpr bool kScaled = true;
+  static constexpr bool kTensor = true;
+  static constexpr int TX = TX_, TY = 16, VY = 1, PF = PF_, MINB = MINB_;
+  static constexpr int HX = Elem<T>::kHaloX;  // 8: 16-byte aligned box start
+  static constexpr int THREADS = 4 * TX;      // one warp per 8 columns
+  static constexpr int SU = PF + 5;
+  static constexpr int SP = PF + 1;
+  static constexpr int NB = PF + 1;
+  static constexpr int UW = TX + 24;      // u slot row (elements): x0-8 .. x0+TX+15
+  static constexpr int UH = TY + 2 * kR;
+  static constexpr int PW = TX + 8;       // u_prev / v^2 dt^2 slot row
+  static constexpr int BOX_U = UW, BOX_P = PW;
+  static constexpr int U_SLOT = UW * UH;
+  static constexpr int P_SLOT = PW * TY;
+  static constexpr uint32_t U_BYTES = U_SLOT * sizeof(T);
+  static constexpr uint32_t UP_BYTES = P_SLOT * sizeof(T);
+  static constexpr uint32_t C_BYTES = P_SLOT * 4;
+  // rings, then one barrier per stage in flight (receivers are recorded
+  // by the threads that own the points: no staging plane)
+  static constexpr size_t SMEM_BYTES = (size_t)SU * U_BYTES +
+                                       (size_t)SP * (UP_BYTES + C_BYTES) + NB * 8;
+  static_assert(SU == 9, "the plane loop keeps ring slot = plane mod 9");
+  static_assert(U_BYTES % 128 == 0 && UP_BYTES % 128 == 0 && C_BYTES % 128 == 0,
+                "slot alignment");
 };
 
 // hi + lo += u d without loss: the product exactly as p + e (an FMA gives
@@ -679,6 +731,373 @@ wait_failed:
   }
 }
 
+// ---------------------------------------------------------------------------
+// 16-bit storage with the x and y parts of Eq. 1 on the tensor cores.
+//
+// In stored units, the y part at output (x, y) is sum_m 5040 w_m (U(y+m) +
+// U(y-m)) / (5040 h_y^2). For a warp's block (all 16 rows of the tile by 8
+// columns) it is a banded 16 x 24 matrix of the integer weights kWInt times
+// the 24 rows of the plane (tile rows -4..19) at those columns: two
+// mma.sync m16n8k16 k-steps over plane rows -4..11 and 12..19, the 16-bit
+// operands straight from the TMA-staged plane (ldmatrix), FP32
+// accumulation. The x part is the plane's 16 rows at columns x-8..x+7 and
+// x+8..x+15 times a banded weight matrix, two more k-steps. Every product
+// of a stored value and an integer weight is exact in FP32; only the sums
+// round. The z part, the centre term and the update stay in FP32 on the
+// CUDA cores as in sweep_cta. Each thread owns the four points of its mma
+// accumulator: rows g and g+8 of the tile, columns 2c and 2c+1 of its
+// warp's block (g = lane / 4, c = lane % 4), i.e. two pairs of adjacent
+// points, loaded and stored as 32-bit pairs.
+
+template <class T>
+__device__ __forceinline__ unsigned pack_pair(float lo, float hi);
+template <>
+__device__ __forceinline__ unsigned pack_pair<__half>(float lo, float hi) {
+  const __half2 h = __floats2half2_rn(lo, hi);
+  return *reinterpret_cast<const unsigned *>(&h);
+}
+template <>
+__device__ __forceinline__ unsigned pack_pair<__nv_bfloat16>(float lo, float hi) {
+  const __nv_bfloat162 h = __floats2bfloat162_rn(lo, hi);
+  return *reinterpret_cast<const unsigned *>(&h);
+}
+
+template <class T>
+__device__ __forceinline__ void mma_16816(float (&d)[4], const unsigned (&a)[4],
+                                          unsigned b0, unsigned b1);
+template <>
+__device__ __forceinline__ void mma_16816<__half>(float (&d)[4], const unsigned (&a)[4],
+                                                  unsigned b0, unsigned b1) {
+  asm("mma.sync.aligned.m16n8k16.row.col.f32.f16.f16.f32 {%0,%1,%2,%3}, "
+      "{%4,%5,%6,%7}, {%8,%9}, {%0,%1,%2,%3};"
+      : "+f"(d[0]), "+f"(d[1]), "+f"(d[2]), "+f"(d[3])
+      : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b0), "r"(b1));
+}
+template <>
+__device__ __forceinline__ void mma_16816<__nv_bfloat16>(float (&d)[4],
+                                                         const unsigned (&a)[4],
+                                                         unsigned b0, unsigned b1) {
+  asm("mma.sync.aligned.m16n8k16.row.col.f32.bf16.bf16.f32 {%0,%1,%2,%3}, "
+      "{%4,%5,%6,%7}, {%8,%9}, {%0,%1,%2,%3};"
+      : "+f"(d[0]), "+f"(d[1]), "+f"(d[2]), "+f"(d[3])
+      : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b0), "r"(b1));
+}
+
+// Four 8 x 8 matrices of 16-bit elements from shared memory (lanes 8j..8j+7
+// give the row addresses of matrix j), as stored or transposed.
+__device__ __forceinline__ void ldsm_x4(unsigned (&r)[4], uint32_t addr) {
+  asm volatile("ldmatrix.sync.aligned.m8n8.x4.shared.b16 {%0,%1,%2,%3}, [%4];"
+               : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3])
+               : "r"(addr)
+               : "memory");
+}
+__device__ __forceinline__ void ldsm_x4_trans(unsigned (&r)[4], uint32_t addr) {
+  asm volatile(
+      "ldmatrix.sync.aligned.m8n8.x4.trans.shared.b16 {%0,%1,%2,%3}, [%4];"
+      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3])
+      : "r"(addr)
+      : "memory");
+}
+
+// Two 16-bit elements (one 32-bit word) to FP32, low element first.
+template <class T>
+__device__ __forceinline__ float2 pair_to_f32(unsigned w);
+template <>
+__device__ __forceinline__ float2 pair_to_f32<__half>(unsigned w) {
+  return __half22float2(*reinterpret_cast<const __half2 *>(&w));
+}
+template <>
+__device__ __forceinline__ float2 pair_to_f32<__nv_bfloat16>(unsigned w) {
+  return make_float2(__uint_as_float(w << 16), __uint_as_float(w & 0xffff0000u));
+}
+
+__device__ __forceinline__ float wint(int off) {
+  switch (off < 0 ? -off : off) {
+    case 1: return 8064.f;   // 5040 w_m, m = 1..4 (kWInt)
+    case 2: return -1008.f;
+    case 3: return 128.f;
+    case 4: return -9.f;
+    default: return 0.f;
+  }
+}
+
+__device__ __forceinline__ float to_f32(__nv_bfloat16 v) {
+  return __bfloat162float(v);
+}
+__device__ __forceinline__ float to_f32(__half v) { return __half2float(v); }
+
+template <class C>
+__device__ __forceinline__ void sweep_cta_tc(const CUtensorMap *tm_u,
+                                             const CUtensorMap *tm_up,
+                                             const CUtensorMap *tm_c,
+                                             const SweepArgs &a,
+                                             const StencilCoefs &co, int bx,
+                                             int by, int bz,
+                                             unsigned char *smem_raw,
+                                             void *unext, int koff) {
+  using T = typename C::T;
+  unsigned char *base = smem_raw;
+  T *su = reinterpret_cast<T *>(base);
+  T *sp = reinterpret_cast<T *>(base + C::SU * C::U_BYTES);
+  float *sc = reinterpret_cast<float *>(base + C::SU * C::U_BYTES +
+                                        C::SP * C::UP_BYTES);
+  uint64_t *bars = reinterpret_cast<uint64_t *>(sc + C::SP * C::P_SLOT);
+
+  const int tid = threadIdx.x;
+  const int lane = tid & 31, warp = tid >> 5;
+  const int g = lane >> 2, cq = lane & 3;
+  // this thread's points, tile-relative: columns xt, xt+1 of rows g, g+8
+  const int xt = 8 * warp + 2 * cq;
+  const int x0 = bx * C::TX;
+  const int y0 = by * C::TY;
+  const int zb = a.zl[bz];
+  const int ze = a.zl[bz + 1];
+  const int NS = (ze - zb) + 2 * kR;
+
+  StepDesc *d = a.desc;
+  const long long n = d->n + koff;
+  const int nrec = d->nrec;
+  const int sx = d->sx - x0, sy = d->sy - y0, sz = d->sz;
+  const bool src_here = d->src_active && sx >= 0 && sx < C::TX && sy >= 0 &&
+                        sy < C::TY && sz >= zb && sz < ze;
+  float wsrc = src_here ? d->wavelet[n] : 0.f;
+  int rcur = 0, rend = 0;
+  const int4 *rec = d->rec;
+  if (nrec > 0) {
+    const int tile = by * a.ntx + bx;
+    rcur = d->rec_start[tile];
+    rend = d->rec_start[tile + 1];
+    while (rcur < rend && rec[rcur].x < zb) ++rcur;
+  }
+  int rz = (rcur < rend) ? rec[rcur].x : 0x7fffffff;
+  float *trow = (nrec > 0) ? d->traces + (size_t)n * nrec : nullptr;
+
+  // Field scales (see sweep_cta).
+  const long long ab = d->step0 + n;
+  float s1, s2, so;
+  {
+    const int eu = d->exps[ab & 3], eup = d->exps[(ab + 3) & 3];
+    const float mu = __uint_as_float(d->maxbits[ab & 3]);
+    const float mup = __uint_as_float(d->maxbits[(ab + 3) & 3]);
+    float bound = 8.f * fmaxf(mu, mup);
+    if (d->src_active) bound += a.cmax * fabsf(d->wavelet[n]);
+    int eo = 0;
+    if (bound > 0.f) {
+      int e2;
+      frexpf(bound, &e2);
+      eo = e2 - 15;
+    }
+    s1 = exp2_int(eu - eo);
+    s2 = exp2_int(eup - eo);
+    so = exp2_int(eo);
+    wsrc *= exp2_int(-eo);
+    if (bx == 0 && by == 0 && bz == 0 && tid == 0) {
+      d->exps[(ab + 1) & 3] = eo;
+      d->maxbits[(ab + 2) & 3] = 0u;
+    }
+  }
+  float vmax_out = 0.f;
+
+  // Constant mma operands. y: A[m][k] = weight of plane row k (slot row,
+  // tile row k - 4) for output row m; k-step 0 takes slot rows 0..15, k-step
+  // 1 slot rows 8..23 of which only 16..23 (k >= 8) carry weights. x: B[k][n]
+  // = weight of column k of the window for output column n; window 0 starts
+  // 8 columns left of the block, window 1 at the block (only k >= 8 used).
+  unsigned ya[2][4], xbw[2][2];
+#pragma unroll
+  for (int ks = 0; ks < 2; ++ks) {
+    auto A = [&](int m, int k) {
+      return ks == 0 ? wint(k - 4 - m) : (k >= 8 ? wint(k + 4 - m) : 0.f);
+    };
+    ya[ks][0] = pack_pair<T>(A(g, 2 * cq), A(g, 2 * cq + 1));
+    ya[ks][1] = pack_pair<T>(A(g + 8, 2 * cq), A(g + 8, 2 * cq + 1));
+    ya[ks][2] = pack_pair<T>(A(g, 2 * cq + 8), A(g, 2 * cq + 9));
+    ya[ks][3] = pack_pair<T>(A(g + 8, 2 * cq + 8), A(g + 8, 2 * cq + 9));
+    auto B = [&](int k, int nn) {
+      return ks == 0 ? wint(k - 8 - nn) : (k >= 8 ? wint(k - nn) : 0.f);
+    };
+    xbw[ks][0] = pack_pair<T>(B(2 * cq, g), B(2 * cq + 1, g));
+    xbw[ks][1] = pack_pair<T>(B(2 * cq + 8, g), B(2 * cq + 9, g));
+  }
+  // ldmatrix row addresses within a u slot (elements). y (transposed): lane
+  // l gives row (l & 7) of matrix l / 8 = slot rows 0..7, 8..15, 8..15,
+  // 16..23 at the block's columns. x (as stored): rows (l & 7) + 8 (l/8 odd)
+  // of the tile (slot rows + 4) at the window's column 0 or 8.
+  const int lj = lane >> 3;
+  const int off_y = (8 * ((lj + 1) >> 1) + (lane & 7)) * C::UW + C::HX + 8 * warp;
+  const int off_x0 = ((lane & 7) + 8 * (lj & 1) + kR) * C::UW + 8 * warp +
+                     8 * (lj >> 1);               // window 0: block column - 8
+  const int off_x1 = off_x0 + C::HX;              // window 1: block column
+  // the thread's points in a u slot and in a tile slot (elements)
+  const int ua = (g + kR) * C::UW + C::HX + xt, ub = ua + 8 * C::UW;
+  const int pa = g * C::PW + xt, pb = pa + 8 * C::PW;
+  // their indices within the tile (receiver table entries) and in the
+  // output field (elements of plane 0), with their bounds
+  const int la = g * C::TX + xt, lb = la + 8 * C::TX;
+  const size_t plane_stride = (size_t)a.ny * a.px;
+  const size_t oa = (size_t)(y0 + g) * a.px + (x0 + xt);
+  const size_t ob = oa + 8 * (size_t)a.px;
+  const bool in_x = x0 + xt < a.px;
+  const bool wa = in_x && y0 + g < a.ny, wb = in_x && y0 + g + 8 < a.ny;
+
+  if (tid == 0) {
+    prefetch_tensormap(tm_u);
+    prefetch_tensormap(tm_up);
+    prefetch_tensormap(tm_c);
+    for (int b = 0; b < C::NB; ++b) mbar_init(&bars[b], 1);
+    fence_barrier_init();
+  }
+  __syncthreads();
+
+  // Stage t brings u plane zb-4+t (slot t % 9) and, once t >= 8, u_prev and
+  // v^2 dt^2 of plane zb-8+t (the plane computed at iteration t).
+  auto issue = [&](int t) {
+    uint64_t *bar = &bars[t % C::NB];
+    const int j = zb - 2 * kR + t;
+    const bool full = j >= zb;
+    mbar_arrive_expect_tx(bar,
+                          C::U_BYTES + (full ? C::UP_BYTES + C::C_BYTES : 0));
+    tma_load_3d(su + (t % C::SU) * C::U_SLOT, tm_u, bar, x0 - C::HX, y0 - kR,
+                j + kR);
+    if (full) {
+      tma_load_3d(sp + (t % C::SP) * C::P_SLOT, tm_up, bar, x0, y0, j);
+      tma_load_3d(sc + (t % C::SP) * C::P_SLOT, tm_c, bar, x0, y0, j);
+    }
+  };
+  if (tid == 0)
+    for (int t = 0; t < C::PF && t < NS; ++t) issue(t);
+
+  // q[k]: u of the thread's points (row g: x, y; row g+8: z, w)
+  float4 q[9];
+#pragma unroll
+  for (int k = 0; k < 9; ++k) q[k] = make_float4(0.f, 0.f, 0.f, 0.f);
+
+  int s = 0;
+  for (int s0 = 0; s0 < NS; s0 += 9) {
+#pragma unroll
+    for (int p = 0; p < 9; ++p) {
+      s = s0 + p;
+      if (s >= NS) break;
+      // One barrier per plane: stage s has landed for every thread (a
+      // uniform verdict, so a timeout leaves the loop everywhere) and every
+      // thread is done with plane s-1, whose slots the next issue reuses.
+      const bool ok =
+          mbar_wait_bounded(&bars[s % C::NB], (s / C::NB) & 1, kWaitLimitNs);
+      if (__syncthreads_or(!ok)) goto wait_failed;
+      if (tid == 0 && s + C::PF < NS) issue(s + C::PF);
+      {
+        const T *uf = su + p * C::U_SLOT;  // SU == 9: slot of stage s is s % 9
+        const float2 fa = pair_to_f32<T>(*reinterpret_cast<const unsigned *>(uf + ua));
+        const float2 fb = pair_to_f32<T>(*reinterpret_cast<const unsigned *>(uf + ub));
+        q[p] = make_float4(fa.x, fa.y, fb.x, fb.y);
+      }
+      const int j = zb - 2 * kR + s;
+      if (j >= zb) {
+        const T *uc = su + ((p + 5) % 9) * C::U_SLOT;  // plane j
+        const T *pp = sp + (s % C::SP) * C::P_SLOT;
+        const float *pc = sc + (s % C::SP) * C::P_SLOT;
+        // x and y parts on the tensor cores (integer weights, stored units)
+        float dyv[4] = {0.f, 0.f, 0.f, 0.f}, dxv[4] = {0.f, 0.f, 0.f, 0.f};
+        {
+          unsigned r[4];
+          ldsm_x4_trans(r, smem_addr(uc + off_y));
+          mma_16816<T>(dyv, ya[0], r[0], r[1]);
+          mma_16816<T>(dyv, ya[1], r[2], r[3]);
+          ldsm_x4(r, smem_addr(uc + off_x0));
+          mma_16816<T>(dxv, r, xbw[0][0], xbw[0][1]);
+          ldsm_x4(r, smem_addr(uc + off_x1));
+          mma_16816<T>(dxv, r, xbw[1][0], xbw[1][1]);
+        }
+        const float2 upa = pair_to_f32<T>(*reinterpret_cast<const unsigned *>(pp + pa));
+        const float2 upb = pair_to_f32<T>(*reinterpret_cast<const unsigned *>(pp + pb));
+        const float2 cvl = *reinterpret_cast<const float2 *>(pc + pa);
+        const float2 cvh = *reinterpret_cast<const float2 *>(pc + pb);
+
+        const float4 a1 = q[(p + 5) % 9];  // centre plane j
+        float2 lo = __fmul2_rn(make_float2(co.c0, co.c0), make_float2(a1.x, a1.y));
+        float2 hi = __fmul2_rn(make_float2(co.c0, co.c0), make_float2(a1.z, a1.w));
+#pragma unroll
+        for (int m = 1; m <= kR; ++m) {
+          const float4 zm = q[(p + 5 - m + 9) % 9];
+          const float4 zp = q[(p + 5 + m) % 9];
+          const float2 cz2 = make_float2(co.cz[m - 1], co.cz[m - 1]);
+          lo = __ffma2_rn(cz2, __fadd2_rn(make_float2(zm.x, zm.y), make_float2(zp.x, zp.y)), lo);
+          hi = __ffma2_rn(cz2, __fadd2_rn(make_float2(zm.z, zm.w), make_float2(zp.z, zp.w)), hi);
+        }
+        const float2 sy2 = make_float2(co.syi, co.syi), sx2 = make_float2(co.sxi, co.sxi);
+        lo = __ffma2_rn(sy2, make_float2(dyv[0], dyv[1]), lo);
+        hi = __ffma2_rn(sy2, make_float2(dyv[2], dyv[3]), hi);
+        lo = __ffma2_rn(sx2, make_float2(dxv[0], dxv[1]), lo);
+        hi = __ffma2_rn(sx2, make_float2(dxv[2], dxv[3]), hi);
+
+        const float2 ul = make_float2(a1.x, a1.y), uh = make_float2(a1.z, a1.w);
+        const float2 s1v = make_float2(s1, s1), s2v = make_float2(s2, s2);
+        float2 ol = __ffma2_rn(s1v, __ffma2_rn(cvl, lo, __fadd2_rn(ul, ul)),
+                               __fmul2_rn(s2v, make_float2(-upa.x, -upa.y)));
+        float2 oh = __ffma2_rn(s1v, __ffma2_rn(cvh, hi, __fadd2_rn(uh, uh)),
+                               __fmul2_rn(s2v, make_float2(-upb.x, -upb.y)));
+        if (src_here && j == sz) {
+          const int e = sx - xt;
+          if (sy == g) {
+            if (e == 0) ol.x = fmaf(cvl.x, wsrc, ol.x);
+            if (e == 1) ol.y = fmaf(cvl.y, wsrc, ol.y);
+          }
+          if (sy == g + 8) {
+            if (e == 0) oh.x = fmaf(cvh.x, wsrc, oh.x);
+            if (e == 1) oh.y = fmaf(cvh.y, wsrc, oh.y);
+          }
+        }
+        vmax_out = fmaxf(vmax_out, fmaxf(fmaxf(fabsf(ol.x), fabsf(ol.y)),
+                                         fmaxf(fabsf(oh.x), fabsf(oh.y))));
+        {
+          T *out = reinterpret_cast<T *>(unext) + (size_t)j * plane_stride;
+          if (wa) __stcs(reinterpret_cast<unsigned *>(out + oa), pack_pair<T>(ol.x, ol.y));
+          if (wb) __stcs(reinterpret_cast<unsigned *>(out + ob), pack_pair<T>(oh.x, oh.y));
+        }
+        // Receivers on this plane: each thread records the entries at its
+        // own points (no staging, so no barrier across the warps).
+        if (j == rz) {
+          int e = rcur;
+          for (; e < rend; ++e) {
+            const int4 r4 = rec[e];
+            if (r4.x != j) break;
+            const int da = r4.y - la, db = r4.y - lb;
+            if (da == 0) trow[r4.z] = ol.x * so;
+            if (da == 1) trow[r4.z] = ol.y * so;
+            if (db == 0) trow[r4.z] = oh.x * so;
+            if (db == 1) trow[r4.z] = oh.y * so;
+          }
+          rcur = e;
+          rz = (rcur < rend) ? rec[rcur].x : 0x7fffffff;
+        }
+      }
+    }
+  }
+  {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1)
+      vmax_out = fmaxf(vmax_out, __shfl_xor_sync(0xffffffffu, vmax_out, o));
+    if ((tid & 31) == 0 && vmax_out > 0.f)
+      atomicMax(&d->maxbits[(ab + 1) & 3], __float_as_uint(vmax_out * so));
+  }
+  return;
+
+wait_failed:
+  {
+    // A wait gave up at stage s: record it, then drain the stages still in
+    // flight (issued: [0, s + PF)) so no TMA write lands in shared memory
+    // after this CTA has exited.
+    if (tid == 0) {
+      atomicCAS(&a.desc->error, 0, kErrTimeout);
+      const int issued = min(NS, s + C::PF);
+      for (int t = s; t < issued; ++t)
+        if (!mbar_wait_bounded(&bars[t % C::NB], (t / C::NB) & 1, kWaitLimitNs))
+          break;
+    }
+    __syncthreads();
+  }
+}
+
 // One step of one grid: CTA (blockIdx.x, .y) is a tile, blockIdx.z a z layer.
 template <class C, bool kVelocityField = false, int kMode = 0>
 __global__ void __launch_bounds__(C::THREADS, C::MINB)
@@ -698,9 +1117,15 @@ __global__ void __launch_bounds__(C::THREADS, C::MINB)
     asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
     asm volatile("griddepcontrol.wait;" ::: "memory");
   }
-  sweep_cta<C, kVelocityField, kMode>(&tm_u, &tm_up, &tm_c, a, a.k, blockIdx.x,
-                                      blockIdx.y, blockIdx.z, smem_raw, a.unext,
-                                      a.koff);
+  if constexpr (C::kTensor) {
+    static_assert(!kVelocityField && kMode == 0, "16-bit sweeps: forward only");
+    sweep_cta_tc<C>(&tm_u, &tm_up, &tm_c, a, a.k, blockIdx.x, blockIdx.y,
+                    blockIdx.z, smem_raw, a.unext, a.koff);
+  } else {
+    sweep_cta<C, kVelocityField, kMode>(&tm_u, &tm_up, &tm_c, a, a.k, blockIdx.x,
+                                        blockIdx.y, blockIdx.z, smem_raw, a.unext,
+                                        a.koff);
+  }
 }
 
 // One shot of a batch (device memory, 128-byte aligned): its tensor maps for
@@ -761,8 +1186,12 @@ __global__ void __launch_bounds__(C::THREADS, C::MINB)
     tensormap_acquire(&sh.tile[cur ^ 1]);
     tensormap_acquire(&sh.cmap);
   }
-  sweep_cta<C, false, 0>(&sh.halo[cur], &sh.tile[cur ^ 1], &sh.cmap, sh.args, co, bx,
-                         by, bz, smem_raw, sh.buf[cur ^ 1], (int)n);
+  if constexpr (C::kTensor)
+    sweep_cta_tc<C>(&sh.halo[cur], &sh.tile[cur ^ 1], &sh.cmap, sh.args, co, bx, by,
+                    bz, smem_raw, sh.buf[cur ^ 1], (int)n);
+  else
+    sweep_cta<C, false, 0>(&sh.halo[cur], &sh.tile[cur ^ 1], &sh.cmap, sh.args, co, bx,
+                           by, bz, smem_raw, sh.buf[cur ^ 1], (int)n);
 }
 
 }  // namespace gbw

@@ -25,17 +25,33 @@ using namespace gbw;
 
 namespace {
 
-// Kernel variants (tile x, tile y, rows per thread, prefetch depth, CTAs/SM,
-// storage type). Variant 0 of each storage is the default, measured fastest
-// on GB300 at 1024 x 1024 x 512 and 512^3; the others stay selectable
-// (GBWAVE_VARIANT) for tuning runs.
-//  FP32: 32 x 16 tiles, 4 CTAs of 4 warps per SM.
+// Kernel variants. Variant 0 of each storage is the default, measured
+// fastest on GB300 at 1024 x 1024 x 512 and 512^3; the others stay
+// selectable (GBWAVE_VARIANT) for tuning runs.
+//  FP32 (tile x, tile y, rows per thread, prefetch depth, CTAs/SM): 32 x 16
+//  tiles, 4 CTAs of 4 warps per SM.
 using Cfg0 = SweepCfg<32, 16, 1, 4, 4>;
 using CfgA = SweepCfg<64, 16, 1, 4, 2>;
 using Cfg2 = SweepCfg<64, 8, 1, 4, 4>;
 using Cfg3 = SweepCfg<32, 16, 1, 3, 4>;
-//  16-bit: 64-wide tiles, so a half-warp reads one contiguous 128-byte row of
-//  16-bit elements (no shared-memory bank conflicts).
+//  16-bit, x and y parts of Eq. 1 on the tensor cores (tile x, prefetch
+//  depth, CTAs/SM): 64 x 16 tiles of 8 warps, 2 per SM. FP16 / BF16 at
+//  1024 x 1024 x 512 (Gpts/s): 64 x 16 529 / 523, 32 x 16 with 4 CTAs/SM
+//  496 / 495, with 5 (96 registers) 439 / 401, 128 x 16 with 1 CTA/SM
+//  462 / 454, 64 x 16 with 3 CTAs/SM (80 registers, spills) 453 / 374.
+using CfgBT64 = TcCfg<64, 4, 2, __nv_bfloat16>;
+using CfgHT64 = TcCfg<64, 4, 2, __half>;
+using CfgBT = TcCfg<32, 4, 4, __nv_bfloat16>;
+using CfgHT = TcCfg<32, 4, 4, __half>;
+using CfgBT5 = TcCfg<32, 4, 5, __nv_bfloat16>;
+using CfgHT5 = TcCfg<32, 4, 5, __half>;
+using CfgBT128 = TcCfg<128, 4, 1, __nv_bfloat16>;
+using CfgHT128 = TcCfg<128, 4, 1, __half>;
+using CfgBT643 = TcCfg<64, 4, 3, __nv_bfloat16>;
+using CfgHT643 = TcCfg<64, 4, 3, __half>;
+//  16-bit on the CUDA cores (the stencil's pair sums as mixed-precision
+//  adds): 64-wide tiles, so a half-warp reads one contiguous 128-byte row of
+//  16-bit elements (no shared-memory bank conflicts). 478 / 487 Gpts/s.
 using CfgB0 = SweepCfg<64, 8, 1, 4, 4, __nv_bfloat16>;
 using CfgB1 = SweepCfg<32, 16, 1, 4, 4, __nv_bfloat16>;
 using CfgB2 = SweepCfg<64, 16, 2, 4, 3, __nv_bfloat16>;
@@ -48,6 +64,7 @@ struct Variant {
   int tx, ty, threads;
   size_t smem;
   int esize, halo_x;  // bytes per wavefield element; box columns left of a tile
+  int box_u, box_p;   // TMA box widths: u plane with halo, u_prev / c tiles
   void (*launch)(dim3, cudaStream_t, const CUtensorMap &, const CUtensorMap &,
                  const CUtensorMap &, const SweepArgs &);
 };
@@ -90,6 +107,8 @@ Variant make_variant() {
                  C::SMEM_BYTES,
                  (int)sizeof(typename C::T),
                  C::HX,
+                 C::BOX_U,
+                 C::BOX_P,
                  &launch_sweep<C>};
 }
 
@@ -98,14 +117,24 @@ Variant pick_variant(int storage, int which) {
     switch (which) {
       case 1: return make_variant<CfgB1>();
       case 2: return make_variant<CfgB2>();
-      default: return make_variant<CfgB0>();
+      case 3: return make_variant<CfgBT>();
+      case 4: return make_variant<CfgBT5>();
+      case 5: return make_variant<CfgB0>();
+      case 6: return make_variant<CfgBT128>();
+      case 7: return make_variant<CfgBT643>();
+      default: return make_variant<CfgBT64>();
     }
   }
   if (storage == WAVE_STORAGE_F16) {
     switch (which) {
       case 1: return make_variant<CfgH1>();
       case 2: return make_variant<CfgH2>();
-      default: return make_variant<CfgH0>();
+      case 3: return make_variant<CfgHT>();
+      case 4: return make_variant<CfgHT5>();
+      case 5: return make_variant<CfgH0>();
+      case 6: return make_variant<CfgHT128>();
+      case 7: return make_variant<CfgHT643>();
+      default: return make_variant<CfgHT64>();
     }
   }
   switch (which) {
@@ -199,18 +228,18 @@ int make_map(CUtensorMap *m, const void *base, const wave_ctx *c, int box_x,
 }
 
 int build_maps(wave_ctx *c) {
-  const int tx = c->var.tx, ty = c->var.ty, hx = c->var.halo_x;
+  const int ty = c->var.ty;
   const CUtensorMapDataType dt = field_dtype(c->storage);
   for (int b = 0; b < 2; ++b) {
-    int st = make_map(&c->tm_halo[b], c->buf[b], c, tx + 2 * hx, ty + 2 * kR,
+    int st = make_map(&c->tm_halo[b], c->buf[b], c, c->var.box_u, ty + 2 * kR,
                       dt, c->pxu, c->var.esize);
     if (st) return st;
-    st = make_map(&c->tm_tile[b], c->buf[b], c, tx, ty, dt, c->pxu,
+    st = make_map(&c->tm_tile[b], c->buf[b], c, c->var.box_p, ty, dt, c->pxu,
                   c->var.esize);
     if (st) return st;
   }
-  return make_map(&c->tm_c, c->c, c, tx, ty, CU_TENSOR_MAP_DATA_TYPE_FLOAT32,
-                  c->px, 4);
+  return make_map(&c->tm_c, c->c, c, c->var.box_p, ty,
+                  CU_TENSOR_MAP_DATA_TYPE_FLOAT32, c->px, 4);
 }
 
 void set_coeffs(wave_ctx *c) {
@@ -221,14 +250,7 @@ void set_coeffs(wave_ctx *c) {
   a.px = c->pxu;
   a.ntx = (int)c->grid.x;
   a.cmax = (float)(c->vmax * c->vmax * c->dt * c->dt);
-  const double ix = 1.0 / (c->dx * c->dx), iy = 1.0 / (c->dy * c->dy),
-               iz = 1.0 / (c->dz * c->dz);
-  a.k.c0 = (float)(kW[0] * (ix + iy + iz));
-  for (int m = 1; m <= 4; ++m) {
-    a.k.cx[m - 1] = (float)(kW[m] * ix);
-    a.k.cy[m - 1] = (float)(kW[m] * iy);
-    a.k.cz[m - 1] = (float)(kW[m] * iz);
-  }
+  a.k = make_coefs(c->dx, c->dy, c->dz);
   a.desc = c->d_desc;
 }
 
@@ -530,9 +552,10 @@ static int setup_launch(wave_ctx *c) {
   const int nty = (c->ny + c->var.ty - 1) / c->var.ty;
   c->ntiles = ntx * nty;
   int layers[kMaxLayers];
+  double preroll = c->storage == WAVE_STORAGE_F32 ? 4.0 : 8.0;
+  if (const char *pr = std::getenv("GBWAVE_PREROLL")) preroll = std::atof(pr);
   const int nl = plan_layers(c->nz, (long long)c->ntiles,
-                             (long long)c->sms * c->ctas_per_sm,
-                             c->storage == WAVE_STORAGE_F32 ? 4.0 : 8.0, layers);
+                             (long long)c->sms * c->ctas_per_sm, preroll, layers);
   c->zchunk = *std::max_element(layers, layers + nl);
   c->grid = dim3(ntx, nty, (unsigned)nl);
   if (c->grid.y > 65535) return WAVE_EINVAL;
@@ -1197,10 +1220,22 @@ int wave_selftest_wait(int64_t limit_ns, void *stream) {
 namespace {
 
 template <int kMode>
-void launch_mode(const wave_ctx *c, const CUtensorMap &tu,
+void launch_mode(const wave_ctx *c, dim3 grid, const CUtensorMap &tu,
                  const CUtensorMap &tup, const SweepArgs &a) {
-  launch_pdl(wave_sweep_kernel<Cfg0, false, kMode>, c->grid, Cfg0::THREADS,
+  launch_pdl(wave_sweep_kernel<Cfg0, false, kMode>, grid, Cfg0::THREADS,
              Cfg0::SMEM_BYTES, c->stream, tu, tup, c->tm_c, a);
+}
+
+// z-layer plan of a gradient sweep mode: the u-only stages that refill the
+// register queue weigh less against a stage that also moves D and the
+// gradient partial, so those sweeps plan with a smaller preroll (more,
+// shorter layers fill the CTA places better).
+dim3 plan_mode(const wave_ctx *c, double preroll, SweepArgs &a) {
+  int layers[kMaxLayers];
+  const int nl = plan_layers(c->nz, (long long)c->ntiles,
+                             (long long)c->sms * c->ctas_per_sm, preroll, layers);
+  set_layers(a, layers, nl);
+  return dim3(c->grid.x, c->grid.y, (unsigned)nl);
 }
 
 // r = traces - observed; misfit += 1/2 sum r^2 in FP64.
@@ -1398,9 +1433,20 @@ int gradient_impl(wave_ctx *c, const wave_shot *shot, int N,
   // p^{k+2}; with kModeGradAcc it adds p^{k+1} D^k to the double-float
   // partial, which is folded into the FP64 sum after every step k that is
   // a multiple of kGradFold (the last fold is after k = 0).
+  // Layer plans of the recompute (D stored) and adjoint sweeps. Preroll
+  // weights timed on 256^3 x 800 steps, checkpoint every 40 (wave_gradient,
+  // best of 4): 4/4 (the forward plan) 0.1864 s, 2/2 0.1827 s, 3.2/1.8
+  // 0.1866, 2/1 0.1909, 1/1 0.1907, 4/1 0.1949 (bitwise equal gradients:
+  // the plan only regroups the planes). GBWAVE_GRAD_PREROLL=d,a overrides.
+  double pre_d = 2.0, pre_a = 2.0;
+  if (const char *gp = std::getenv("GBWAVE_GRAD_PREROLL"))
+    std::sscanf(gp, "%lf,%lf", &pre_d, &pre_a);
+  SweepArgs args_d = c->args, args_a = c->args;
+  const dim3 grid_d = plan_mode(c, pre_d, args_d);
+  const dim3 grid_a = plan_mode(c, pre_a, args_a);
   int ca = 0;
   auto adjoint_step = [&](int k, const float *dsrc) {
-    SweepArgs a = c->args;
+    SweepArgs a = args_a;
     a.desc = dadj;
     a.koff = N - k;
     a.unext = padj[ca ^ 1];
@@ -1408,9 +1454,9 @@ int gradient_impl(wave_ctx *c, const wave_shot *shot, int N,
     a.ghi = ghi;
     a.glo = glo;
     if (dsrc)
-      launch_mode<kModeInject | kModeGradAcc>(c, ahalo[ca], atile[ca ^ 1], a);
+      launch_mode<kModeInject | kModeGradAcc>(c, grid_a, ahalo[ca], atile[ca ^ 1], a);
     else
-      launch_mode<kModeInject>(c, ahalo[ca], atile[ca ^ 1], a);
+      launch_mode<kModeInject>(c, grid_a, ahalo[ca], atile[ca ^ 1], a);
     if (dsrc && k % kGradFold == 0)
       grad_fold_kernel<<<c->sms * 4, 256, 0, st>>>(gacc, ghi, glo, (long long)fe);
     ca ^= 1;
@@ -1426,12 +1472,12 @@ int gradient_impl(wave_ctx *c, const wave_shot *shot, int N,
                                   fb, cudaMemcpyDeviceToDevice, st));
     int cur = 0;
     for (int n = s0; n < s1; ++n) {
-      SweepArgs a = c->args;
+      SweepArgs a = args_d;
       a.desc = dfwd;
       a.koff = n;
       a.unext = c->buf[cur ^ 1];
       a.dout = dbuf + (size_t)(n - s0) * fe;
-      launch_mode<kModeStoreD>(c, c->tm_halo[cur], c->tm_tile[cur ^ 1], a);
+      launch_mode<kModeStoreD>(c, grid_d, c->tm_halo[cur], c->tm_tile[cur ^ 1], a);
       cur ^= 1;
     }
     for (int k = s1 - 1; k >= s0; --k)
@@ -1707,14 +1753,7 @@ extern "C" int wave_propagate_noalloc(const wave_grid *g, const wave_spacing *h,
   a.nz = nz;
   a.px = nx;
   a.ntx = ntx;
-  const double ix = 1.0 / (h->dx * h->dx), iy = 1.0 / (h->dy * h->dy),
-               iz = 1.0 / (h->dz * h->dz);
-  a.k.c0 = (float)(kW[0] * (ix + iy + iz));
-  for (int m = 1; m <= 4; ++m) {
-    a.k.cx[m - 1] = (float)(kW[m] * ix);
-    a.k.cy[m - 1] = (float)(kW[m] * iy);
-    a.k.cz[m - 1] = (float)(kW[m] * iz);
-  }
+  a.k = make_coefs(h->dx, h->dy, h->dz);
   a.desc = reinterpret_cast<StepDesc *>(scr);
   a.dt2 = (float)(dt * dt);
   for (int k = 0; k < nsteps; ++k) {
