@@ -550,9 +550,10 @@ def main():
     clocks = sampler.summary(tw0, tw1)
     value = replica_value(npts, K, ms * 1e-3, world)
     # graph chunks of GRAPH_STEPS sweeps + a step-counter node, the remainder
-    # as direct sweeps + one counter kernel, and the final check of the traces
+    # as direct sweeps + one counter kernel, the receiver table's four build
+    # kernels and the final check of the traces
     launches = (K // GRAPH_STEPS) * (GRAPH_STEPS + 1) + \
-        ((K % GRAPH_STEPS) + 1 if K % GRAPH_STEPS else 0) + (1 if nrec else 0)
+        ((K % GRAPH_STEPS) + 1 if K % GRAPH_STEPS else 0) + (5 if nrec else 0)
     tr_ok = bool(torch.isfinite(traces_d[:K]).all().item())
     solver.close()
     del traces_d
