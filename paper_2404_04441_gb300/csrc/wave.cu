@@ -37,18 +37,15 @@ using Cfg3 = SweepCfg<32, 16, 1, 3, 4>;
 //  16-bit, x and y parts of Eq. 1 on the tensor cores (tile x, prefetch
 //  depth, CTAs/SM): 64 x 16 tiles of 8 warps, 2 per SM. FP16 / BF16 at
 //  1024 x 1024 x 512 (Gpts/s): 64 x 16 529 / 523, 32 x 16 with 4 CTAs/SM
-//  496 / 495, with 5 (96 registers) 439 / 401, 128 x 16 with 1 CTA/SM
-//  462 / 454, 64 x 16 with 3 CTAs/SM (80 registers, spills) 453 / 374.
+//  496 / 495, 128 x 16 with 1 CTA/SM 462 / 454. Forcing more CTAs per SM
+//  spilled registers and was slower (32 x 16 with 5: 439 / 401; 64 x 16
+//  with 3: 453 / 374), so those forms are not built.
 using CfgBT64 = TcCfg<64, 4, 2, __nv_bfloat16>;
 using CfgHT64 = TcCfg<64, 4, 2, __half>;
 using CfgBT = TcCfg<32, 4, 4, __nv_bfloat16>;
 using CfgHT = TcCfg<32, 4, 4, __half>;
-using CfgBT5 = TcCfg<32, 4, 5, __nv_bfloat16>;
-using CfgHT5 = TcCfg<32, 4, 5, __half>;
 using CfgBT128 = TcCfg<128, 4, 1, __nv_bfloat16>;
 using CfgHT128 = TcCfg<128, 4, 1, __half>;
-using CfgBT643 = TcCfg<64, 4, 3, __nv_bfloat16>;
-using CfgHT643 = TcCfg<64, 4, 3, __half>;
 //  16-bit on the CUDA cores (the stencil's pair sums as mixed-precision
 //  adds): 64-wide tiles, so a half-warp reads one contiguous 128-byte row of
 //  16-bit elements (no shared-memory bank conflicts). 478 / 487 Gpts/s.
@@ -118,10 +115,8 @@ Variant pick_variant(int storage, int which) {
       case 1: return make_variant<CfgB1>();
       case 2: return make_variant<CfgB2>();
       case 3: return make_variant<CfgBT>();
-      case 4: return make_variant<CfgBT5>();
       case 5: return make_variant<CfgB0>();
       case 6: return make_variant<CfgBT128>();
-      case 7: return make_variant<CfgBT643>();
       default: return make_variant<CfgBT64>();
     }
   }
@@ -130,10 +125,8 @@ Variant pick_variant(int storage, int which) {
       case 1: return make_variant<CfgH1>();
       case 2: return make_variant<CfgH2>();
       case 3: return make_variant<CfgHT>();
-      case 4: return make_variant<CfgHT5>();
       case 5: return make_variant<CfgH0>();
       case 6: return make_variant<CfgHT128>();
-      case 7: return make_variant<CfgHT643>();
       default: return make_variant<CfgHT64>();
     }
   }
