@@ -56,6 +56,12 @@ def _load():
             + [ctypes.c_int] * 3 + [ctypes.c_double] * 3
             + [ctypes.c_void_p, ctypes.c_int, ctypes.c_void_p, ctypes.c_void_p])
         lib.oracle_gradient.restype = ctypes.c_int
+        lib.oracle_gradient_cpml.argtypes = (
+            [ctypes.c_int] * 3 + [ctypes.c_double] * 4 + [ctypes.c_void_p, ctypes.c_int]
+            + [ctypes.c_int] + [ctypes.c_double] * 3
+            + [ctypes.c_int] * 3 + [ctypes.c_double] * 3
+            + [ctypes.c_void_p, ctypes.c_int, ctypes.c_void_p, ctypes.c_void_p])
+        lib.oracle_gradient_cpml.restype = ctypes.c_int
         lib.oracle_first_weights.argtypes = [dp]
         lib.oracle_first_weights.restype = None
         lib.oracle_cpml_profile.argtypes = [ctypes.c_int, ctypes.c_int] + [ctypes.c_double] * 5 + [
@@ -168,6 +174,29 @@ def gradient(vel, spacing, dt, nsteps, source, receivers, resid):
                                  g.ctypes.data)
     if rc != 0:
         raise ValueError("oracle_gradient rejected its input (rc=%d)" % rc)
+    return g
+
+
+def gradient_cpml(vel, spacing, dt, nsteps, npml, source, receivers, resid, R=1e-3,
+                  fcps=15.0, vmax=None):
+    """Discrete adjoint gradient dJ/d(v^2) of a CPML run from rest (the layer's
+    profile held fixed at vmax, default the model's largest velocity), given
+    resid[n, r] = dJ/d traces[n, r]. Returns (nz, ny, nx) FP64."""
+    vel = _f64(vel)
+    nz, ny, nx = vel.shape
+    rec = np.ascontiguousarray(receivers, dtype=np.int32).reshape(-1, 3)
+    res = _f64(resid).reshape(nsteps, rec.shape[0])
+    sx, sy, sz, f, t0, amp = source
+    if t0 is None or t0 < 0:
+        t0 = 1.0 / f
+    vm = float(vel.max()) if vmax is None else float(vmax)
+    g = np.zeros_like(vel)
+    rc = _load().oracle_gradient_cpml(
+        nx, ny, nz, *map(float, spacing), float(dt), vel.ctypes.data, int(nsteps), int(npml),
+        float(R), float(fcps), vm, int(sx), int(sy), int(sz), float(f), float(t0), float(amp),
+        rec.ctypes.data, rec.shape[0], res.ctypes.data, g.ctypes.data)
+    if rc != 0:
+        raise ValueError("oracle_gradient_cpml rejected its input (rc=%d)" % rc)
     return g
 
 

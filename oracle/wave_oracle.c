@@ -456,3 +456,165 @@ int oracle_propagate_cpml(int nx, int ny, int nz, double dx, double dy,
   for (int ax = 0; ax < 3; ax++) { free(b[ax]); free(a[ax]); }
   return 0;
 }
+
+/*
+ * Discrete adjoint gradient dJ/dm (m = v^2) of oracle_propagate_cpml from
+ * rest, the layer held fixed (its profile uses the given vmax, not the
+ * model, so b and a do not depend on m).
+ *
+ * Forward, step n = 0 .. N-1 (psi^-1 = zeta^-1 = 0, u^0 = u^-1 = 0):
+ *     psi_a^n  = B_a psi_a^{n-1}  + A_a D1_a u^n
+ *     zeta_a^n = B_a zeta_a^{n-1} + A_a (D2_a u^n + D1_a psi_a^n)
+ *     u^{n+1}  = 2u^n - u^{n-1} + C sum_a (D2_a u^n + D1_a psi_a^n + zeta_a^n)
+ *                + C s_n e_src,     d^n = R u^{n+1},   C = m dt^2
+ * (B_a, A_a the diagonal per-axis b and a). With multipliers q^{n+1} for the
+ * u equation, mu_a^n for psi and nu_a^n for zeta, setting the derivative of
+ * the Lagrangian J - sum (multiplier . residual) with respect to every state
+ * to zero gives, for k = N .. 1 (q^{N+1} = q^{N+2} = 0, mu^N = nu^N = 0):
+ *     nu_a^k = C q^{k+1} + B_a nu_a^{k+1}
+ *     mu_a^k = D1_a^T (C q^{k+1} + A_a nu_a^k) + B_a mu_a^{k+1}
+ *     q^k    = 2q^{k+1} - q^{k+2}
+ *              + sum_a [D2_a^T (C q^{k+1} + A_a nu_a^k) + D1_a^T A_a mu_a^k]
+ *              + R^T r^{k-1},        r^n = dJ/dd^n,
+ * and dJ/dm = (1/m) sum_n q^{n+1} (u^{n+1} - 2u^n + u^{n-1}) as without the
+ * layer. With the zero halo D2_a is symmetric and D1_a antisymmetric, so
+ * D2_a^T = D2_a and D1_a^T = -D1_a. Every forward field is kept.
+ */
+int oracle_gradient_cpml(int nx, int ny, int nz, double dx, double dy,
+                         double dz, double dt, const double *vel, int nsteps,
+                         int npml, double R, double fcps, double vmax, int sx,
+                         int sy, int sz, double f, double t0, double amp,
+                         const int32_t *rec, int nrec, const double *resid,
+                         double *grad) {
+  if (nx < 1 || ny < 1 || nz < 1 || nsteps < 1 || nrec < 0 || npml < 0 ||
+      !(R > 0.0 && R <= 1.0))
+    return -1;
+  if (sx < 0 || sx >= nx || sy < 0 || sy >= ny || sz < 0 || sz >= nz) return -1;
+  for (int r = 0; r < nrec; r++)
+    if (rec[3 * r] < 0 || rec[3 * r] >= nx || rec[3 * r + 1] < 0 ||
+        rec[3 * r + 1] >= ny || rec[3 * r + 2] < 0 || rec[3 * r + 2] >= nz)
+      return -1;
+  const size_t n = (size_t)nx * ny * nz;
+  const int dims[3] = {nx, ny, nz};
+  const double hs[3] = {dx, dy, dz};
+  /* u[k] holds u^{k-1}, k = 0..nsteps+1 */
+  double *u = (double *)calloc(n * (size_t)(nsteps + 2), sizeof(double));
+  double *c = (double *)malloc(n * sizeof(double));
+  double *psi = (double *)calloc(3 * n, sizeof(double));
+  double *zeta = (double *)calloc(3 * n, sizeof(double));
+  double *mu = (double *)calloc(3 * n, sizeof(double));
+  double *nu = (double *)calloc(3 * n, sizeof(double));
+  double *q0 = (double *)calloc(n, sizeof(double)); /* q^{k+2} */
+  double *q1 = (double *)calloc(n, sizeof(double)); /* q^{k+1} */
+  double *q2 = (double *)calloc(n, sizeof(double)); /* q^k */
+  double *g = (double *)malloc(3 * n * sizeof(double)); /* C q + A nu, per axis */
+  double *am = (double *)malloc(3 * n * sizeof(double)); /* A mu, per axis */
+  double *b[3], *a[3];
+  int ok = u && c && psi && zeta && mu && nu && q0 && q1 && q2 && g && am;
+  for (int ax = 0; ax < 3; ax++) {
+    b[ax] = (double *)malloc(dims[ax] * sizeof(double));
+    a[ax] = (double *)malloc(dims[ax] * sizeof(double));
+    ok = ok && b[ax] && a[ax];
+  }
+  if (ok) {
+    for (int ax = 0; ax < 3; ax++)
+      oracle_cpml_profile(dims[ax], npml, hs[ax], dt, vmax, R, fcps, b[ax], a[ax]);
+    for (size_t p = 0; p < n; p++) c[p] = vel[p] * vel[p] * dt * dt;
+    /* forward, keeping every u */
+    for (int s = 0; s < nsteps; s++) {
+      const double *um = u + (size_t)s * n, *uc = u + (size_t)(s + 1) * n;
+      double *un = u + (size_t)(s + 2) * n;
+#pragma omp parallel for schedule(static)
+      for (int k = 0; k < nz; k++)
+        for (int j = 0; j < ny; j++)
+          for (int i = 0; i < nx; i++) {
+            const size_t p = ((size_t)k * ny + j) * nx + i;
+            const int idx[3] = {i, j, k};
+            for (int ax = 0; ax < 3; ax++)
+              psi[ax * n + p] = b[ax][idx[ax]] * psi[ax * n + p] +
+                                a[ax][idx[ax]] * oracle_d1(uc, nx, ny, nz, i, j, k, ax, hs[ax]);
+          }
+#pragma omp parallel for schedule(static)
+      for (int k = 0; k < nz; k++)
+        for (int j = 0; j < ny; j++)
+          for (int i = 0; i < nx; i++) {
+            const size_t p = ((size_t)k * ny + j) * nx + i;
+            const int idx[3] = {i, j, k};
+            double sum = 0.0;
+            for (int ax = 0; ax < 3; ax++) {
+              const double d2 = oracle_d2(uc, nx, ny, nz, i, j, k, ax, hs[ax]);
+              const double d1p = oracle_d1(psi + ax * n, nx, ny, nz, i, j, k, ax, hs[ax]);
+              zeta[ax * n + p] = b[ax][idx[ax]] * zeta[ax * n + p] +
+                                 a[ax][idx[ax]] * (d2 + d1p);
+              sum += d2 + d1p + zeta[ax * n + p];
+            }
+            un[p] = 2.0 * uc[p] - um[p] + c[p] * sum;
+          }
+      const size_t ps = ((size_t)sz * ny + sy) * nx + sx;
+      un[ps] += c[ps] * oracle_ricker(s * dt, f, t0, amp);
+    }
+    for (size_t p = 0; p < n; p++) grad[p] = 0.0;
+    /* adjoint, k = N .. 1 */
+    for (int kk = nsteps; kk >= 1; kk--) {
+      const int last = kk == nsteps; /* mu^N = nu^N = 0 */
+#pragma omp parallel for schedule(static)
+      for (int k = 0; k < nz; k++)
+        for (int j = 0; j < ny; j++)
+          for (int i = 0; i < nx; i++) {
+            const size_t p = ((size_t)k * ny + j) * nx + i;
+            const int idx[3] = {i, j, k};
+            const double cq = c[p] * q1[p];
+            for (int ax = 0; ax < 3; ax++) {
+              if (!last) nu[ax * n + p] = cq + b[ax][idx[ax]] * nu[ax * n + p];
+              g[ax * n + p] = cq + a[ax][idx[ax]] * nu[ax * n + p];
+            }
+          }
+      if (!last) {
+#pragma omp parallel for schedule(static)
+        for (int k = 0; k < nz; k++)
+          for (int j = 0; j < ny; j++)
+            for (int i = 0; i < nx; i++) {
+              const size_t p = ((size_t)k * ny + j) * nx + i;
+              const int idx[3] = {i, j, k};
+              for (int ax = 0; ax < 3; ax++)
+                mu[ax * n + p] = -oracle_d1(g + ax * n, nx, ny, nz, i, j, k, ax, hs[ax]) +
+                                 b[ax][idx[ax]] * mu[ax * n + p];
+            }
+      }
+#pragma omp parallel for schedule(static)
+      for (int k = 0; k < nz; k++)
+        for (int j = 0; j < ny; j++)
+          for (int i = 0; i < nx; i++) {
+            const size_t p = ((size_t)k * ny + j) * nx + i;
+            const int idx[3] = {i, j, k};
+            for (int ax = 0; ax < 3; ax++)
+              am[ax * n + p] = a[ax][idx[ax]] * mu[ax * n + p];
+          }
+#pragma omp parallel for schedule(static)
+      for (int k = 0; k < nz; k++)
+        for (int j = 0; j < ny; j++)
+          for (int i = 0; i < nx; i++) {
+            const size_t p = ((size_t)k * ny + j) * nx + i;
+            double sum = 0.0;
+            for (int ax = 0; ax < 3; ax++)
+              sum += oracle_d2(g + ax * n, nx, ny, nz, i, j, k, ax, hs[ax]) -
+                     oracle_d1(am + ax * n, nx, ny, nz, i, j, k, ax, hs[ax]);
+            q2[p] = 2.0 * q1[p] - q0[p] + sum;
+          }
+      for (int r = 0; r < nrec; r++) {
+        const size_t pr = ((size_t)rec[3 * r + 2] * ny + rec[3 * r + 1]) * nx + rec[3 * r];
+        q2[pr] += resid[(size_t)(kk - 1) * nrec + r];
+      }
+      /* term n = kk - 1: q^kk (u^kk - 2 u^{kk-1} + u^{kk-2}) */
+      const double *ua = u + (size_t)(kk + 1) * n, *ub = u + (size_t)kk * n,
+                   *ud = u + (size_t)(kk - 1) * n;
+      for (size_t p = 0; p < n; p++) grad[p] += q2[p] * (ua[p] - 2.0 * ub[p] + ud[p]);
+      double *t = q0; q0 = q1; q1 = q2; q2 = t;
+    }
+    for (size_t p = 0; p < n; p++) grad[p] /= vel[p] * vel[p];
+  }
+  free(u); free(c); free(psi); free(zeta); free(mu); free(nu);
+  free(q0); free(q1); free(q2); free(g); free(am);
+  for (int ax = 0; ax < 3; ax++) { free(b[ax]); free(a[ax]); }
+  return ok ? 0 : -1;
+}

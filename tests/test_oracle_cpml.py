@@ -301,3 +301,68 @@ def test_recursive_convolution_is_exact_for_a_step(oracle_mod):
             psi = b[i] * psi + a[i] * 1.0
             exact = -d / (d + al) * (1.0 - math.exp(-(d + al) * (n + 1) * dt))
             assert psi == pytest.approx(exact, rel=1e-12, abs=1e-15), (i, n)
+
+
+def _cpml_gradient_case():
+    rng = np.random.default_rng(17)
+    nz, ny, nx = 13, 12, 14
+    sp = (10.0, 11.0, 9.0)
+    true = 2000.0 + 400.0 * rng.random((nz, ny, nx))
+    vel = 2000.0 + 400.0 * rng.random((nz, ny, nx))
+    shot = (7, 6, 6, 25.0, 0.02, 1e3)
+    rec = np.array([[1, 1, 1], [4, 6, 2], [12, 3, 10], [7, 10, 12], [0, 11, 6]],
+                   dtype=np.int32)
+    return sp, vel, true, shot, rec
+
+
+def _cpml_misfit(oracle_mod, vel, sp, dt, nsteps, npml, vmax, shot, rec, obs):
+    tr = oracle_mod.propagate_cpml(vel, sp, dt, nsteps, npml, R=1e-2, fcps=20.0, vmax=vmax,
+                                   source=shot, receivers=rec)[4]
+    return 0.5 * float(np.sum((tr - obs) ** 2)), tr
+
+
+def test_cpml_adjoint_gradient_matches_finite_differences(oracle_mod):
+    """The CPML adjoint gradient against central differences of the oracle's
+    CPML misfit, the layer's profile held at a fixed vmax (FP64, step 1e-5
+    relative), at points inside and outside the layer and along a smooth
+    direction through the whole model."""
+    sp, vel, true, shot, rec = _cpml_gradient_case()
+    vmax = 2500.0
+    dt = 0.5 * oracle_mod.cfl_dt(sp, vmax)
+    nsteps, npml = 28, 3
+    obs = oracle_mod.propagate_cpml(true, sp, dt, nsteps, npml, R=1e-2, fcps=20.0, vmax=vmax,
+                                    source=shot, receivers=rec)[4]
+    _, tr = _cpml_misfit(oracle_mod, vel, sp, dt, nsteps, npml, vmax, shot, rec, obs)
+    g = oracle_mod.gradient_cpml(vel, sp, dt, nsteps, npml, shot, rec, tr - obs, R=1e-2,
+                                 fcps=20.0, vmax=vmax)
+    m = vel ** 2
+    # in the layer (corner, face, edge), at its inner edge, and inside
+    for idx in [(0, 0, 0), (1, 6, 7), (6, 1, 12), (3, 3, 3), (6, 6, 7), (9, 8, 4), (12, 11, 13)]:
+        h = 1e-5 * m[idx]
+        mp, mm = m.copy(), m.copy()
+        mp[idx] += h
+        mm[idx] -= h
+        jp, _ = _cpml_misfit(oracle_mod, np.sqrt(mp), sp, dt, nsteps, npml, vmax, shot, rec, obs)
+        jm, _ = _cpml_misfit(oracle_mod, np.sqrt(mm), sp, dt, nsteps, npml, vmax, shot, rec, obs)
+        fd = (jp - jm) / (2 * h)
+        assert fd == pytest.approx(g[idx], rel=2e-5, abs=1e-6 * np.max(np.abs(g))), idx
+    z, y, x = np.meshgrid(*[np.arange(s) for s in m.shape], indexing="ij")
+    dm = np.exp(-((x - 3.0) ** 2 + (y - 6.0) ** 2 + (z - 5.0) ** 2) / 10.0) * m
+    eps = 1e-6
+    jp, _ = _cpml_misfit(oracle_mod, np.sqrt(m + eps * dm), sp, dt, nsteps, npml, vmax, shot,
+                         rec, obs)
+    jm, _ = _cpml_misfit(oracle_mod, np.sqrt(m - eps * dm), sp, dt, nsteps, npml, vmax, shot,
+                         rec, obs)
+    assert (jp - jm) / (2 * eps) == pytest.approx(float(np.sum(g * dm)), rel=1e-6)
+
+
+def test_cpml_adjoint_without_damping_is_the_plain_adjoint(oracle_mod):
+    """With R = 1 the layer does not damp (b = 1, a = 0): the CPML adjoint
+    must equal the plain one (to FP64 rounding of a different order)."""
+    sp, vel, _, shot, rec = _cpml_gradient_case()
+    dt = 0.5 * oracle_mod.cfl_dt(sp, vel.max())
+    rng = np.random.default_rng(3)
+    res = rng.standard_normal((20, rec.shape[0]))
+    g0 = oracle_mod.gradient(vel, sp, dt, 20, shot, rec, res)
+    g1 = oracle_mod.gradient_cpml(vel, sp, dt, 20, 4, shot, rec, res, R=1.0, fcps=0.0)
+    assert np.max(np.abs(g1 - g0)) <= 1e-12 * np.max(np.abs(g0))

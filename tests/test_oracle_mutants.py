@@ -82,6 +82,17 @@ MUTANTS = {
     "CPML psi term with the wrong sign": (
         "sum += d2 + d1p + zeta[ax * n + p];", "sum += d2 - d1p + zeta[ax * n + p];",
         [cpml_pins.test_dense_state_space_brute_force]),
+    "CPML adjoint with D1 in place of its transpose": (
+        "mu[ax * n + p] = -oracle_d1(g + ax * n,", "mu[ax * n + p] = oracle_d1(g + ax * n,",
+        [cpml_pins.test_cpml_adjoint_gradient_matches_finite_differences]),
+    "CPML adjoint zeta multiplier without its decay": (
+        "if (!last) nu[ax * n + p] = cq + b[ax][idx[ax]] * nu[ax * n + p];",
+        "if (!last) nu[ax * n + p] = cq;",
+        [cpml_pins.test_cpml_adjoint_gradient_matches_finite_differences]),
+    "CPML adjoint psi multiplier term with the wrong sign": (
+        "oracle_d1(am + ax * n, nx, ny, nz, i, j, k, ax, hs[ax]);\n            q2[p]",
+        "-oracle_d1(am + ax * n, nx, ny, nz, i, j, k, ax, hs[ax]);\n            q2[p]",
+        [cpml_pins.test_cpml_adjoint_gradient_matches_finite_differences]),
     "CPML psi from the previous field": (
         "oracle_d1(u, nx, ny, nz, i, j, k, ax, hs[ax]);",
         "oracle_d1(u_prev, nx, ny, nz, i, j, k, ax, hs[ax]);",
