@@ -324,13 +324,14 @@ def serve_saturated(gw, torch, n_requests=48):
     return out
 
 
-def gradient_workload(gw, torch, cfg=wl.CFG_GRAD):
+def gradient_workload(gw, torch, cfg=wl.CFG_GRAD, npml=0):
     """L2 trace misfit gradient d/d(v^2): true model = layers + Gaussian
     300 m/s anomaly, start = smoothed truth, 256^3, 800 steps, checkpoint
     every 40 steps. Observed traces come from a forward run of the true model
     (not timed); the timed region is one wave_gradient call (forward with
     checkpoints, residual and FP64 misfit, segment recomputes, adjoint,
-    FP64 time sums)."""
+    FP64 time sums). npml > 0: the same with the CPML layer at all faces
+    (R = 1e-3, f_cps = f_peak) in both runs."""
     nx, ny, nz = cfg["shape"]
     true = wl.anomaly_model(nx, ny, nz, seed=cfg["seed"], anomaly=cfg["anomaly_mps"])
     start = wl.smoothed_start(true)
@@ -340,9 +341,13 @@ def gradient_workload(gw, torch, cfg=wl.CFG_GRAD):
     dt = 0.5 * gw.wave_cfl_dt(cfg["spacing"], max(float(true.max()), float(start.max())))
     obs = torch.zeros((n, rec.shape[0]), device="cuda")
     st = gw.WaveSolver((nx, ny, nz), cfg["spacing"], dt, torch.from_numpy(true).cuda())
+    if npml:
+        st.set_cpml(npml, 1e-3, cfg["f_peak"])
     st.propagate(shot, n, rec, obs)
     st.close()
     s = gw.WaveSolver((nx, ny, nz), cfg["spacing"], dt, torch.from_numpy(start).cuda())
+    if npml:
+        s.set_cpml(npml, 1e-3, cfg["f_peak"])
     g = torch.empty((nz, ny, nx), device="cuda")
     # forward alone, for the cost ratio
     tr = torch.empty_like(obs)
@@ -357,13 +362,32 @@ def gradient_workload(gw, torch, cfg=wl.CFG_GRAD):
     t_grad = time.perf_counter() - t0
     s.close()
     pts = nx * ny * nz * n
-    return {"workload": "%s, %d steps, checkpoint every %d" % (cfg["name"], n, cfg["ckpt_every"]),
+    name = "%s, %d steps, checkpoint every %d" % (cfg["name"], n, cfg["ckpt_every"])
+    if npml:
+        name += ", CPML layer of %d cells" % npml
+    return {"workload": name,
             "seconds": t_grad, "forward_seconds": t_fwd, "cost_vs_forward": t_grad / t_fwd,
             "gpts_model_steps": pts / t_grad / 1e9, "misfit": misfit,
             "grad_finite": bool(torch.isfinite(g).all().item()),
             "grad_max_abs": float(g.abs().max().item()),
             "device_memory_fields": 2 * ((n + cfg["ckpt_every"] - 1) // cfg["ckpt_every"])
             + cfg["ckpt_every"] + 3}
+
+
+def cpml_gradient_bytes_per_step(shape, npml):
+    """Algorithmic DRAM bytes per model step of the gradient with the CPML
+    layer: the plain gradient's 72 B per point, plus per axis and per line
+    along it: the forward's layer pass (cpml_bytes_per_step's line term), the
+    recompute's, which also reads and writes D at the 2 w segment points
+    (+8 B), and the adjoint's: p^{k+1} and C read and p^k read and written at
+    the segment points (16 B), nu and mu read and written at the slab cells
+    (16 B)."""
+    nx, ny, nz = shape
+    npts = nx * ny * nz
+    w = npml + 4
+    lines = npts / nx + npts / ny + npts / nz
+    fwd = 16 * (2 * w + 2 * npml)
+    return 72 * npts + (2 * fwd + 8 * 2 * w + 16 * (2 * w + 2 * npml)) * lines
 
 
 def cpml_bytes_per_step(shape, npml):
@@ -661,6 +685,20 @@ def main():
         gradient["roofline"] = {"bound": "hbm", "achieved": ach, "peak": peaks["hbm_gbs"],
                                 "unit": "GB/s", "frac": ach / peaks["hbm_gbs"],
                                 "algorithmic_bytes_per_model_point_step": 72}
+        if not args.no_cpml:
+            npml = 16
+            gl = gradient_workload(gw, torch, npml=npml)
+            b = cpml_gradient_bytes_per_step(wl.CFG_GRAD["shape"], npml)
+            gsteps = wl.CFG_GRAD["nsteps"] / gl["seconds"]
+            ach = b * gsteps / 1e9
+            gradient["cpml_npml%d" % npml] = {
+                "workload": gl["workload"], "seconds": gl["seconds"],
+                "vs_plain_gradient": gl["seconds"] / gradient["seconds"],
+                "cost_vs_forward": gl["cost_vs_forward"], "misfit": gl["misfit"],
+                "grad_finite": gl["grad_finite"],
+                "roofline": {"bound": "hbm", "achieved": ach, "peak": peaks["hbm_gbs"],
+                             "unit": "GB/s", "frac": ach / peaks["hbm_gbs"],
+                             "algorithmic_bytes_per_model_step": b}}
 
     cpml = None
     if side and not args.no_cpml:

@@ -237,7 +237,7 @@ int wave_reset(wave_ctx *ctx);
  * layer's memory variables start at zero here and are zeroed by wave_reset
  * and wave_set_state. The
  * source and receivers may lie in the layer. wave_adjoint / wave_gradient
- * do not support the layer (WAVE_ENOTSUP).
+ * differentiate the run with the layer (its profile held fixed).
  */
 int wave_set_cpml(wave_ctx *ctx, int npml, double reflection, double f_cps);
 
@@ -286,6 +286,16 @@ int wave_selftest_wait(int64_t limit_ns, void *stream);
  * segment recomputed at a time; the time sum is accumulated in FP64 (each
  * block of 32 steps, counted from step 0, is first summed exactly as an
  * FP32 double-float pair, then added to the FP64 sum).
+ * With the CPML layer (wave_set_cpml) the forward map includes the memory
+ * variables and the adjoint is that of the whole layered update: per axis
+ * a, with A = the profile's a, B = its b and p^{N+1} = nu^{N+1} = mu^{N+1}
+ * = 0, each backward step k forms nu^k = p^{k+1} + B nu^{k+1} and mu^k =
+ * -D1_a (p^{k+1} + A nu^k) + B mu^{k+1} in the slabs and adds
+ * C (D2_a (A nu^k) - D1_a (A mu^k)) to p^k; u^{n+1} - 2u^n + u^{n-1}
+ * includes the layer's term, and the checkpoints also hold psi and zeta.
+ * The profile (which depends on the largest velocity) is held fixed.
+ * Device memory then also holds (2 ceil(nsteps/ckpt_every) + 2) times the
+ * memory-variable slabs (2 npml (ny nz + nz nx + ny nx) floats each).
  *
  *   shot         Ricker source of the forward run (NULL: none)
  *   rec_xyz      nrec*3 int32 receivers (host or device), as wave_propagate

@@ -80,10 +80,14 @@ __device__ __forceinline__ void cpml_row4(const float *row, int p, int n, float 
 // are in flight while the current one is computed. x rows are walked in
 // batches aligned to 4 positions and moved as float4 (a row is contiguous
 // in one thread); y and z lines are coalesced across the threads.
-template <int AX>
+// kStoreD (the gradient's recompute): the same correction C (D1 psi + zeta)
+// is also added to dout, the step's forward increment D = u^{n+1} - 2u^n +
+// u^{n-1} stored by the sweep (field layout).
+template <int AX, bool kStoreD = false>
 __global__ void __launch_bounds__(128)
     cpml_line_kernel(CpmlGeom g, const float *__restrict__ u,
-                     float *__restrict__ unext, const float *__restrict__ c) {
+                     float *__restrict__ unext, const float *__restrict__ c,
+                     float *__restrict__ dout = nullptr) {
   constexpr int F = kCpmlChunk;
   const int t = blockIdx.x * blockDim.x + threadIdx.x;
   const int q = blockIdx.y;  // z for x and y lines, y for z lines
@@ -107,6 +111,7 @@ __global__ void __launch_bounds__(128)
   const float *__restrict__ ul = u + ub;
   const float *__restrict__ cl = c + ub;
   float *__restrict__ nl = unext + ub;
+  float *__restrict__ dl = kStoreD ? dout + ub : nullptr;
   float *__restrict__ psi = g.psi[AX] + sb;
   float *__restrict__ zeta = g.zeta[AX] + sb;
   const float *bp = g.bprof[AX];
@@ -206,6 +211,7 @@ __global__ void __launch_bounds__(128)
         }
         out[f] = fmaf(cc[f], corr, un[f]);
         if (AX != 0) nl[p * us] = out[f];
+        if constexpr (kStoreD) dl[p * us] = fmaf(cc[f], corr, dl[p * us]);
       }
       // x: the whole aligned batch in one store (positions outside the
       // segment keep the value just read; this thread owns the row)
@@ -215,6 +221,117 @@ __global__ void __launch_bounds__(128)
       for (int m = 0; m < 12; ++m) W[m] = W[m + F];
 #pragma unroll
       for (int m = 0; m < 8; ++m) P[m] = P[m + F];
+    }
+  }
+}
+
+// Discrete adjoint of the layer (the gradient's backward steps), in the
+// form the sweep runs it, p = C q. After the plain adjoint sweep has written
+// p^k = 2p^{k+1} - p^{k+2} + C L p^{k+1} (+ injections), for each axis a:
+//     nu_a^k = p^{k+1} + B_a nu_a^{k+1}              (slab cells)
+//     mu_a^k = -D1_a (p^{k+1} + A_a nu_a^k) + B_a mu_a^{k+1}
+//     p^k   += C ( D2_a (A_a nu_a^k) - D1_a (A_a mu_a^k) )
+// (D2_a symmetric and D1_a antisymmetric with the zero halo). A nu and A mu
+// vanish outside the slabs, so the correction reaches w = npml + 4 cells
+// from each face, as in the forward. One thread per line, the same end
+// segments; the walk starts 8 positions before a segment: at position i it
+// forms nu (and g = p + A nu) at i + 8, mu at i + 4 (from g at i .. i + 8)
+// and, inside the segment, the correction at i. Each slab cell is updated
+// by the segment that owns it (the whole line when the segments overlap).
+template <int AX>
+__global__ void __launch_bounds__(128)
+    cpml_adjoint_line_kernel(CpmlGeom g, const float *__restrict__ p1,
+                             float *__restrict__ p0, const float *__restrict__ c,
+                             float *__restrict__ nus, float *__restrict__ mus) {
+  const int t = blockIdx.x * blockDim.x + threadIdx.x;
+  const int q = blockIdx.y;
+  int n;
+  long long ub, us, sb, ss;
+  if (AX == 0) {
+    if (t >= g.ny) return;
+    n = g.nx;
+    ub = ((long long)q * g.ny + t) * g.px;
+    us = 1;
+    sb = (long long)q * g.ny + t;
+    ss = (long long)g.nz * g.ny;
+  } else {
+    if (t >= g.nx) return;
+    n = AX == 1 ? g.ny : g.nz;
+    ub = AX == 1 ? (long long)q * g.ny * g.px + t : (long long)q * g.px + t;
+    us = AX == 1 ? (long long)g.px : (long long)g.ny * g.px;
+    sb = (long long)q * g.nx + t;
+    ss = AX == 1 ? (long long)g.nz * g.nx : (long long)g.ny * g.nx;
+  }
+  const float *__restrict__ pl = p1 + ub;
+  const float *__restrict__ cl = c + ub;
+  float *__restrict__ ol = p0 + ub;
+  float *__restrict__ nu = nus + sb;
+  float *__restrict__ mu = mus + sb;
+  const float *bp = g.bprof[AX];
+  const float *ap = g.aprof[AX];
+  const int npml = g.npml, w = g.w;
+  const bool two = n >= 2 * w;
+  for (int sg = 0; sg < (two ? 2 : 1); ++sg) {
+    const int i0 = (two && sg == 1) ? n - w : 0;
+    const int i1 = two ? (sg == 0 ? w : n) : n;
+    // slab cells this segment updates
+    auto owned = [&](int k) {
+      if (k < 0 || k >= n || !cpml_in_slab(k, n, npml)) return false;
+      return !two || (sg == 0 ? k < npml : k >= n - npml);
+    };
+    float G[9];    // g = p + A nu at positions i .. i+8
+    float AN[13];  // A nu at i-4 .. i+8
+    float AM[9];   // A mu at i-4 .. i+4
+#pragma unroll
+    for (int m = 0; m < 9; ++m) G[m] = AM[m] = 0.f;
+#pragma unroll
+    for (int m = 0; m < 13; ++m) AN[m] = 0.f;
+    for (int i = i0 - 8; i < i1; ++i) {
+      // nu and g at i + 8
+      const int k8 = i + 8;
+      float pv = 0.f, an = 0.f;
+      if (k8 >= 0 && k8 < n) {
+        pv = pl[k8 * us];
+        if (cpml_in_slab(k8, n, npml)) {
+          const long long cell = cpml_cell(k8, n, npml) * ss;
+          const float nv = fmaf(__ldg(bp + k8), nu[cell], pv);
+          if (owned(k8)) nu[cell] = nv;
+          an = __ldg(ap + k8) * nv;
+        }
+      }
+      G[8] = pv + an;
+      AN[12] = an;
+      // mu at i + 4 from g at i .. i + 8
+      const int k4 = i + 4;
+      float am = 0.f;
+      if (k4 >= 0 && k4 < n && cpml_in_slab(k4, n, npml)) {
+        float d1 = 0.f;
+#pragma unroll
+        for (int m = 1; m <= kR; ++m) d1 = fmaf(g.c1[AX][m], G[4 + m] - G[4 - m], d1);
+        const long long cell = cpml_cell(k4, n, npml) * ss;
+        const float mv = fmaf(__ldg(bp + k4), mu[cell], -d1);
+        if (owned(k4)) mu[cell] = mv;
+        am = __ldg(ap + k4) * mv;
+      }
+      AM[8] = am;
+      // correction at i
+      if (i >= i0) {
+        float d2 = g.c2[AX][0] * AN[4];
+        float d1 = 0.f;
+#pragma unroll
+        for (int m = 1; m <= kR; ++m) {
+          d2 = fmaf(g.c2[AX][m], AN[4 + m] + AN[4 - m], d2);
+          d1 = fmaf(g.c1[AX][m], AM[4 + m] - AM[4 - m], d1);
+        }
+        const float corr = d2 - d1;
+        if (corr != 0.f) ol[i * us] = fmaf(cl[i * us], corr, ol[i * us]);
+      }
+#pragma unroll
+      for (int m = 0; m < 8; ++m) G[m] = G[m + 1];
+#pragma unroll
+      for (int m = 0; m < 12; ++m) AN[m] = AN[m + 1];
+#pragma unroll
+      for (int m = 0; m < 8; ++m) AM[m] = AM[m + 1];
     }
   }
 }

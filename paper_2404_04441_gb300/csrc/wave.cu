@@ -1307,7 +1307,7 @@ int gradient_impl(wave_ctx *c, const wave_shot *shot, int N,
                   float *traces_out) {
   if (!c || N < 1 || nrec < 0 || K < 1 || !grad) return WAVE_EINVAL;
   if (nrec > 0 && (!rec_xyz || !data)) return WAVE_EINVAL;
-  if (c->storage != WAVE_STORAGE_F32 || c->cpml ||
+  if (c->storage != WAVE_STORAGE_F32 ||
       c->var.func != reinterpret_cast<const void *>(&wave_sweep_kernel<Cfg0>))
     return WAVE_ENOTSUP;
   int ms = finish_model(c);
@@ -1331,6 +1331,31 @@ int gradient_impl(wave_ctx *c, const wave_shot *shot, int N,
       (e = mem.alloc(&dadj, sizeof(StepDesc))) ||
       (e = mem.alloc(&dfwd, sizeof(StepDesc))))
     return e;
+  // With the CPML layer: the memory variables psi, zeta (per axis) are saved
+  // with each checkpoint, and the adjoint carries its own nu, mu slabs.
+  const CpmlGeom &cg = c->cg;
+  size_t sl[3] = {0, 0, 0};
+  float *ckpt_l = nullptr, *nus[3] = {}, *mus[3] = {};
+  if (c->cpml) {
+    sl[0] = 2ull * cg.npml * c->ny * c->nz;
+    sl[1] = 2ull * cg.npml * c->nz * c->nx;
+    sl[2] = 2ull * cg.npml * c->ny * c->nx;
+    if ((e = mem.alloc(&ckpt_l, (sl[0] + sl[1] + sl[2]) * 2 * 4 * ncp))) return e;
+    for (int ax = 0; ax < 3; ++ax)
+      if ((e = mem.alloc(&nus[ax], sl[ax] * 4)) || (e = mem.alloc(&mus[ax], sl[ax] * 4)))
+        return e;
+  }
+  // copies the layer's memory variables to (save) or from a checkpoint
+  auto layer_ckpt = [&](int sgm, bool save) -> int {
+    float *q = ckpt_l + (sl[0] + sl[1] + sl[2]) * 2 * sgm;
+    for (int ax = 0; ax < 3; ++ax)
+      for (float *f : {cg.psi[ax], cg.zeta[ax]}) {
+        WAVE_TRY_CUDA(cudaMemcpyAsync(save ? q : f, save ? f : q, sl[ax] * 4,
+                                      cudaMemcpyDeviceToDevice, st));
+        q += sl[ax];
+      }
+    return WAVE_OK;
+  };
   const int mode_attr[3] = {kModeStoreD, kModeInject, kModeInject | kModeGradAcc};
   const void *fns[3] = {
       reinterpret_cast<const void *>(&wave_sweep_kernel<Cfg0, false, kModeStoreD>),
@@ -1361,6 +1386,7 @@ int gradient_impl(wave_ctx *c, const wave_shot *shot, int N,
     WAVE_TRY_CUDA(cudaMemcpyAsync(ckpt + (size_t)(2 * sgm + 1) * fe,
                                   c->buf[c->cur ^ 1], fb,
                                   cudaMemcpyDeviceToDevice, st));
+    if (c->cpml && (e = layer_ckpt(sgm, true))) return e;
     const int len = std::min(K, N - sgm * K);
     if ((e = wave_propagate(c, shot, len, rec_xyz, nrec,
                             nrec ? trd + (size_t)sgm * K * nrec : nullptr)))
@@ -1421,6 +1447,12 @@ int gradient_impl(wave_ctx *c, const wave_shot *shot, int N,
   WAVE_TRY_CUDA(cudaMemsetAsync(gacc, 0, fe * 8, st));
   WAVE_TRY_CUDA(cudaMemsetAsync(ghi, 0, fb, st));
   WAVE_TRY_CUDA(cudaMemsetAsync(glo, 0, fb, st));
+  for (int ax = 0; ax < 3 && c->cpml; ++ax) {
+    WAVE_TRY_CUDA(cudaMemsetAsync(nus[ax], 0, sl[ax] * 4, st));
+    WAVE_TRY_CUDA(cudaMemsetAsync(mus[ax], 0, sl[ax] * 4, st));
+  }
+  const dim3 lgrid[3] = {dim3((c->ny + 127) / 128, c->nz), dim3((c->nx + 127) / 128, c->nz),
+                         dim3((c->nx + 127) / 128, c->ny)};
 
   // Adjoint launch a = N - k computes p^k from p^{k+1} (padj[ca]) and
   // p^{k+2}; with kModeGradAcc it adds p^{k+1} D^k to the double-float
@@ -1450,6 +1482,13 @@ int gradient_impl(wave_ctx *c, const wave_shot *shot, int N,
       launch_mode<kModeInject | kModeGradAcc>(c, grid_a, ahalo[ca], atile[ca ^ 1], a);
     else
       launch_mode<kModeInject>(c, grid_a, ahalo[ca], atile[ca ^ 1], a);
+    if (c->cpml) {  // the layer's adjoint terms, from p^{k+1} into p^k
+      const float *p1 = padj[ca];
+      float *p0 = padj[ca ^ 1];
+      cpml_adjoint_line_kernel<0><<<lgrid[0], 128, 0, st>>>(cg, p1, p0, c->c, nus[0], mus[0]);
+      cpml_adjoint_line_kernel<1><<<lgrid[1], 128, 0, st>>>(cg, p1, p0, c->c, nus[1], mus[1]);
+      cpml_adjoint_line_kernel<2><<<lgrid[2], 128, 0, st>>>(cg, p1, p0, c->c, nus[2], mus[2]);
+    }
     if (dsrc && k % kGradFold == 0)
       grad_fold_kernel<<<c->sms * 4, 256, 0, st>>>(gacc, ghi, glo, (long long)fe);
     ca ^= 1;
@@ -1458,11 +1497,12 @@ int gradient_impl(wave_ctx *c, const wave_shot *shot, int N,
   for (int sgm = ncp - 1; sgm >= 0; --sgm) {
     const int s0 = sgm * K, s1 = std::min(N, s0 + K);
     // Recompute the segment's forward steps from its checkpoint, keeping
-    // D^n = C L u^n + source for n in [s0, s1).
+    // D^n = C L u^n + source (+ the layer's term) for n in [s0, s1).
     WAVE_TRY_CUDA(cudaMemcpyAsync(c->buf[0], ckpt + (size_t)2 * sgm * fe, fb,
                                   cudaMemcpyDeviceToDevice, st));
     WAVE_TRY_CUDA(cudaMemcpyAsync(c->buf[1], ckpt + (size_t)(2 * sgm + 1) * fe,
                                   fb, cudaMemcpyDeviceToDevice, st));
+    if (c->cpml && (e = layer_ckpt(sgm, false))) return e;
     int cur = 0;
     for (int n = s0; n < s1; ++n) {
       SweepArgs a = args_d;
@@ -1471,6 +1511,13 @@ int gradient_impl(wave_ctx *c, const wave_shot *shot, int N,
       a.unext = c->buf[cur ^ 1];
       a.dout = dbuf + (size_t)(n - s0) * fe;
       launch_mode<kModeStoreD>(c, grid_d, c->tm_halo[cur], c->tm_tile[cur ^ 1], a);
+      if (c->cpml) {  // the layer's terms, into u^{n+1} and D^n
+        const float *u = (const float *)c->buf[cur];
+        float *un = (float *)c->buf[cur ^ 1];
+        cpml_line_kernel<0, true><<<lgrid[0], 128, 0, st>>>(cg, u, un, c->c, a.dout);
+        cpml_line_kernel<1, true><<<lgrid[1], 128, 0, st>>>(cg, u, un, c->c, a.dout);
+        cpml_line_kernel<2, true><<<lgrid[2], 128, 0, st>>>(cg, u, un, c->c, a.dout);
+      }
       cur ^= 1;
     }
     for (int k = s1 - 1; k >= s0; --k)

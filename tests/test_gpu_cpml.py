@@ -197,12 +197,6 @@ def test_invalid_and_unsupported(wave_lib):
                 s.set_cpml(*args)
             assert ei.value.code == -1
         s.set_cpml(8, 1e-3, 15.0)  # 2 npml == nz: allowed
-        rec = torch.zeros((1, 3), dtype=torch.int32, device="cuda")
-        obs = torch.zeros((5, 1), device="cuda")
-        g = torch.zeros((nz, ny, nx), device="cuda")
-        with pytest.raises(E) as ei:
-            s.gradient((5, 5, 5, 15.0, -1.0, 1.0), 5, rec, obs, g, 2)
-        assert ei.value.code == -8
     finally:
         s.close()
     h = wave_lib.WaveSolver((nx, ny, nz), sp, dt, vel, storage=2)
