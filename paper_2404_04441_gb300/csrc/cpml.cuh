@@ -296,10 +296,10 @@ __global__ void __launch_bounds__(128)
           const long long cell = cpml_cell(k8, n, npml) * ss;
           const float nv = fmaf(__ldg(bp + k8), nu[cell], pv);
           if (owned(k8)) nu[cell] = nv;
-          an = __ldg(ap + k8) * nv;
+          an = __fmul_rn(__ldg(ap + k8), nv);
         }
       }
-      G[8] = pv + an;
+      G[8] = __fadd_rn(pv, an);  // rounded as written (no contraction)
       AN[12] = an;
       // mu at i + 4 from g at i .. i + 8
       const int k4 = i + 4;
@@ -311,7 +311,7 @@ __global__ void __launch_bounds__(128)
         const long long cell = cpml_cell(k4, n, npml) * ss;
         const float mv = fmaf(__ldg(bp + k4), mu[cell], -d1);
         if (owned(k4)) mu[cell] = mv;
-        am = __ldg(ap + k4) * mv;
+        am = __fmul_rn(__ldg(ap + k4), mv);
       }
       AM[8] = am;
       // correction at i
@@ -334,6 +334,265 @@ __global__ void __launch_bounds__(128)
       for (int m = 0; m < 8; ++m) AM[m] = AM[m + 1];
     }
   }
+}
+
+// Unrolled segment kernels for layers of NPML = 8 or 16 cells, on axes
+// where the two end segments are disjoint (n >= 2 w): one thread per line
+// end (blockIdx.z: 0 the low face, 1 the high face), so the two segments of
+// a line run in parallel. Positions are counted from the face, j = 0 .. w-1
+// (i = j, or i = n-1-j at the high face); mirroring flips the sign of D1,
+// which the kernels fold into the order of each difference, so every
+// operation rounds exactly as in the line walks above (the results are
+// bitwise equal). With NPML fixed the whole segment is unrolled: u^n is read
+// at the w positions the layer needs (psi reaches u up to npml + 3 cells from
+// the face), psi and zeta at the npml slab cells, C and u^{n+1} at the w
+// correction points, with no per-position predicates; the profile values
+// travel in the kernel's parameters (constant operands of the FMAs).
+template <int NPML>
+struct CpmlSideProf {
+  float b[2][NPML], a[2][NPML];  // [face][j], j counted from the face
+};
+
+// Segment addressing shared by the unrolled kernels: line offset of
+// position j (field layout) and of slab cell j (slab layout).
+// The per-position steps are 32-bit (the host takes these kernels only
+// where (w - 1) times the field step and (npml - 1) times the slab step fit
+// in an int), which keeps one register per offset instead of a 64-bit
+// address for each of the segment's loads and stores.
+struct CpmlSeg {
+  long long u0;  // field offset of j = 0
+  long long s0;  // slab offset of j = 0
+  int ustep;     // per-position field step
+  int sstep;     // per-cell slab step
+  int n;
+};
+
+template <int AX, int NPML>
+__device__ __forceinline__ bool cpml_seg_setup(const CpmlGeom &g, int side, CpmlSeg &sg) {
+  const int t = blockIdx.x * blockDim.x + threadIdx.x;
+  const int q = blockIdx.y;
+  long long ub, us, sb, ss;
+  if (AX == 0) {
+    if (t >= g.ny) return false;
+    sg.n = g.nx;
+    ub = ((long long)q * g.ny + t) * g.px;
+    us = 1;
+    sb = (long long)q * g.ny + t;
+    ss = (long long)g.nz * g.ny;
+  } else {
+    if (t >= g.nx) return false;
+    sg.n = AX == 1 ? g.ny : g.nz;
+    ub = AX == 1 ? (long long)q * g.ny * g.px + t : (long long)q * g.px + t;
+    us = AX == 1 ? (long long)g.px : (long long)g.ny * g.px;
+    sb = (long long)q * g.nx + t;
+    ss = AX == 1 ? (long long)g.nz * g.nx : (long long)g.ny * g.nx;
+  }
+  // the high face's slab cell of position j is 2 npml - 1 - j
+  sg.u0 = side ? ub + (long long)(sg.n - 1) * us : ub;
+  sg.ustep = (int)(side ? -us : us);
+  sg.s0 = side ? sb + (long long)(2 * NPML - 1) * ss : sb;
+  sg.sstep = (int)(side ? -ss : ss);
+  return true;
+}
+
+// W = NPML + 4 values of a field along the segment, v[j] = f(position j).
+// x lines are rows: read as float4 when the segment starts on a 16-byte
+// boundary (the low face always; the high face when n is a multiple of 4).
+template <int AX, int W, int SIDE>
+__device__ __forceinline__ void cpml_seg_load(const float *f, const CpmlSeg &sg, float *v) {
+  if (AX == 0 && (SIDE == 0 || (sg.n & 3) == 0)) {
+    const float *r = SIDE == 0 ? f + sg.u0 : f + sg.u0 - (W - 1);
+#pragma unroll
+    for (int k = 0; k < W; k += 4) {
+      const float4 t = *reinterpret_cast<const float4 *>(r + k);
+      const float e[4] = {t.x, t.y, t.z, t.w};
+#pragma unroll
+      for (int m = 0; m < 4; ++m) v[SIDE == 0 ? k + m : W - 1 - (k + m)] = e[m];
+    }
+  } else {
+    const float *r = f + sg.u0;
+#pragma unroll
+    for (int j = 0; j < W; ++j) v[j] = r[j * sg.ustep];
+  }
+}
+
+template <int AX, int W, int SIDE>
+__device__ __forceinline__ void cpml_seg_store(float *f, const CpmlSeg &sg, const float *v) {
+  if (AX == 0 && (SIDE == 0 || (sg.n & 3) == 0)) {
+    float *r = SIDE == 0 ? f + sg.u0 : f + sg.u0 - (W - 1);
+#pragma unroll
+    for (int k = 0; k < W; k += 4) {
+      float e[4];
+#pragma unroll
+      for (int m = 0; m < 4; ++m) e[m] = v[SIDE == 0 ? k + m : W - 1 - (k + m)];
+      *reinterpret_cast<float4 *>(r + k) = make_float4(e[0], e[1], e[2], e[3]);
+    }
+  } else {
+    float *r = f + sg.u0;
+#pragma unroll
+    for (int j = 0; j < W; ++j) r[j * sg.ustep] = v[j];
+  }
+}
+
+// Window value v[k], zero outside [0, N) (k is a compile-time constant
+// after unrolling, so the test costs nothing).
+template <int N>
+__device__ __forceinline__ float cpml_seg_at(const float *v, int k) {
+  return (k >= 0 && k < N) ? v[k] : 0.f;
+}
+
+// D1 at position j of a window v (zero outside [0, N)), as the line walks
+// round it: sum over m of c1_m (f(i+m) - f(i-m)), i the grid position, which
+// at the high face is v(j-m) - v(j+m).
+template <int SIDE, int N>
+__device__ __forceinline__ float cpml_seg_d1(const float *v, int j, const float *c1) {
+  float d = 0.f;
+#pragma unroll
+  for (int m = 1; m <= kR; ++m) {
+    const float hi = cpml_seg_at<N>(v, j + m);
+    const float lo = cpml_seg_at<N>(v, j - m);
+    d = fmaf(c1[m], SIDE == 0 ? hi - lo : lo - hi, d);
+  }
+  return d;
+}
+
+template <int N>
+__device__ __forceinline__ float cpml_seg_d2(const float *v, int j, const float *c2) {
+  float d = c2[0] * cpml_seg_at<N>(v, j);
+#pragma unroll
+  for (int m = 1; m <= kR; ++m)
+    d = fmaf(c2[m], cpml_seg_at<N>(v, j + m) + cpml_seg_at<N>(v, j - m), d);
+  return d;
+}
+
+template <int AX, int NPML, bool kStoreD, int SIDE>
+__device__ __forceinline__ void cpml_seg_forward(const CpmlGeom &g, const CpmlSideProf<NPML> &pf,
+                                                 const float *__restrict__ u,
+                                                 float *__restrict__ unext,
+                                                 const float *__restrict__ c,
+                                                 float *__restrict__ dout) {
+  constexpr int W = NPML + 4;
+  CpmlSeg sg;
+  if (!cpml_seg_setup<AX, NPML>(g, SIDE, sg)) return;
+  float *psi = g.psi[AX] + sg.s0;
+  float *zeta = g.zeta[AX] + sg.s0;
+  // Every load is issued before the first store (the slabs and the fields
+  // are not known to be distinct, so a load after a store would wait for it).
+  float U[W], PS[NPML], ZT[NPML], CC[W], UN[W], DO[kStoreD ? W : 1];
+  cpml_seg_load<AX, W, SIDE>(u, sg, U);
+#pragma unroll
+  for (int j = 0; j < NPML; ++j) {
+    PS[j] = psi[j * sg.sstep];
+    ZT[j] = zeta[j * sg.sstep];
+  }
+  cpml_seg_load<AX, W, SIDE>(c, sg, CC);
+  cpml_seg_load<AX, W, SIDE>(unext, sg, UN);
+  if constexpr (kStoreD) cpml_seg_load<AX, W, SIDE>(dout, sg, DO);
+  // psi^n at the slab cells from u^n (u^n is zero past the face)
+#pragma unroll
+  for (int j = 0; j < NPML; ++j) {
+    const float d1 = cpml_seg_d1<SIDE, W>(U, j, g.c1[AX]);
+    PS[j] = fmaf(pf.b[SIDE][j], PS[j], pf.a[SIDE][j] * d1);
+  }
+  // zeta^n in the slab, then u^{n+1} += C (D1 psi^n + zeta^n) over the
+  // segment (psi is zero past the slab)
+#pragma unroll
+  for (int j = 0; j < W; ++j) {
+    const float d1p = cpml_seg_d1<SIDE, NPML>(PS, j, g.c1[AX]);
+    float corr = d1p;
+    if (j < NPML) {
+      const float d2 = cpml_seg_d2<W>(U, j, g.c2[AX]);
+      ZT[j] = fmaf(pf.b[SIDE][j], ZT[j], pf.a[SIDE][j] * (d2 + d1p));
+      corr += ZT[j];
+    }
+    UN[j] = fmaf(CC[j], corr, UN[j]);
+    if constexpr (kStoreD) DO[j] = fmaf(CC[j], corr, DO[j]);
+  }
+#pragma unroll
+  for (int j = 0; j < NPML; ++j) {
+    psi[j * sg.sstep] = PS[j];
+    zeta[j * sg.sstep] = ZT[j];
+  }
+  cpml_seg_store<AX, W, SIDE>(unext, sg, UN);
+  if constexpr (kStoreD) cpml_seg_store<AX, W, SIDE>(dout, sg, DO);
+}
+
+template <int AX, int NPML, bool kStoreD = false>
+__global__ void __launch_bounds__(128)
+    cpml_seg_kernel(CpmlGeom g, CpmlSideProf<NPML> pf, const float *__restrict__ u,
+                    float *__restrict__ unext, const float *__restrict__ c,
+                    float *__restrict__ dout = nullptr) {
+  if (blockIdx.z == 0)
+    cpml_seg_forward<AX, NPML, kStoreD, 0>(g, pf, u, unext, c, dout);
+  else
+    cpml_seg_forward<AX, NPML, kStoreD, 1>(g, pf, u, unext, c, dout);
+}
+
+// The adjoint's segment form (cpml_adjoint_line_kernel, unrolled): nu and
+// g = p^{k+1} + A nu at the w positions, mu at the slab cells, then
+// p^k += C (D2 (A nu) - D1 (A mu)) over the segment.
+template <int AX, int NPML, int SIDE>
+__device__ __forceinline__ void cpml_seg_adjoint(const CpmlGeom &g, const CpmlSideProf<NPML> &pf,
+                                                 const float *__restrict__ p1,
+                                                 float *__restrict__ p0,
+                                                 const float *__restrict__ c,
+                                                 float *__restrict__ nus,
+                                                 float *__restrict__ mus) {
+  constexpr int W = NPML + 4;
+  CpmlSeg sg;
+  if (!cpml_seg_setup<AX, NPML>(g, SIDE, sg)) return;
+  float *nu = nus + sg.s0;
+  float *mu = mus + sg.s0;
+  // every load before the first store, as in the forward
+  float P[W], G[W], NU[NPML], MU[NPML], AN[NPML], AM[NPML], CC[W], PO[W];
+  cpml_seg_load<AX, W, SIDE>(p1, sg, P);
+#pragma unroll
+  for (int j = 0; j < NPML; ++j) {
+    NU[j] = nu[j * sg.sstep];
+    MU[j] = mu[j * sg.sstep];
+  }
+  cpml_seg_load<AX, W, SIDE>(c, sg, CC);
+  cpml_seg_load<AX, W, SIDE>(p0, sg, PO);
+#pragma unroll
+  for (int j = 0; j < W; ++j) {
+    G[j] = P[j];
+    if (j < NPML) {
+      NU[j] = fmaf(pf.b[SIDE][j], NU[j], P[j]);
+      AN[j] = __fmul_rn(pf.a[SIDE][j], NU[j]);
+      G[j] = __fadd_rn(P[j], AN[j]);  // as the line walk: no contraction
+    }
+  }
+#pragma unroll
+  for (int j = 0; j < NPML; ++j) {
+    const float d1 = cpml_seg_d1<SIDE, W>(G, j, g.c1[AX]);
+    MU[j] = fmaf(pf.b[SIDE][j], MU[j], -d1);
+    AM[j] = __fmul_rn(pf.a[SIDE][j], MU[j]);
+  }
+#pragma unroll
+  for (int j = 0; j < NPML; ++j) {
+    nu[j * sg.sstep] = NU[j];
+    mu[j * sg.sstep] = MU[j];
+  }
+#pragma unroll
+  for (int j = 0; j < W; ++j) {
+    // A nu and A mu are zero past the slab
+    const float d2 = cpml_seg_d2<NPML>(AN, j, g.c2[AX]);
+    const float d1 = cpml_seg_d1<SIDE, NPML>(AM, j, g.c1[AX]);
+    const float corr = d2 - d1;
+    PO[j] = fmaf(CC[j], corr, PO[j]);
+  }
+  cpml_seg_store<AX, W, SIDE>(p0, sg, PO);
+}
+
+template <int AX, int NPML>
+__global__ void __launch_bounds__(128)
+    cpml_seg_adjoint_kernel(CpmlGeom g, CpmlSideProf<NPML> pf, const float *__restrict__ p1,
+                            float *__restrict__ p0, const float *__restrict__ c,
+                            float *__restrict__ nus, float *__restrict__ mus) {
+  if (blockIdx.z == 0)
+    cpml_seg_adjoint<AX, NPML, 0>(g, pf, p1, p0, c, nus, mus);
+  else
+    cpml_seg_adjoint<AX, NPML, 1>(g, pf, p1, p0, c, nus, mus);
 }
 
 // Receivers within w of a face: {x, y, z, receiver id}.

@@ -208,6 +208,9 @@ struct wave_ctx {
   std::vector<void *> cpml_mem;
   DeviceBuf srec;            // receivers within w of a face: {x, y, z, id}
   int *d_nsrec = nullptr;    // their count (device: graphs stay valid)
+  int cpml_seg_axes = 0;     // bit a: axis a runs the unrolled segment kernels
+  CpmlSideProf<8> prof8[3];  // their profile values (npml 8 or 16)
+  CpmlSideProf<16> prof16[3];
 };
 
 namespace {
@@ -247,6 +250,47 @@ void set_coeffs(wave_ctx *c) {
   a.desc = c->d_desc;
 }
 
+// The layer's pass along axis AX of one forward step (dout: the layer's
+// term also into the stored increment D), and of one adjoint step.
+template <int AX, bool kD>
+void launch_cpml_axis(const wave_ctx *c, cudaStream_t st, const float *u, float *un,
+                      float *dout) {
+  const CpmlGeom &g = c->cg;
+  const int inner = AX == 0 ? c->ny : c->nx, outer = AX == 2 ? c->ny : c->nz;
+  const bool seg = (c->cpml_seg_axes >> AX) & 1;
+  const dim3 grid((inner + 127) / 128, outer, seg ? 2 : 1);
+  if (!seg)
+    cpml_line_kernel<AX, kD><<<grid, 128, 0, st>>>(g, u, un, c->c, dout);
+  else if (g.npml == 8)
+    cpml_seg_kernel<AX, 8, kD><<<grid, 128, 0, st>>>(g, c->prof8[AX], u, un, c->c, dout);
+  else
+    cpml_seg_kernel<AX, 16, kD><<<grid, 128, 0, st>>>(g, c->prof16[AX], u, un, c->c, dout);
+}
+
+template <bool kD>
+void launch_cpml_forward(const wave_ctx *c, cudaStream_t st, const float *u, float *un,
+                         float *dout) {
+  launch_cpml_axis<0, kD>(c, st, u, un, dout);
+  launch_cpml_axis<1, kD>(c, st, u, un, dout);
+  launch_cpml_axis<2, kD>(c, st, u, un, dout);
+}
+
+template <int AX>
+void launch_cpml_adjoint_axis(const wave_ctx *c, cudaStream_t st, const float *p1, float *p0,
+                              float *nus, float *mus) {
+  const CpmlGeom &g = c->cg;
+  const int inner = AX == 0 ? c->ny : c->nx, outer = AX == 2 ? c->ny : c->nz;
+  const bool seg = (c->cpml_seg_axes >> AX) & 1;
+  const dim3 grid((inner + 127) / 128, outer, seg ? 2 : 1);
+  if (!seg)
+    cpml_adjoint_line_kernel<AX><<<grid, 128, 0, st>>>(g, p1, p0, c->c, nus, mus);
+  else if (g.npml == 8)
+    cpml_seg_adjoint_kernel<AX, 8><<<grid, 128, 0, st>>>(g, c->prof8[AX], p1, p0, c->c, nus, mus);
+  else
+    cpml_seg_adjoint_kernel<AX, 16><<<grid, 128, 0, st>>>(g, c->prof16[AX], p1, p0, c->c, nus,
+                                                          mus);
+}
+
 // Enqueue one step on stream st: u = buf[cur], u_prev = buf[cur ^ 1]. With
 // the CPML layer: memory variables and shell points before the sweep, the
 // shell values committed after it.
@@ -259,9 +303,7 @@ void enqueue_step(wave_ctx *c, cudaStream_t st, int cur, int koff) {
     const float *u = (const float *)c->buf[cur];
     float *un = (float *)c->buf[cur ^ 1];
     const CpmlGeom &g = c->cg;
-    cpml_line_kernel<0><<<dim3((c->ny + 127) / 128, c->nz), 128, 0, st>>>(g, u, un, c->c);
-    cpml_line_kernel<1><<<dim3((c->nx + 127) / 128, c->nz), 128, 0, st>>>(g, u, un, c->c);
-    cpml_line_kernel<2><<<dim3((c->nx + 127) / 128, c->ny), 128, 0, st>>>(g, u, un, c->c);
+    launch_cpml_forward<false>(c, st, u, un, nullptr);
     cpml_record_kernel<<<c->sms, 256, 0, st>>>(g, un, c->d_desc,
                                                (const int4 *)c->srec.p, c->d_nsrec, koff);
   }
@@ -280,6 +322,7 @@ void free_cpml(wave_ctx *c) {
   c->cpml_mem.clear();
   c->cpml = false;
   c->cg = CpmlGeom{};
+  c->cpml_seg_axes = 0;
 }
 
 int zero_cpml(wave_ctx *c) {
@@ -1151,6 +1194,30 @@ int wave_set_cpml(wave_ctx *c, int npml, double R, double f_cps) {
         hb[i] = (float)bb;
         ha[i] = (float)(dd + al > 0.0 ? dd / (dd + al) * (bb - 1.0) : 0.0);
       }
+      // The unrolled segment kernels take npml 8 or 16 on axes where the two
+      // end segments are disjoint; GBWAVE_CPML_GENERIC=1 keeps the line walks
+      // everywhere (the two give bitwise equal results).
+      const char *gen = std::getenv("GBWAVE_CPML_GENERIC");
+      // field and slab steps along the axis (the kernels' 32-bit offsets)
+      const long long fstep[3] = {1, c->px, (long long)c->ny * c->px};
+      const long long sstep[3] = {(long long)c->nz * c->ny, (long long)c->nz * c->nx,
+                                  (long long)c->ny * c->nx};
+      if ((npml == 8 || npml == 16) && dims[ax] >= 2 * (npml + 4) &&
+          (long long)(npml + 3) * fstep[ax] <= INT32_MAX &&
+          (long long)(npml - 1) * sstep[ax] <= INT32_MAX && !(gen && std::atoi(gen) == 1)) {
+        c->cpml_seg_axes |= 1 << ax;
+        for (int j = 0; j < npml; ++j)
+          for (int sd = 0; sd < 2; ++sd) {
+            const int i = sd ? dims[ax] - 1 - j : j;
+            if (npml == 8) {
+              c->prof8[ax].b[sd][j] = hb[i];
+              c->prof8[ax].a[sd][j] = ha[i];
+            } else {
+              c->prof16[ax].b[sd][j] = hb[i];
+              c->prof16[ax].a[sd][j] = ha[i];
+            }
+          }
+      }
       WAVE_TRY_CUDA(cudaMemcpy((void *)g.bprof[ax], hb.data(), dims[ax] * 4,
                                cudaMemcpyHostToDevice));
       WAVE_TRY_CUDA(cudaMemcpy((void *)g.aprof[ax], ha.data(), dims[ax] * 4,
@@ -1451,8 +1518,6 @@ int gradient_impl(wave_ctx *c, const wave_shot *shot, int N,
     WAVE_TRY_CUDA(cudaMemsetAsync(nus[ax], 0, sl[ax] * 4, st));
     WAVE_TRY_CUDA(cudaMemsetAsync(mus[ax], 0, sl[ax] * 4, st));
   }
-  const dim3 lgrid[3] = {dim3((c->ny + 127) / 128, c->nz), dim3((c->nx + 127) / 128, c->nz),
-                         dim3((c->nx + 127) / 128, c->ny)};
 
   // Adjoint launch a = N - k computes p^k from p^{k+1} (padj[ca]) and
   // p^{k+2}; with kModeGradAcc it adds p^{k+1} D^k to the double-float
@@ -1485,9 +1550,9 @@ int gradient_impl(wave_ctx *c, const wave_shot *shot, int N,
     if (c->cpml) {  // the layer's adjoint terms, from p^{k+1} into p^k
       const float *p1 = padj[ca];
       float *p0 = padj[ca ^ 1];
-      cpml_adjoint_line_kernel<0><<<lgrid[0], 128, 0, st>>>(cg, p1, p0, c->c, nus[0], mus[0]);
-      cpml_adjoint_line_kernel<1><<<lgrid[1], 128, 0, st>>>(cg, p1, p0, c->c, nus[1], mus[1]);
-      cpml_adjoint_line_kernel<2><<<lgrid[2], 128, 0, st>>>(cg, p1, p0, c->c, nus[2], mus[2]);
+      launch_cpml_adjoint_axis<0>(c, st, p1, p0, nus[0], mus[0]);
+      launch_cpml_adjoint_axis<1>(c, st, p1, p0, nus[1], mus[1]);
+      launch_cpml_adjoint_axis<2>(c, st, p1, p0, nus[2], mus[2]);
     }
     if (dsrc && k % kGradFold == 0)
       grad_fold_kernel<<<c->sms * 4, 256, 0, st>>>(gacc, ghi, glo, (long long)fe);
@@ -1512,11 +1577,8 @@ int gradient_impl(wave_ctx *c, const wave_shot *shot, int N,
       a.dout = dbuf + (size_t)(n - s0) * fe;
       launch_mode<kModeStoreD>(c, grid_d, c->tm_halo[cur], c->tm_tile[cur ^ 1], a);
       if (c->cpml) {  // the layer's terms, into u^{n+1} and D^n
-        const float *u = (const float *)c->buf[cur];
-        float *un = (float *)c->buf[cur ^ 1];
-        cpml_line_kernel<0, true><<<lgrid[0], 128, 0, st>>>(cg, u, un, c->c, a.dout);
-        cpml_line_kernel<1, true><<<lgrid[1], 128, 0, st>>>(cg, u, un, c->c, a.dout);
-        cpml_line_kernel<2, true><<<lgrid[2], 128, 0, st>>>(cg, u, un, c->c, a.dout);
+        launch_cpml_forward<true>(c, st, (const float *)c->buf[cur], (float *)c->buf[cur ^ 1],
+                                  a.dout);
       }
       cur ^= 1;
     }

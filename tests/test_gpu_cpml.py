@@ -126,6 +126,41 @@ def test_ragged_random_state(wave_lib, oracle_mod, shape, spacing, npml, chunks,
     assert rel_l2(gtr, otr) <= tol(n)
 
 
+# npml 8 and 16 on axes of at least 2 (npml + 4) cells run the unrolled
+# segment kernels (both faces of a line in parallel, x rows as float4 where
+# the segment is aligned); the last case keeps the line walk on y (35 < 40).
+SEG_CASES = [((75, 52, 44), 8), ((72, 41, 40), 16), ((88, 40, 57), 16), ((72, 35, 44), 16)]
+
+
+@pytest.mark.parametrize("shape,npml", SEG_CASES)
+def test_unrolled_segments_equal_the_line_walks(wave_lib, oracle_mod, monkeypatch, shape, npml):
+    """The segment kernels round every operation as the line walks do, so the
+    two give the same fields and traces bit for bit (GBWAVE_CPML_GENERIC=1
+    keeps the line walks); both against the oracle at the FP32 bar. Random
+    state, the source inside the low z layer, shell receivers, 37 steps in
+    chunks across a graph's length."""
+    nx, ny, nz = shape
+    sp = (10.0, 12.0, 9.0)
+    rng = np.random.default_rng(npml * 7 + nx)
+    vel = rng.uniform(1500.0, 4000.0, size=(nz, ny, nx)).astype(np.float32)
+    u0, up0 = wl.random_state((nz, ny, nx), seed=nx + ny)
+    dt = 0.5 * wave_lib.wave_cfl_dt(sp, float(vel.max()))
+    shot = (nx // 3, ny - 5, 3, 20.0, -1.0, 1e3)
+    rec = shell_receivers(nx, ny, nz, npml + 4)
+    chunks = [3, 34]
+    R, fcps = 1e-3, 15.0
+    monkeypatch.setenv("GBWAVE_CPML_GENERIC", "1")
+    gu, gup, gtr = gpu_cpml(wave_lib, vel, sp, dt, chunks, npml, R, fcps, shot, rec, u0, up0, 2)
+    monkeypatch.delenv("GBWAVE_CPML_GENERIC")
+    su, sup, s_tr = gpu_cpml(wave_lib, vel, sp, dt, chunks, npml, R, fcps, shot, rec, u0, up0, 2)
+    assert np.array_equal(su, gu) and np.array_equal(sup, gup) and np.array_equal(s_tr, gtr)
+    ou, _, _, _, otr = oracle_mod.propagate_cpml(vel, sp, dt, sum(chunks), npml, R=R, fcps=fcps,
+                                                 u=u0, u_prev=up0, step0=2, source=shot,
+                                                 receivers=rec)
+    assert rel_l2(su, ou) <= tol(sum(chunks))
+    assert rel_l2(s_tr, otr) <= tol(sum(chunks))
+
+
 def test_layer_absorbs_compared_with_the_zero_halo(wave_lib):
     """After the wavelet has crossed the grid, the field left with the layer is
     a small fraction of the field left with the bare zero (reflecting) halo."""

@@ -48,6 +48,45 @@ def _gpu(pkg, vel, sp, dt, npml, shot, n, rec, obs, ckpt):
 CASES = [((32, 32, 32), 6, 7), ((21, 18, 12), 6, 11)]
 
 
+# npml 8 and 16 on axes of at least 2 (npml + 4) cells run the unrolled
+# segment kernels (recompute and adjoint); x = 45 and 41 leave the high-face
+# x rows unaligned.
+SEG_CASES = [((45, 36, 30), 8, 9), ((41, 44, 40), 16, 13)]
+
+
+@pytest.mark.parametrize("shape,npml,ckpt", SEG_CASES)
+def test_unrolled_segments_in_the_gradient(wave_lib, oracle_mod, monkeypatch, shape, npml, ckpt):
+    """The gradient with the unrolled segment kernels equals the one with the
+    line walks (GBWAVE_CPML_GENERIC=1) bit for bit, and the oracle's layered
+    adjoint within the gradient bar."""
+    cfg = wl.CFG_GRAD_SMALL
+    nx, ny, nz = shape
+    sp = cfg["spacing"]
+    n = cfg["nsteps"]
+    true = wl.anomaly_model(nx, ny, nz, seed=cfg["seed"], anomaly=cfg["anomaly_mps"])
+    start = wl.smoothed_start(true)
+    rec = wl.receiver_plane(nx, ny, 4, 3)
+    shot = (nx // 2, ny // 3, 3, 25.0, -1.0, 1e3)
+    dt = 0.5 * wave_lib.wave_cfl_dt(sp, max(float(true.max()), float(start.max())) * 1.02)
+    _, _, _, _, obs = oracle_mod.propagate_cpml(true, sp, dt, n, npml, R=R, fcps=FCPS,
+                                                source=shot, receivers=rec)
+    obs = obs.astype(np.float32)
+    monkeypatch.setenv("GBWAVE_CPML_GENERIC", "1")
+    mis_g, g_g, tr_g = _gpu(wave_lib, start, sp, dt, npml, shot, n, rec, obs, ckpt)
+    monkeypatch.delenv("GBWAVE_CPML_GENERIC")
+    mis, g, tr = _gpu(wave_lib, start, sp, dt, npml, shot, n, rec, obs, ckpt)
+    assert np.array_equal(tr, tr_g) and np.array_equal(g, g_g)
+    assert mis == pytest.approx(mis_g, rel=1e-12)
+    vmax = float(start.max())
+    _, _, _, _, otr = oracle_mod.propagate_cpml(start, sp, dt, n, npml, R=R, fcps=FCPS,
+                                                vmax=vmax, source=shot, receivers=rec)
+    og = oracle_mod.gradient_cpml(start, sp, dt, n, npml, shot, rec, otr - obs, R=R,
+                                  fcps=FCPS, vmax=vmax)
+    err = rel_l2(g, og)
+    print("\nCPML gradient (unrolled segments) rel-L2 vs oracle adjoint %s: %.3e" % (shape, err))
+    assert err <= 2e-4
+
+
 @pytest.mark.parametrize("shape,npml,ckpt", CASES)
 def test_cpml_gradient_matches_oracle_adjoint(wave_lib, oracle_mod, shape, npml, ckpt):
     cfg = wl.CFG_GRAD_SMALL
