@@ -467,51 +467,56 @@ __device__ __forceinline__ float cpml_seg_d2(const float *v, int j, const float 
 
 template <int AX, int NPML, bool kStoreD, int SIDE>
 __device__ __forceinline__ void cpml_seg_forward(const CpmlGeom &g, const CpmlSideProf<NPML> &pf,
-                                                 const float *__restrict__ u,
-                                                 float *__restrict__ unext,
-                                                 const float *__restrict__ c,
-                                                 float *__restrict__ dout) {
+                                                  const float *__restrict__ u,
+                                                  float *__restrict__ unext,
+                                                  const float *__restrict__ c,
+                                                  float *__restrict__ dout) {
   constexpr int W = NPML + 4;
   CpmlSeg sg;
   if (!cpml_seg_setup<AX, NPML>(g, SIDE, sg)) return;
   float *psi = g.psi[AX] + sg.s0;
   float *zeta = g.zeta[AX] + sg.s0;
-  // Every load is issued before the first store (the slabs and the fields
-  // are not known to be distinct, so a load after a store would wait for it).
-  float U[W], PS[NPML], ZT[NPML], CC[W], UN[W], DO[kStoreD ? W : 1];
+  // Two phases, each issuing all of its loads before its first store (the
+  // slabs and the fields are not known to be distinct, so a load after a
+  // store waits for it): u^n, psi and zeta -> the new psi, zeta and the
+  // corrections; then C, u^{n+1} (and D) -> u^{n+1} (and D) updated. The
+  // second phase's loads wait behind the slab stores once per thread, and
+  // the live set stays about half of what one phase would hold.
+  float U[W], PS[NPML], ZT[NPML], CORR[W];
   cpml_seg_load<AX, W, SIDE>(u, sg, U);
 #pragma unroll
   for (int j = 0; j < NPML; ++j) {
     PS[j] = psi[j * sg.sstep];
     ZT[j] = zeta[j * sg.sstep];
   }
-  cpml_seg_load<AX, W, SIDE>(c, sg, CC);
-  cpml_seg_load<AX, W, SIDE>(unext, sg, UN);
-  if constexpr (kStoreD) cpml_seg_load<AX, W, SIDE>(dout, sg, DO);
-  // psi^n at the slab cells from u^n (u^n is zero past the face)
 #pragma unroll
   for (int j = 0; j < NPML; ++j) {
     const float d1 = cpml_seg_d1<SIDE, W>(U, j, g.c1[AX]);
     PS[j] = fmaf(pf.b[SIDE][j], PS[j], pf.a[SIDE][j] * d1);
   }
-  // zeta^n in the slab, then u^{n+1} += C (D1 psi^n + zeta^n) over the
-  // segment (psi is zero past the slab)
 #pragma unroll
   for (int j = 0; j < W; ++j) {
     const float d1p = cpml_seg_d1<SIDE, NPML>(PS, j, g.c1[AX]);
-    float corr = d1p;
+    CORR[j] = d1p;
     if (j < NPML) {
       const float d2 = cpml_seg_d2<W>(U, j, g.c2[AX]);
       ZT[j] = fmaf(pf.b[SIDE][j], ZT[j], pf.a[SIDE][j] * (d2 + d1p));
-      corr += ZT[j];
+      CORR[j] += ZT[j];
     }
-    UN[j] = fmaf(CC[j], corr, UN[j]);
-    if constexpr (kStoreD) DO[j] = fmaf(CC[j], corr, DO[j]);
   }
 #pragma unroll
   for (int j = 0; j < NPML; ++j) {
     psi[j * sg.sstep] = PS[j];
     zeta[j * sg.sstep] = ZT[j];
+  }
+  float CC[W], UN[W], DO[kStoreD ? W : 1];
+  cpml_seg_load<AX, W, SIDE>(c, sg, CC);
+  cpml_seg_load<AX, W, SIDE>(unext, sg, UN);
+  if constexpr (kStoreD) cpml_seg_load<AX, W, SIDE>(dout, sg, DO);
+#pragma unroll
+  for (int j = 0; j < W; ++j) {
+    UN[j] = fmaf(CC[j], CORR[j], UN[j]);
+    if constexpr (kStoreD) DO[j] = fmaf(CC[j], CORR[j], DO[j]);
   }
   cpml_seg_store<AX, W, SIDE>(unext, sg, UN);
   if constexpr (kStoreD) cpml_seg_store<AX, W, SIDE>(dout, sg, DO);
@@ -543,16 +548,15 @@ __device__ __forceinline__ void cpml_seg_adjoint(const CpmlGeom &g, const CpmlSi
   if (!cpml_seg_setup<AX, NPML>(g, SIDE, sg)) return;
   float *nu = nus + sg.s0;
   float *mu = mus + sg.s0;
-  // every load before the first store, as in the forward
-  float P[W], G[W], NU[NPML], MU[NPML], AN[NPML], AM[NPML], CC[W], PO[W];
+  // two phases as in the forward: p^{k+1}, nu, mu -> nu, mu and the
+  // corrections; then C, p^k -> p^k updated
+  float P[W], G[W], NU[NPML], MU[NPML], AN[NPML], AM[NPML], CORR[W];
   cpml_seg_load<AX, W, SIDE>(p1, sg, P);
 #pragma unroll
   for (int j = 0; j < NPML; ++j) {
     NU[j] = nu[j * sg.sstep];
     MU[j] = mu[j * sg.sstep];
   }
-  cpml_seg_load<AX, W, SIDE>(c, sg, CC);
-  cpml_seg_load<AX, W, SIDE>(p0, sg, PO);
 #pragma unroll
   for (int j = 0; j < W; ++j) {
     G[j] = P[j];
@@ -569,18 +573,22 @@ __device__ __forceinline__ void cpml_seg_adjoint(const CpmlGeom &g, const CpmlSi
     AM[j] = __fmul_rn(pf.a[SIDE][j], MU[j]);
   }
 #pragma unroll
-  for (int j = 0; j < NPML; ++j) {
-    nu[j * sg.sstep] = NU[j];
-    mu[j * sg.sstep] = MU[j];
-  }
-#pragma unroll
   for (int j = 0; j < W; ++j) {
     // A nu and A mu are zero past the slab
     const float d2 = cpml_seg_d2<NPML>(AN, j, g.c2[AX]);
     const float d1 = cpml_seg_d1<SIDE, NPML>(AM, j, g.c1[AX]);
-    const float corr = d2 - d1;
-    PO[j] = fmaf(CC[j], corr, PO[j]);
+    CORR[j] = d2 - d1;
   }
+#pragma unroll
+  for (int j = 0; j < NPML; ++j) {
+    nu[j * sg.sstep] = NU[j];
+    mu[j * sg.sstep] = MU[j];
+  }
+  float CC[W], PO[W];
+  cpml_seg_load<AX, W, SIDE>(c, sg, CC);
+  cpml_seg_load<AX, W, SIDE>(p0, sg, PO);
+#pragma unroll
+  for (int j = 0; j < W; ++j) PO[j] = fmaf(CC[j], CORR[j], PO[j]);
   cpml_seg_store<AX, W, SIDE>(p0, sg, PO);
 }
 
