@@ -253,9 +253,8 @@ void set_coeffs(wave_ctx *c) {
 // The layer's pass along axis AX of one forward step (dout: the layer's
 // term also into the stored increment D), and of one adjoint step.
 template <int AX, bool kD>
-void launch_cpml_axis(const wave_ctx *c, cudaStream_t st, const float *u, float *un,
-                      float *dout) {
-  const CpmlGeom &g = c->cg;
+void launch_cpml_axis(const wave_ctx *c, const CpmlGeom &g, cudaStream_t st, const float *u,
+                      float *un, float *dout) {
   const int inner = AX == 0 ? c->ny : c->nx, outer = AX == 2 ? c->ny : c->nz;
   const bool seg = (c->cpml_seg_axes >> AX) & 1;
   const dim3 grid((inner + 127) / 128, outer, seg ? 2 : 1);
@@ -267,12 +266,13 @@ void launch_cpml_axis(const wave_ctx *c, cudaStream_t st, const float *u, float 
     cpml_seg_kernel<AX, 16, kD><<<grid, 128, 0, st>>>(g, c->prof16[AX], u, un, c->c, dout);
 }
 
+// g: the context's layer, or the same layer on other memory-variable slabs
 template <bool kD>
-void launch_cpml_forward(const wave_ctx *c, cudaStream_t st, const float *u, float *un,
-                         float *dout) {
-  launch_cpml_axis<0, kD>(c, st, u, un, dout);
-  launch_cpml_axis<1, kD>(c, st, u, un, dout);
-  launch_cpml_axis<2, kD>(c, st, u, un, dout);
+void launch_cpml_forward(const wave_ctx *c, const CpmlGeom &g, cudaStream_t st, const float *u,
+                         float *un, float *dout) {
+  launch_cpml_axis<0, kD>(c, g, st, u, un, dout);
+  launch_cpml_axis<1, kD>(c, g, st, u, un, dout);
+  launch_cpml_axis<2, kD>(c, g, st, u, un, dout);
 }
 
 template <int AX>
@@ -303,7 +303,7 @@ void enqueue_step(wave_ctx *c, cudaStream_t st, int cur, int koff) {
     const float *u = (const float *)c->buf[cur];
     float *un = (float *)c->buf[cur ^ 1];
     const CpmlGeom &g = c->cg;
-    launch_cpml_forward<false>(c, st, u, un, nullptr);
+    launch_cpml_forward<false>(c, g, st, u, un, nullptr);
     cpml_record_kernel<<<c->sms, 256, 0, st>>>(g, un, c->d_desc,
                                                (const int4 *)c->srec.p, c->d_nsrec, koff);
   }
@@ -823,8 +823,16 @@ int wave_step(wave_ctx *c, int nsteps) {
   return run_steps(c, nsteps);
 }
 
-int wave_propagate(wave_ctx *c, const wave_shot *shot, int nsteps,
-                   const int32_t *rec_xyz, int nrec, float *traces) {
+}  // extern "C"
+
+namespace {
+
+// The part of a propagation call before its steps: validation, receiver
+// table, wavelet and descriptor for nsteps steps from the context's step.
+// host_traces / stage: traces staged on the device for a host buffer.
+int propagate_begin(wave_ctx *c, const wave_shot *shot, int nsteps,
+                    const int32_t *rec_xyz, int nrec, float *traces, bool &host_traces,
+                    float *&stage) {
   if (!c || nsteps < 0 || nrec < 0) return WAVE_EINVAL;
   if (nrec > 0 && (!rec_xyz || !traces)) return WAVE_EINVAL;
   if (shot) {
@@ -835,6 +843,8 @@ int wave_propagate(wave_ctx *c, const wave_shot *shot, int nsteps,
         !std::isfinite(shot->amp))
       return WAVE_EINVAL;
   }
+  host_traces = false;
+  stage = nullptr;
   if (nsteps == 0) return WAVE_OK;
   cudaStream_t st = c->stream;
   int s;
@@ -847,7 +857,7 @@ int wave_propagate(wave_ctx *c, const wave_shot *shot, int nsteps,
   // the interior are left out and reported as WAVE_EINVAL by the next
   // synchronizing call.
   const bool host_rec = nrec > 0 && !is_device_ptr(rec_xyz);
-  const bool host_traces = nrec > 0 && !is_device_ptr(traces);
+  host_traces = nrec > 0 && !is_device_ptr(traces);
   if (host_rec) {
     c->h_rec_raw.resize((size_t)nrec * 3);
     for (int r = 0; r < nrec; ++r) {
@@ -879,6 +889,7 @@ int wave_propagate(wave_ctx *c, const wave_shot *shot, int nsteps,
   c->d_rec = reinterpret_cast<int4 *>(tb + o_rec);
   c->d_rec_start = reinterpret_cast<int *>(tb + o_start);
   float *d_traces_stage = reinterpret_cast<float *>(tb + o_tr);
+  stage = d_traces_stage;
   const int32_t *drec = rec_xyz;
   if (host_rec) {
     drec = reinterpret_cast<const int32_t *>(tb + o_raw);
@@ -930,7 +941,37 @@ int wave_propagate(wave_ctx *c, const wave_shot *shot, int nsteps,
       WAVE_TRY_CUDA(cudaGetLastError());
     }
   }
-  if ((s = upload_desc(c))) return s;
+  return upload_desc(c);
+}
+
+// The part after the steps: the traces' finite check and, for a host
+// buffer, their copy (which synchronizes and reports errors).
+int propagate_end(wave_ctx *c, int nsteps, int nrec, float *traces, bool host_traces,
+                  const float *stage) {
+  cudaStream_t st = c->stream;
+  if (nrec > 0) {  // NaN / infinity in the traces: WAVE_ENAN at the next sync
+    finite_check_kernel<<<c->sms * 4, 256, 0, st>>>(
+        c->host_desc.traces, (long long)nsteps * nrec, &c->d_desc->error);
+    WAVE_TRY_CUDA(cudaGetLastError());
+  }
+  if (host_traces) {
+    WAVE_TRY_CUDA(cudaMemcpyAsync(traces, stage, (size_t)nsteps * nrec * 4,
+                                  cudaMemcpyDeviceToHost, st));
+    return read_device_error(c);
+  }
+  return WAVE_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+int wave_propagate(wave_ctx *c, const wave_shot *shot, int nsteps,
+                   const int32_t *rec_xyz, int nrec, float *traces) {
+  bool host_traces;
+  float *stage;
+  int s = propagate_begin(c, shot, nsteps, rec_xyz, nrec, traces, host_traces, stage);
+  if (s || nsteps == 0) return s;
   int early = 0;
   if (c->upload_pending) {
     if (c->at_rest && shot)
@@ -940,17 +981,7 @@ int wave_propagate(wave_ctx *c, const wave_shot *shot, int nsteps,
     if (early < 0) return early;
   }
   if ((s = run_steps(c, nsteps - early))) return s;
-  if (nrec > 0) {  // NaN / infinity in the traces: WAVE_ENAN at the next sync
-    finite_check_kernel<<<c->sms * 4, 256, 0, st>>>(
-        c->host_desc.traces, (long long)nsteps * nrec, &c->d_desc->error);
-    WAVE_TRY_CUDA(cudaGetLastError());
-  }
-  if (host_traces) {
-    WAVE_TRY_CUDA(cudaMemcpyAsync(traces, d_traces_stage, (size_t)nsteps * nrec * 4,
-                                  cudaMemcpyDeviceToHost, st));
-    return read_device_error(c);
-  }
-  return WAVE_OK;
+  return propagate_end(c, nsteps, nrec, traces, host_traces, stage);
 }
 
 }  // extern "C"
@@ -1280,11 +1311,30 @@ int wave_selftest_wait(int64_t limit_ns, void *stream) {
 namespace {
 
 template <int kMode>
-void launch_mode(const wave_ctx *c, dim3 grid, const CUtensorMap &tu,
+void launch_mode(const wave_ctx *c, cudaStream_t st, dim3 grid, const CUtensorMap &tu,
                  const CUtensorMap &tup, const SweepArgs &a) {
   launch_pdl(wave_sweep_kernel<Cfg0, false, kMode>, grid, Cfg0::THREADS,
-             Cfg0::SMEM_BYTES, c->stream, tu, tup, c->tm_c, a);
+             Cfg0::SMEM_BYTES, st, tu, tup, c->tm_c, a);
 }
+
+// The backward pass's second stream and its events, released on scope exit.
+struct GradStreams {
+  cudaStream_t rs = nullptr;      // segment recomputes
+  cudaEvent_t start = nullptr;    // the backward's inputs are ready
+  cudaEvent_t rec_done[2] = {};   // recompute into D buffer slot s finished
+  cudaEvent_t adj_done[2] = {};   // adjoint steps reading slot s finished
+  ~GradStreams() {
+    if (rs) cudaStreamDestroy(rs);
+    for (cudaEvent_t e : {start, rec_done[0], rec_done[1], adj_done[0], adj_done[1]})
+      if (e) cudaEventDestroy(e);
+  }
+  int init() {
+    WAVE_TRY_CUDA(cudaStreamCreateWithFlags(&rs, cudaStreamNonBlocking));
+    for (cudaEvent_t *e : {&start, &rec_done[0], &rec_done[1], &adj_done[0], &adj_done[1]})
+      WAVE_TRY_CUDA(cudaEventCreateWithFlags(e, cudaEventDisableTiming));
+    return WAVE_OK;
+  }
+};
 
 // z-layer plan of a gradient sweep mode: the u-only stages that refill the
 // register queue weigh less against a stage that also moves D and the
@@ -1389,8 +1439,15 @@ int gradient_impl(wave_ctx *c, const wave_shot *shot, int N,
   double *gacc, *dmis;
   StepDesc *dadj, *dfwd;
   int e;
-  if ((e = mem.alloc(&ckpt, fb * 2 * ncp)) || (e = mem.alloc(&dbuf, fb * K)) ||
+  // two D buffers (slots) when there are several segments: the recompute of
+  // one segment runs beside the adjoint steps of the next. The recompute has
+  // fields (rbuf) and layer slabs of its own, so that the last segment's
+  // recompute can also run beside the forward's last segment.
+  const int nslot = ncp > 1 ? 2 : 1;
+  float *rbuf[2];
+  if ((e = mem.alloc(&ckpt, fb * 2 * ncp)) || (e = mem.alloc(&dbuf, fb * K * nslot)) ||
       (e = mem.alloc(&padj[0], fb)) || (e = mem.alloc(&padj[1], fb)) ||
+      (e = mem.alloc(&rbuf[0], fb)) || (e = mem.alloc(&rbuf[1], fb)) ||
       (e = mem.alloc(&trd, tn * 4)) || (e = mem.alloc(&res, tn * 4)) ||
       (e = mem.alloc(&inj, (tn + nrec) * 4)) || (e = mem.alloc(&wl, (size_t)N * 4)) ||
       (e = mem.alloc(&gacc, fe * 8)) || (e = mem.alloc(&dmis, 8)) ||
@@ -1399,8 +1456,10 @@ int gradient_impl(wave_ctx *c, const wave_shot *shot, int N,
       (e = mem.alloc(&dfwd, sizeof(StepDesc))))
     return e;
   // With the CPML layer: the memory variables psi, zeta (per axis) are saved
-  // with each checkpoint, and the adjoint carries its own nu, mu slabs.
+  // with each checkpoint, the recompute steps them on slabs of its own (rg),
+  // and the adjoint carries its nu, mu slabs.
   const CpmlGeom &cg = c->cg;
+  CpmlGeom rg = cg;
   size_t sl[3] = {0, 0, 0};
   float *ckpt_l = nullptr, *nus[3] = {}, *mus[3] = {};
   if (c->cpml) {
@@ -1409,56 +1468,131 @@ int gradient_impl(wave_ctx *c, const wave_shot *shot, int N,
     sl[2] = 2ull * cg.npml * c->ny * c->nx;
     if ((e = mem.alloc(&ckpt_l, (sl[0] + sl[1] + sl[2]) * 2 * 4 * ncp))) return e;
     for (int ax = 0; ax < 3; ++ax)
-      if ((e = mem.alloc(&nus[ax], sl[ax] * 4)) || (e = mem.alloc(&mus[ax], sl[ax] * 4)))
+      if ((e = mem.alloc(&nus[ax], sl[ax] * 4)) || (e = mem.alloc(&mus[ax], sl[ax] * 4)) ||
+          (e = mem.alloc(&rg.psi[ax], sl[ax] * 4)) || (e = mem.alloc(&rg.zeta[ax], sl[ax] * 4)))
         return e;
   }
-  // copies the layer's memory variables to (save) or from a checkpoint
-  auto layer_ckpt = [&](int sgm, bool save) -> int {
+  // copies the memory variables of layer slabs gg to (save) or from a
+  // checkpoint
+  auto layer_ckpt = [&](int sgm, bool save, cudaStream_t cs, const CpmlGeom &gg) -> int {
     float *q = ckpt_l + (sl[0] + sl[1] + sl[2]) * 2 * sgm;
     for (int ax = 0; ax < 3; ++ax)
-      for (float *f : {cg.psi[ax], cg.zeta[ax]}) {
+      for (float *f : {gg.psi[ax], gg.zeta[ax]}) {
         WAVE_TRY_CUDA(cudaMemcpyAsync(save ? q : f, save ? f : q, sl[ax] * 4,
-                                      cudaMemcpyDeviceToDevice, st));
+                                      cudaMemcpyDeviceToDevice, cs));
         q += sl[ax];
       }
     return WAVE_OK;
   };
-  const int mode_attr[3] = {kModeStoreD, kModeInject, kModeInject | kModeGradAcc};
+  GradStreams gs;
+  if ((e = gs.init())) return e;
   const void *fns[3] = {
       reinterpret_cast<const void *>(&wave_sweep_kernel<Cfg0, false, kModeStoreD>),
       reinterpret_cast<const void *>(&wave_sweep_kernel<Cfg0, false, kModeInject>),
       reinterpret_cast<const void *>(
           &wave_sweep_kernel<Cfg0, false, kModeInject | kModeGradAcc>)};
-  (void)mode_attr;
   for (const void *f : fns)
     WAVE_TRY_CUDA(cudaFuncSetAttribute(
         f, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)Cfg0::SMEM_BYTES));
-
-  // Receivers on the host once, so that they are validated before anything
-  // is launched (each segment's wave_propagate checks host receivers).
-  std::vector<int32_t> hrec;
-  if (nrec > 0 && is_device_ptr(rec_xyz)) {
-    hrec.resize((size_t)nrec * 3);
-    WAVE_TRY_CUDA(cudaMemcpyAsync(hrec.data(), rec_xyz, hrec.size() * 4,
-                                  cudaMemcpyDeviceToHost, st));
-    WAVE_TRY_CUDA(cudaStreamSynchronize(st));
-    rec_xyz = hrec.data();
+  // tensor maps of the adjoint fields and of the recompute's fields
+  CUtensorMap ahalo[2], atile[2], rhalo[2], rtile[2];
+  for (int b = 0; b < 2; ++b) {
+    const void *bufs[2] = {padj[b], rbuf[b]};
+    CUtensorMap *halos[2] = {&ahalo[b], &rhalo[b]}, *tiles[2] = {&atile[b], &rtile[b]};
+    for (int i = 0; i < 2; ++i) {
+      if ((e = make_map(halos[i], bufs[i], c, c->var.tx + 2 * c->var.halo_x,
+                        c->var.ty + 2 * kR, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, c->pxu, 4)))
+        return e;
+      if ((e = make_map(tiles[i], bufs[i], c, c->var.tx, c->var.ty,
+                        CU_TENSOR_MAP_DATA_TYPE_FLOAT32, c->pxu, 4)))
+        return e;
+    }
   }
 
-  // Forward run from rest with a checkpoint (u^{sK}, u^{sK-1}) per segment.
+  // Layer plans of the recompute (D stored) and adjoint sweeps. Preroll
+  // weights timed on 256^3 x 800 steps, checkpoint every 40 (wave_gradient,
+  // best of 4): 4/4 (the forward plan) 0.1864 s, 2/2 0.1827 s, 3.2/1.8
+  // 0.1866, 2/1 0.1909, 1/1 0.1907, 4/1 0.1949 (bitwise equal gradients:
+  // the plan only regroups the planes). GBWAVE_GRAD_PREROLL=d,a overrides.
+  double pre_d = 2.0, pre_a = 2.0;
+  if (const char *gp = std::getenv("GBWAVE_GRAD_PREROLL"))
+    std::sscanf(gp, "%lf,%lf", &pre_d, &pre_a);
+  SweepArgs args_d = c->args, args_a = c->args;
+  const dim3 grid_d = plan_mode(c, pre_d, args_d);
+  const dim3 grid_a = plan_mode(c, pre_a, args_a);
+
+  // Descriptor of the recompute (source, no receivers).
+  std::vector<float> hw(N, 0.f);
+  StepDesc hf{}, ha{};
+  if (shot) {
+    const double t0 = shot->t0 < 0 ? 1.0 / shot->f_peak : shot->t0;
+    for (int n = 0; n < N; ++n)
+      hw[n] = (float)ricker(n * c->dt, shot->f_peak, t0, shot->amp);
+    hf.wavelet = wl;
+    hf.src_active = 1;
+    hf.sx = shot->sx;
+    hf.sy = shot->sy;
+    hf.sz = shot->sz;
+  }
+  WAVE_TRY_CUDA(cudaMemcpyAsync(wl, hw.data(), (size_t)N * 4,
+                                cudaMemcpyHostToDevice, st));
+  WAVE_TRY_CUDA(cudaMemcpyAsync(dfwd, &hf, sizeof(hf), cudaMemcpyHostToDevice, st));
+
+  // Recompute of a segment's forward steps from its checkpoint on stream
+  // rs, keeping D^n = C L u^n + source (+ the layer's term) for n in
+  // [s0, s1) in the segment's D slot.
+  auto dslot_of = [&](int sgm) {
+    return dbuf + (size_t)(nslot == 2 ? (sgm & 1) : 0) * K * fe;
+  };
+  auto recompute = [&](int sgm, cudaStream_t rs) -> int {
+    const int s0 = sgm * K, s1 = std::min(N, s0 + K);
+    float *dslot = dslot_of(sgm);
+    WAVE_TRY_CUDA(cudaMemcpyAsync(rbuf[0], ckpt + (size_t)2 * sgm * fe, fb,
+                                  cudaMemcpyDeviceToDevice, rs));
+    WAVE_TRY_CUDA(cudaMemcpyAsync(rbuf[1], ckpt + (size_t)(2 * sgm + 1) * fe, fb,
+                                  cudaMemcpyDeviceToDevice, rs));
+    int le;
+    if (c->cpml && (le = layer_ckpt(sgm, false, rs, rg))) return le;
+    int cur = 0;
+    for (int n = s0; n < s1; ++n) {
+      SweepArgs a = args_d;
+      a.desc = dfwd;
+      a.koff = n;
+      a.unext = rbuf[cur ^ 1];
+      a.dout = dslot + (size_t)(n - s0) * fe;
+      launch_mode<kModeStoreD>(c, rs, grid_d, rhalo[cur], rtile[cur ^ 1], a);
+      if (c->cpml)  // the layer's terms, into u^{n+1} and D^n
+        launch_cpml_forward<true>(c, rg, rs, rbuf[cur], rbuf[cur ^ 1], a.dout);
+      cur ^= 1;
+    }
+    if (nslot == 2) WAVE_TRY_CUDA(cudaEventRecord(gs.rec_done[sgm & 1], rs));
+    return WAVE_OK;
+  };
+
+  // Forward run from rest, prepared once for all N steps (receiver table,
+  // wavelet, descriptor), with a checkpoint (u^{sK}, u^{sK-1}) and the
+  // layer's memory variables before each segment. The last segment's
+  // recompute starts beside the forward's last segment.
   if ((e = wave_reset(c))) return e;
+  bool host_tr;
+  float *stage;
+  if ((e = propagate_begin(c, shot, N, rec_xyz, nrec, nrec ? trd : nullptr, host_tr, stage)))
+    return e;
   for (int sgm = 0; sgm < ncp; ++sgm) {
     WAVE_TRY_CUDA(cudaMemcpyAsync(ckpt + (size_t)2 * sgm * fe, c->buf[c->cur],
                                   fb, cudaMemcpyDeviceToDevice, st));
     WAVE_TRY_CUDA(cudaMemcpyAsync(ckpt + (size_t)(2 * sgm + 1) * fe,
                                   c->buf[c->cur ^ 1], fb,
                                   cudaMemcpyDeviceToDevice, st));
-    if (c->cpml && (e = layer_ckpt(sgm, true))) return e;
-    const int len = std::min(K, N - sgm * K);
-    if ((e = wave_propagate(c, shot, len, rec_xyz, nrec,
-                            nrec ? trd + (size_t)sgm * K * nrec : nullptr)))
-      return e;
+    if (c->cpml && (e = layer_ckpt(sgm, true, st, cg))) return e;
+    if (sgm == ncp - 1 && nslot == 2) {
+      WAVE_TRY_CUDA(cudaEventRecord(gs.start, st));
+      WAVE_TRY_CUDA(cudaStreamWaitEvent(gs.rs, gs.start, 0));
+      if ((e = recompute(sgm, gs.rs))) return e;
+    }
+    if ((e = run_steps(c, std::min(K, N - sgm * K)))) return e;
   }
+  if ((e = propagate_end(c, N, nrec, nrec ? trd : nullptr, false, nullptr))) return e;
 
   // Residual (dJ/dtraces) and, for the L2 misfit, its FP64 sum.
   if (nrec > 0) {
@@ -1475,40 +1609,14 @@ int gradient_impl(wave_ctx *c, const wave_shot *shot, int N,
     WAVE_TRY_CUDA(cudaMemsetAsync(dmis, 0, 8, st));
   }
 
-  // Descriptors: forward recompute (source, no receivers) and adjoint
-  // (receiver injections, no source).
-  std::vector<float> hw(N, 0.f);
-  StepDesc hf{}, ha{};
-  if (shot) {
-    const double t0 = shot->t0 < 0 ? 1.0 / shot->f_peak : shot->t0;
-    for (int n = 0; n < N; ++n)
-      hw[n] = (float)ricker(n * c->dt, shot->f_peak, t0, shot->amp);
-    hf.wavelet = wl;
-    hf.src_active = 1;
-    hf.sx = shot->sx;
-    hf.sy = shot->sy;
-    hf.sz = shot->sz;
-  }
-  WAVE_TRY_CUDA(cudaMemcpyAsync(wl, hw.data(), (size_t)N * 4,
-                                cudaMemcpyHostToDevice, st));
+  // Descriptor of the adjoint (receiver injections, no source).
   if (nrec > 0) {
     ha.inj_val = inj;
     ha.inj = c->d_rec;  // receiver table of the forward run
     ha.inj_start = c->d_rec_start;
     ha.ninj = nrec;
   }
-  WAVE_TRY_CUDA(cudaMemcpyAsync(dfwd, &hf, sizeof(hf), cudaMemcpyHostToDevice, st));
   WAVE_TRY_CUDA(cudaMemcpyAsync(dadj, &ha, sizeof(ha), cudaMemcpyHostToDevice, st));
-  CUtensorMap ahalo[2], atile[2];
-  for (int b = 0; b < 2; ++b) {
-    if ((e = make_map(&ahalo[b], padj[b], c, c->var.tx + 2 * c->var.halo_x,
-                      c->var.ty + 2 * kR, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, c->pxu,
-                      4)))
-      return e;
-    if ((e = make_map(&atile[b], padj[b], c, c->var.tx, c->var.ty,
-                      CU_TENSOR_MAP_DATA_TYPE_FLOAT32, c->pxu, 4)))
-      return e;
-  }
   WAVE_TRY_CUDA(cudaMemsetAsync(padj[0], 0, fb, st));
   WAVE_TRY_CUDA(cudaMemsetAsync(padj[1], 0, fb, st));
   WAVE_TRY_CUDA(cudaMemsetAsync(gacc, 0, fe * 8, st));
@@ -1523,17 +1631,6 @@ int gradient_impl(wave_ctx *c, const wave_shot *shot, int N,
   // p^{k+2}; with kModeGradAcc it adds p^{k+1} D^k to the double-float
   // partial, which is folded into the FP64 sum after every step k that is
   // a multiple of kGradFold (the last fold is after k = 0).
-  // Layer plans of the recompute (D stored) and adjoint sweeps. Preroll
-  // weights timed on 256^3 x 800 steps, checkpoint every 40 (wave_gradient,
-  // best of 4): 4/4 (the forward plan) 0.1864 s, 2/2 0.1827 s, 3.2/1.8
-  // 0.1866, 2/1 0.1909, 1/1 0.1907, 4/1 0.1949 (bitwise equal gradients:
-  // the plan only regroups the planes). GBWAVE_GRAD_PREROLL=d,a overrides.
-  double pre_d = 2.0, pre_a = 2.0;
-  if (const char *gp = std::getenv("GBWAVE_GRAD_PREROLL"))
-    std::sscanf(gp, "%lf,%lf", &pre_d, &pre_a);
-  SweepArgs args_d = c->args, args_a = c->args;
-  const dim3 grid_d = plan_mode(c, pre_d, args_d);
-  const dim3 grid_a = plan_mode(c, pre_a, args_a);
   int ca = 0;
   auto adjoint_step = [&](int k, const float *dsrc) {
     SweepArgs a = args_a;
@@ -1544,9 +1641,9 @@ int gradient_impl(wave_ctx *c, const wave_shot *shot, int N,
     a.ghi = ghi;
     a.glo = glo;
     if (dsrc)
-      launch_mode<kModeInject | kModeGradAcc>(c, grid_a, ahalo[ca], atile[ca ^ 1], a);
+      launch_mode<kModeInject | kModeGradAcc>(c, st, grid_a, ahalo[ca], atile[ca ^ 1], a);
     else
-      launch_mode<kModeInject>(c, grid_a, ahalo[ca], atile[ca ^ 1], a);
+      launch_mode<kModeInject>(c, st, grid_a, ahalo[ca], atile[ca ^ 1], a);
     if (c->cpml) {  // the layer's adjoint terms, from p^{k+1} into p^k
       const float *p1 = padj[ca];
       float *p0 = padj[ca ^ 1];
@@ -1559,31 +1656,28 @@ int gradient_impl(wave_ctx *c, const wave_shot *shot, int N,
     ca ^= 1;
   };
   adjoint_step(N, nullptr);  // p^N (no D^N term)
+  // Segments from the last: the recompute of a segment (stream gs.rs, D into
+  // slot sgm & 1) runs beside the adjoint steps of the segment after it
+  // (stream st), which read the other slot. A recompute waits for the
+  // adjoint steps that last read its slot; the adjoint steps wait for their
+  // recompute. The sweeps of one 256^3 step fill the GPU's CTA places less
+  // than once, so two chains of launches keep it busier. With one segment
+  // everything runs on st.
   for (int sgm = ncp - 1; sgm >= 0; --sgm) {
-    const int s0 = sgm * K, s1 = std::min(N, s0 + K);
-    // Recompute the segment's forward steps from its checkpoint, keeping
-    // D^n = C L u^n + source (+ the layer's term) for n in [s0, s1).
-    WAVE_TRY_CUDA(cudaMemcpyAsync(c->buf[0], ckpt + (size_t)2 * sgm * fe, fb,
-                                  cudaMemcpyDeviceToDevice, st));
-    WAVE_TRY_CUDA(cudaMemcpyAsync(c->buf[1], ckpt + (size_t)(2 * sgm + 1) * fe,
-                                  fb, cudaMemcpyDeviceToDevice, st));
-    if (c->cpml && (e = layer_ckpt(sgm, false))) return e;
-    int cur = 0;
-    for (int n = s0; n < s1; ++n) {
-      SweepArgs a = args_d;
-      a.desc = dfwd;
-      a.koff = n;
-      a.unext = c->buf[cur ^ 1];
-      a.dout = dbuf + (size_t)(n - s0) * fe;
-      launch_mode<kModeStoreD>(c, grid_d, c->tm_halo[cur], c->tm_tile[cur ^ 1], a);
-      if (c->cpml) {  // the layer's terms, into u^{n+1} and D^n
-        launch_cpml_forward<true>(c, st, (const float *)c->buf[cur], (float *)c->buf[cur ^ 1],
-                                  a.dout);
+    const int s0 = sgm * K, s1 = std::min(N, s0 + K), slot = sgm & 1;
+    if (nslot == 1) {
+      if ((e = recompute(sgm, st))) return e;
+    } else {
+      if (sgm < ncp - 1) {  // the last segment's recompute is under way
+        if (sgm + 2 < ncp) WAVE_TRY_CUDA(cudaStreamWaitEvent(gs.rs, gs.adj_done[slot], 0));
+        if ((e = recompute(sgm, gs.rs))) return e;
       }
-      cur ^= 1;
+      WAVE_TRY_CUDA(cudaStreamWaitEvent(st, gs.rec_done[slot], 0));
     }
+    float *dslot = dslot_of(sgm);
     for (int k = s1 - 1; k >= s0; --k)
-      adjoint_step(k, dbuf + (size_t)(k - s0) * fe);
+      adjoint_step(k, dslot + (size_t)(k - s0) * fe);
+    if (nslot == 2) WAVE_TRY_CUDA(cudaEventRecord(gs.adj_done[slot], st));
   }
   WAVE_TRY_CUDA(cudaGetLastError());
 
