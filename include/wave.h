@@ -284,8 +284,9 @@ int wave_selftest_wait(int64_t limit_ns, void *stream);
  * with the residuals injected at the receivers, on the same sweep kernel;
  * the forward fields come from checkpoints every ckpt_every steps, one
  * segment recomputed at a time; the time sum is accumulated in FP64 (each
- * block of 32 steps, counted from step 0, is first summed exactly as an
- * FP32 double-float pair, then added to the FP64 sum).
+ * block of 128 steps, counted from step 0, is first summed as an FP32
+ * double-float pair of about 48 significant bits, then added to the FP64
+ * sum).
  * With the CPML layer (wave_set_cpml) the forward map includes the memory
  * variables and the adjoint is that of the whole layered update: per axis
  * a, with A = the profile's a, B = its b and p^{N+1} = nu^{N+1} = mu^{N+1}
