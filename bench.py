@@ -390,29 +390,31 @@ def cpml_gradient_bytes_per_step(shape, npml):
     return 72 * npts + (2 * fwd + 8 * 2 * w + 16 * (2 * w + 2 * npml)) * lines
 
 
-def cpml_bytes_per_step(shape, npml):
+def cpml_bytes_per_step(shape, npml, esize=4):
     """Algorithmic DRAM bytes of one step with the CPML layer: the sweep's
-    16 B per point, plus per axis a and per line along a, at the 2 w = 2
-    (npml + 4) segment points u^n, C and u^{n+1} read and u^{n+1} written
-    (16 B) and at the 2 npml slab cells psi and zeta read and written (16 B)."""
+    16 B per point (10 with 16-bit fields, esize 2), plus per axis a and per
+    line along a, at the 2 w = 2 (npml + 4) segment points u^n, C and
+    u^{n+1} read and u^{n+1} written (16 B; 10 with 16-bit fields) and at the
+    2 npml slab cells psi and zeta read and written (16 B, FP32)."""
     nx, ny, nz = shape
     npts = nx * ny * nz
     w = npml + 4
     lines = npts / nx + npts / ny + npts / nz
-    return BYTES_PER_POINT * npts + 16 * (2 * w + 2 * npml) * lines
+    per_pt = 3 * esize + 4
+    return per_pt * npts + (per_pt * 2 * w + 16 * 2 * npml) * lines
 
 
 def cpml_workload(gw, torch, cfg, vel_d, dt, steps, peak_gbs, plain_ms):
     """The same grid and model stepped with the CPML layer at all six faces
-    (npml 8 and 16, R = 1e-3, f_cps = f_peak); source and receiver plane
-    moved below the top layer."""
+    (npml 8 and 16 with FP32 fields, npml 16 with FP16 fields; R = 1e-3,
+    f_cps = f_peak); source and receiver plane moved below the top layer."""
     nx, ny, nz = cfg["shape"]
     npts = nx * ny * nz
     out = {}
-    for npml in (8, 16):
+    for npml, storage in ((8, 0), (16, 0), (16, 2)):
         rec = torch.from_numpy(wl.receiver_plane(nx, ny, npml + 8, cfg["rec_stride"])).cuda()
         shot = (cfg["source"][0], cfg["source"][1], npml + 10, cfg["f_peak"], -1.0, 1.0)
-        s = gw.WaveSolver((nx, ny, nz), cfg["spacing"], dt, vel_d)
+        s = gw.WaveSolver((nx, ny, nz), cfg["spacing"], dt, vel_d, storage=storage)
         s.set_cpml(npml, 1e-3, cfg["f_peak"])
         tr = torch.empty((steps, rec.shape[0]), device="cuda")
         s.propagate(shot, min(steps, 64), rec, tr)
@@ -428,11 +430,12 @@ def cpml_workload(gw, torch, cfg, vel_d, dt, steps, peak_gbs, plain_ms):
         ms = e0.elapsed_time(e1) / steps
         ok = bool(torch.isfinite(tr).all().item())
         s.close()
-        b = cpml_bytes_per_step((nx, ny, nz), npml)
+        b = cpml_bytes_per_step((nx, ny, nz), npml, 2 if storage else 4)
         ach = b / (ms * 1e-3) / 1e9
-        out["npml%d" % npml] = {
+        out["npml%d%s" % (npml, "_f16" if storage else "")] = {
             "value": npts / (ms * 1e-3) / 1e9, "unit": "Gpts/s", "ms_per_step": ms,
-            "steps": steps, "vs_plain_step": ms / plain_ms, "traces_finite": ok,
+            "steps": steps, ("vs_plain_f32_step" if storage else "vs_plain_step"): ms / plain_ms,
+            "storage": "f16" if storage else "f32", "traces_finite": ok,
             "roofline": {"bound": "hbm", "achieved": ach, "peak": peak_gbs,
                          "unit": "GB/s", "frac": ach / peak_gbs,
                          "algorithmic_bytes_per_step": b,

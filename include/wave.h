@@ -233,7 +233,10 @@ int wave_reset(wave_ctx *ctx);
  *               1 <= npml and 2 npml <= nx, ny, nz
  *   reflection  target reflection coefficient, 0 < reflection < 1
  *   f_cps       frequency shift (Hz, >= 0), typically the source's peak
- * FP32 storage and ny, nz <= 65535 only (WAVE_ENOTSUP otherwise). The
+ * ny, nz <= 65535 only (WAVE_ENOTSUP otherwise). With 16-bit storage the
+ * layer's passes read and write the stored fields through the step's
+ * power-of-two scales (one more rounding to the format per pass at the
+ * shell points); psi and zeta stay FP32. The
  * layer's memory variables start at zero here and are zeroed by wave_reset
  * and wave_set_state. The
  * source and receivers may lie in the layer. wave_adjoint / wave_gradient

@@ -501,13 +501,18 @@ def _make_traces_function():
         the incoming gradient as dJ/dtraces, checkpointing every ``ckpt_every``
         steps. dt stays fixed, so the map m -> traces is a fixed discrete
         function; the library takes m itself (wave_create_m: v^2 dt^2 = m dt^2).
+        cpml: None, npml, or (npml, reflection, f_cps) for the CPML layer
+        (wave_set_cpml); its profile, set from the largest velocity of m, is
+        held fixed by the derivative.
         """
 
         @staticmethod
-        def forward(fctx, m, spacing, dt, shot, nsteps, rec, ckpt_every=40):
+        def forward(fctx, m, spacing, dt, shot, nsteps, rec, ckpt_every=40, cpml=None):
             nz, ny, nx = m.shape
             solver = WaveSolver((nx, ny, nz), spacing, dt,
                                 m.detach().to(torch.float32).contiguous(), squared=True)
+            if cpml is not None:
+                solver.set_cpml(*((cpml,) if isinstance(cpml, int) else tuple(cpml)))
             traces = torch.zeros((nsteps, rec.shape[0]), dtype=torch.float32, device=m.device)
             solver.propagate(shot, nsteps, rec, traces)
             solver.synchronize()
@@ -524,14 +529,14 @@ def _make_traces_function():
             solver.adjoint(shot, nsteps, rec, grad_traces.to(torch.float32).contiguous(), grad,
                            ckpt_every=ckpt)
             solver.close()
-            return grad, None, None, None, None, None, None
+            return grad, None, None, None, None, None, None, None
 
     return WaveTraces
 
 
-def wave_traces(m, spacing, dt, shot, nsteps, rec, ckpt_every=40):
+def wave_traces(m, spacing, dt, shot, nsteps, rec, ckpt_every=40, cpml=None):
     """Differentiable traces(m = v^2); see WaveTraces."""
-    return _make_traces_function().apply(m, spacing, dt, shot, nsteps, rec, ckpt_every)
+    return _make_traces_function().apply(m, spacing, dt, shot, nsteps, rec, ckpt_every, cpml)
 
 
 def __getattr__(name):

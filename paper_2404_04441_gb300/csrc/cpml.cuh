@@ -29,7 +29,9 @@
 namespace gbw {
 
 struct CpmlGeom {
-  int nx, ny, nz, px;  // grid and row pitch of the fields (floats)
+  int nx, ny, nz;
+  int px;   // row pitch of v^2 dt^2 (floats)
+  int pxu;  // row pitch of the wavefields (elements; px for FP32 storage)
   int npml, w;         // layer cells; correction width npml + 4
   float *psi[3], *zeta[3];           // slab storage per axis
   const float *bprof[3], *aprof[3];  // per-axis b, a (length n_a)
@@ -51,19 +53,101 @@ __device__ __forceinline__ int cpml_cell(int i, int n, int npml) {
 
 constexpr int kCpmlChunk = 4;  // positions per batch of loads
 
+// Wavefield elements in the layer kernels. FP32 fields are used as stored.
+// 16-bit fields (BF16 / FP16 storage) hold value / 2^e, e the exponent of
+// the time step the field holds (StepDesc::exps, chosen by the sweep that
+// wrote it): a read converts exactly and multiplies by 2^e, a write
+// multiplies by 2^-e (exact) and rounds once to the format, as the sweep's
+// stores do. v^2 dt^2, psi and zeta stay FP32.
+template <class T>
+__device__ __forceinline__ float cpml_get(const T *p, float s) {
+  if constexpr (std::is_same<T, float>::value) return *p;
+  else return to_f32(*p) * s;
+}
+
+template <class T>
+__device__ __forceinline__ void cpml_put(T *p, float v, float inv) {
+  if constexpr (std::is_same<T, float>::value) *p = v;
+  else if constexpr (std::is_same<T, __half>::value) *p = __float2half_rn(v * inv);
+  else *p = __float2bfloat16_rn(v * inv);
+}
+
+// Four consecutive elements from p (16 bytes for FP32, 8 for 16-bit; p
+// aligned to that).
+template <class T>
+__device__ __forceinline__ void cpml_get4(const T *p, float s, float *v) {
+  if constexpr (std::is_same<T, float>::value) {
+    const float4 t = *reinterpret_cast<const float4 *>(p);
+    v[0] = t.x;
+    v[1] = t.y;
+    v[2] = t.z;
+    v[3] = t.w;
+  } else {
+    const uint2 w = *reinterpret_cast<const uint2 *>(p);
+    const T *e = reinterpret_cast<const T *>(&w);
+#pragma unroll
+    for (int k = 0; k < 4; ++k) v[k] = to_f32(e[k]) * s;
+  }
+}
+
+template <class T>
+__device__ __forceinline__ void cpml_put4(T *p, const float *v, float inv) {
+  if constexpr (std::is_same<T, float>::value) {
+    *reinterpret_cast<float4 *>(p) = make_float4(v[0], v[1], v[2], v[3]);
+  } else {
+    uint2 w;
+    T *e = reinterpret_cast<T *>(&w);
+#pragma unroll
+    for (int k = 0; k < 4; ++k) cpml_put(e + k, v[k], inv);
+    *reinterpret_cast<uint2 *>(p) = w;
+  }
+}
+
+// Scales of one step's fields (16-bit storage): 2^e of u^n and of u^{n+1},
+// 2^-e of u^{n+1}, for absolute step step0 + n + koff; and the running
+// maximum of |u^{n+1}| that the next step's scale is chosen from (the
+// corrected shell values enter it). FP32: all ones, nothing read.
+template <class T>
+struct CpmlScale {
+  float su = 1.f, so = 1.f, inv_so = 1.f;
+  unsigned *maxbits = nullptr;
+  __device__ __forceinline__ void init(const StepDesc *d, int koff) {
+    if constexpr (!std::is_same<T, float>::value) {
+      const long long ab = d->step0 + d->n + koff;
+      su = exp2_int(d->exps[ab & 3]);
+      const int eo = d->exps[(ab + 1) & 3];
+      so = exp2_int(eo);
+      inv_so = exp2_int(-eo);
+      maxbits = const_cast<unsigned *>(&d->maxbits[(ab + 1) & 3]);
+    }
+  }
+  // the largest |value| the warp's remaining lanes wrote (lanes past the
+  // last line have returned), into the running maximum: non-negative floats
+  // order as their bit patterns
+  __device__ __forceinline__ void commit(float vmax) const {
+    if constexpr (!std::is_same<T, float>::value) {
+      const unsigned m = __activemask();
+      const unsigned r = __reduce_max_sync(m, __float_as_uint(vmax));
+      if ((threadIdx.x & 31) == __ffs(m) - 1 && r != 0u) atomicMax(maxbits, r);
+    }
+  }
+};
+
 // Four consecutive values of an x row from position p (p a multiple of 4,
 // the row 16-byte aligned with its padding up to a multiple of 4 in
 // bounds); positions outside [0, n) read as zero.
-__device__ __forceinline__ void cpml_row4(const float *row, int p, int n, float *v) {
+template <class T>
+__device__ __forceinline__ void cpml_row4(const T *row, int p, int n, float *v, float s) {
   if (p < 0 || p >= n) {
     v[0] = v[1] = v[2] = v[3] = 0.f;
     return;
   }
-  const float4 t = *reinterpret_cast<const float4 *>(row + p);
-  v[0] = t.x;
-  v[1] = p + 1 < n ? t.y : 0.f;
-  v[2] = p + 2 < n ? t.z : 0.f;
-  v[3] = p + 3 < n ? t.w : 0.f;
+  float t[4];
+  cpml_get4(row + p, s, t);
+  v[0] = t[0];
+  v[1] = p + 1 < n ? t[1] : 0.f;
+  v[2] = p + 2 < n ? t[2] : 0.f;
+  v[3] = p + 3 < n ? t[3] : 0.f;
 }
 
 // One kernel per axis AX (0 = x, 1 = y, 2 = z): one thread per line along
@@ -83,34 +167,50 @@ __device__ __forceinline__ void cpml_row4(const float *row, int p, int n, float 
 // kStoreD (the gradient's recompute): the same correction C (D1 psi + zeta)
 // is also added to dout, the step's forward increment D = u^{n+1} - 2u^n +
 // u^{n-1} stored by the sweep (field layout).
-template <int AX, bool kStoreD = false>
+// T: the wavefields' storage (float, or 16-bit with the step's scales read
+// from d at absolute step step0 + n + koff).
+template <int AX, class T, bool kStoreD = false>
 __global__ void __launch_bounds__(128)
-    cpml_line_kernel(CpmlGeom g, const float *__restrict__ u,
-                     float *__restrict__ unext, const float *__restrict__ c,
-                     float *__restrict__ dout = nullptr) {
+    cpml_line_kernel(CpmlGeom g, const T *__restrict__ u, T *__restrict__ unext,
+                     const float *__restrict__ c, float *__restrict__ dout,
+                     const StepDesc *d, int koff) {
+  static_assert(!kStoreD || std::is_same<T, float>::value, "D is stored for FP32 only");
   constexpr int F = kCpmlChunk;
   const int t = blockIdx.x * blockDim.x + threadIdx.x;
   const int q = blockIdx.y;  // z for x and y lines, y for z lines
   int n;
-  long long ub, us, sb, ss;  // u offset and stride; slab offset and stride
+  // field offset and stride (pitch pxu), v^2 dt^2 offset and stride (px),
+  // slab offset and stride
+  long long ub, us, cb, cs, sb, ss;
   if (AX == 0) {
     if (t >= g.ny) return;
     n = g.nx;
-    ub = ((long long)q * g.ny + t) * g.px;
+    ub = ((long long)q * g.ny + t) * g.pxu;
     us = 1;
+    cb = ((long long)q * g.ny + t) * g.px;
+    cs = 1;
     sb = (long long)q * g.ny + t;
     ss = (long long)g.nz * g.ny;
   } else {
     if (t >= g.nx) return;
     n = AX == 1 ? g.ny : g.nz;
-    ub = AX == 1 ? (long long)q * g.ny * g.px + t : (long long)q * g.px + t;
-    us = AX == 1 ? (long long)g.px : (long long)g.ny * g.px;
+    ub = AX == 1 ? (long long)q * g.ny * g.pxu + t : (long long)q * g.pxu + t;
+    us = AX == 1 ? (long long)g.pxu : (long long)g.ny * g.pxu;
+    cb = AX == 1 ? (long long)q * g.ny * g.px + t : (long long)q * g.px + t;
+    cs = AX == 1 ? (long long)g.px : (long long)g.ny * g.px;
     sb = (long long)q * g.nx + t;
     ss = AX == 1 ? (long long)g.nz * g.nx : (long long)g.ny * g.nx;
   }
-  const float *__restrict__ ul = u + ub;
-  const float *__restrict__ cl = c + ub;
-  float *__restrict__ nl = unext + ub;
+  if constexpr (std::is_same<T, float>::value) {  // FP32 storage: pxu == px
+    cb = ub;
+    cs = us;
+  }
+  CpmlScale<T> sc;
+  sc.init(d, koff);
+  float vmax = 0.f;
+  const T *__restrict__ ul = u + ub;
+  const float *__restrict__ cl = c + cb;
+  T *__restrict__ nl = unext + ub;
   float *__restrict__ dl = kStoreD ? dout + ub : nullptr;
   float *__restrict__ psi = g.psi[AX] + sb;
   float *__restrict__ zeta = g.zeta[AX] + sb;
@@ -126,10 +226,10 @@ __global__ void __launch_bounds__(128)
     float nw[F], npp[F], nzp[F], ncc[F], nun[F];
     auto load = [&](int i) {
       if (AX == 0) {
-        cpml_row4(ul, i + 8, n, nw);
+        cpml_row4(ul, i + 8, n, nw, sc.su);
         if (i + F > i0 && i < i1) {
-          cpml_row4(cl, i, n, ncc);
-          cpml_row4(nl, i, n, nun);
+          cpml_row4(cl, i, n, ncc, 1.f);
+          cpml_row4(nl, i, n, nun, sc.so);
         } else {
 #pragma unroll
           for (int f = 0; f < F; ++f) ncc[f] = nun[f] = 0.f;
@@ -145,9 +245,9 @@ __global__ void __launch_bounds__(128)
         nzp[f] = (act && cpml_in_slab(p, n, npml)) ? zeta[cpml_cell(p, n, npml) * ss] : 0.f;
         if (AX != 0) {
           const int kw = i + 8 + f;
-          nw[f] = (kw < n) ? ul[kw * us] : 0.f;
-          ncc[f] = act ? cl[p * us] : 0.f;
-          nun[f] = act ? nl[p * us] : 0.f;
+          nw[f] = (kw < n) ? cpml_get(ul + kw * us, sc.su) : 0.f;
+          ncc[f] = act ? cl[p * cs] : 0.f;
+          nun[f] = act ? cpml_get(nl + p * us, sc.so) : 0.f;
         }
       }
     };
@@ -156,12 +256,12 @@ __global__ void __launch_bounds__(128)
     int i = AX == 0 ? ((i0 - 4) & ~3) : i0 - 4;
     if (AX == 0) {
 #pragma unroll
-      for (int m = 0; m < 12; m += 4) cpml_row4(ul, i - 4 + m, n, W + m);
+      for (int m = 0; m < 12; m += 4) cpml_row4(ul, i - 4 + m, n, W + m, sc.su);
     } else {
 #pragma unroll
       for (int m = 0; m < 12; ++m) {
         const int k = i - 4 + m;
-        W[m] = (k >= 0 && k < n) ? ul[k * us] : 0.f;
+        W[m] = (k >= 0 && k < n) ? cpml_get(ul + k * us, sc.su) : 0.f;
       }
     }
 #pragma unroll
@@ -210,19 +310,21 @@ __global__ void __launch_bounds__(128)
           corr += zt;
         }
         out[f] = fmaf(cc[f], corr, un[f]);
-        if (AX != 0) nl[p * us] = out[f];
+        vmax = fmaxf(vmax, fabsf(out[f]));
+        if (AX != 0) cpml_put(nl + p * us, out[f], sc.inv_so);
         if constexpr (kStoreD) dl[p * us] = fmaf(cc[f], corr, dl[p * us]);
       }
       // x: the whole aligned batch in one store (positions outside the
-      // segment keep the value just read; this thread owns the row)
-      if (AX == 0 && i + F > i0 && i < i1)
-        *reinterpret_cast<float4 *>(nl + i) = make_float4(out[0], out[1], out[2], out[3]);
+      // segment keep the value just read, which a 16-bit write reproduces
+      // exactly; this thread owns the row)
+      if (AX == 0 && i + F > i0 && i < i1) cpml_put4(nl + i, out, sc.inv_so);
 #pragma unroll
       for (int m = 0; m < 12; ++m) W[m] = W[m + F];
 #pragma unroll
       for (int m = 0; m < 8; ++m) P[m] = P[m + F];
     }
   }
+  sc.commit(vmax);
 }
 
 // Discrete adjoint of the layer (the gradient's backward steps), in the
@@ -360,9 +462,11 @@ struct CpmlSideProf {
 // in an int), which keeps one register per offset instead of a 64-bit
 // address for each of the segment's loads and stores.
 struct CpmlSeg {
-  long long u0;  // field offset of j = 0
+  long long u0;  // field offset of j = 0 (pitch pxu)
+  long long c0;  // v^2 dt^2 offset of j = 0 (pitch px)
   long long s0;  // slab offset of j = 0
   int ustep;     // per-position field step
+  int cstep;     // per-position v^2 dt^2 step
   int sstep;     // per-cell slab step
   int n;
 };
@@ -371,66 +475,76 @@ template <int AX, int NPML>
 __device__ __forceinline__ bool cpml_seg_setup(const CpmlGeom &g, int side, CpmlSeg &sg) {
   const int t = blockIdx.x * blockDim.x + threadIdx.x;
   const int q = blockIdx.y;
-  long long ub, us, sb, ss;
+  long long ub, us, cb, cs, sb, ss;
   if (AX == 0) {
     if (t >= g.ny) return false;
     sg.n = g.nx;
-    ub = ((long long)q * g.ny + t) * g.px;
+    ub = ((long long)q * g.ny + t) * g.pxu;
     us = 1;
+    cb = ((long long)q * g.ny + t) * g.px;
+    cs = 1;
     sb = (long long)q * g.ny + t;
     ss = (long long)g.nz * g.ny;
   } else {
     if (t >= g.nx) return false;
     sg.n = AX == 1 ? g.ny : g.nz;
-    ub = AX == 1 ? (long long)q * g.ny * g.px + t : (long long)q * g.px + t;
-    us = AX == 1 ? (long long)g.px : (long long)g.ny * g.px;
+    ub = AX == 1 ? (long long)q * g.ny * g.pxu + t : (long long)q * g.pxu + t;
+    us = AX == 1 ? (long long)g.pxu : (long long)g.ny * g.pxu;
+    cb = AX == 1 ? (long long)q * g.ny * g.px + t : (long long)q * g.px + t;
+    cs = AX == 1 ? (long long)g.px : (long long)g.ny * g.px;
     sb = (long long)q * g.nx + t;
     ss = AX == 1 ? (long long)g.nz * g.nx : (long long)g.ny * g.nx;
   }
   // the high face's slab cell of position j is 2 npml - 1 - j
   sg.u0 = side ? ub + (long long)(sg.n - 1) * us : ub;
   sg.ustep = (int)(side ? -us : us);
+  sg.c0 = side ? cb + (long long)(sg.n - 1) * cs : cb;
+  sg.cstep = (int)(side ? -cs : cs);
   sg.s0 = side ? sb + (long long)(2 * NPML - 1) * ss : sb;
   sg.sstep = (int)(side ? -ss : ss);
   return true;
 }
 
-// W = NPML + 4 values of a field along the segment, v[j] = f(position j).
-// x lines are rows: read as float4 when the segment starts on a 16-byte
-// boundary (the low face always; the high face when n is a multiple of 4).
-template <int AX, int W, int SIDE>
-__device__ __forceinline__ void cpml_seg_load(const float *f, const CpmlSeg &sg, float *v) {
-  if (AX == 0 && (SIDE == 0 || (sg.n & 3) == 0)) {
-    const float *r = SIDE == 0 ? f + sg.u0 : f + sg.u0 - (W - 1);
+// W = NPML + 4 values of a field along the segment, v[j] = f(position j)
+// (base: offset of j = 0, step: per position), times s (16-bit fields).
+// x lines are rows: read as 4-element vectors when the segment starts on a
+// vector boundary (the low face always; the high face when n is a multiple
+// of 4).
+template <int AX, int W, int SIDE, class T>
+__device__ __forceinline__ void cpml_seg_load(const T *f, long long base, int step, int n,
+                                              float s, float *v) {
+  if (AX == 0 && (SIDE == 0 || (n & 3) == 0)) {
+    const T *r = SIDE == 0 ? f + base : f + base - (W - 1);
 #pragma unroll
     for (int k = 0; k < W; k += 4) {
-      const float4 t = *reinterpret_cast<const float4 *>(r + k);
-      const float e[4] = {t.x, t.y, t.z, t.w};
+      float e[4];
+      cpml_get4(r + k, s, e);
 #pragma unroll
       for (int m = 0; m < 4; ++m) v[SIDE == 0 ? k + m : W - 1 - (k + m)] = e[m];
     }
   } else {
-    const float *r = f + sg.u0;
+    const T *r = f + base;
 #pragma unroll
-    for (int j = 0; j < W; ++j) v[j] = r[j * sg.ustep];
+    for (int j = 0; j < W; ++j) v[j] = cpml_get(r + j * step, s);
   }
 }
 
-template <int AX, int W, int SIDE>
-__device__ __forceinline__ void cpml_seg_store(float *f, const CpmlSeg &sg, const float *v) {
-  if (AX == 0 && (SIDE == 0 || (sg.n & 3) == 0)) {
-    float *r = SIDE == 0 ? f + sg.u0 : f + sg.u0 - (W - 1);
+template <int AX, int W, int SIDE, class T>
+__device__ __forceinline__ void cpml_seg_store(T *f, long long base, int step, int n,
+                                               float inv, const float *v) {
+  if (AX == 0 && (SIDE == 0 || (n & 3) == 0)) {
+    T *r = SIDE == 0 ? f + base : f + base - (W - 1);
 #pragma unroll
     for (int k = 0; k < W; k += 4) {
       float e[4];
 #pragma unroll
       for (int m = 0; m < 4; ++m) e[m] = v[SIDE == 0 ? k + m : W - 1 - (k + m)];
-      *reinterpret_cast<float4 *>(r + k) = make_float4(e[0], e[1], e[2], e[3]);
+      cpml_put4(r + k, e, inv);
     }
   } else {
-    float *r = f + sg.u0;
+    T *r = f + base;
 #pragma unroll
-    for (int j = 0; j < W; ++j) r[j * sg.ustep] = v[j];
+    for (int j = 0; j < W; ++j) cpml_put(r + j * step, v[j], inv);
   }
 }
 
@@ -465,15 +579,18 @@ __device__ __forceinline__ float cpml_seg_d2(const float *v, int j, const float 
   return d;
 }
 
-template <int AX, int NPML, bool kStoreD, int SIDE>
+template <int AX, int NPML, class T, bool kStoreD, int SIDE>
 __device__ __forceinline__ void cpml_seg_forward(const CpmlGeom &g, const CpmlSideProf<NPML> &pf,
-                                                  const float *__restrict__ u,
-                                                  float *__restrict__ unext,
-                                                  const float *__restrict__ c,
-                                                  float *__restrict__ dout) {
+                                                 const T *__restrict__ u,
+                                                 T *__restrict__ unext,
+                                                 const float *__restrict__ c,
+                                                 float *__restrict__ dout,
+                                                 const StepDesc *d, int koff) {
   constexpr int W = NPML + 4;
   CpmlSeg sg;
   if (!cpml_seg_setup<AX, NPML>(g, SIDE, sg)) return;
+  CpmlScale<T> sc;
+  sc.init(d, koff);
   float *psi = g.psi[AX] + sg.s0;
   float *zeta = g.zeta[AX] + sg.s0;
   // Two phases, each issuing all of its loads before its first store (the
@@ -483,7 +600,7 @@ __device__ __forceinline__ void cpml_seg_forward(const CpmlGeom &g, const CpmlSi
   // second phase's loads wait behind the slab stores once per thread, and
   // the live set stays about half of what one phase would hold.
   float U[W], PS[NPML], ZT[NPML], CORR[W];
-  cpml_seg_load<AX, W, SIDE>(u, sg, U);
+  cpml_seg_load<AX, W, SIDE>(u, sg.u0, sg.ustep, sg.n, sc.su, U);
 #pragma unroll
   for (int j = 0; j < NPML; ++j) {
     PS[j] = psi[j * sg.sstep];
@@ -510,27 +627,36 @@ __device__ __forceinline__ void cpml_seg_forward(const CpmlGeom &g, const CpmlSi
     zeta[j * sg.sstep] = ZT[j];
   }
   float CC[W], UN[W], DO[kStoreD ? W : 1];
-  cpml_seg_load<AX, W, SIDE>(c, sg, CC);
-  cpml_seg_load<AX, W, SIDE>(unext, sg, UN);
-  if constexpr (kStoreD) cpml_seg_load<AX, W, SIDE>(dout, sg, DO);
+  if constexpr (std::is_same<T, float>::value)  // FP32 storage: pxu == px
+    cpml_seg_load<AX, W, SIDE>(c, sg.u0, sg.ustep, sg.n, 1.f, CC);
+  else
+    cpml_seg_load<AX, W, SIDE>(c, sg.c0, sg.cstep, sg.n, 1.f, CC);
+  cpml_seg_load<AX, W, SIDE>(unext, sg.u0, sg.ustep, sg.n, sc.so, UN);
+  if constexpr (kStoreD) cpml_seg_load<AX, W, SIDE>(dout, sg.u0, sg.ustep, sg.n, 1.f, DO);
+  float vmax = 0.f;
 #pragma unroll
   for (int j = 0; j < W; ++j) {
     UN[j] = fmaf(CC[j], CORR[j], UN[j]);
+    vmax = fmaxf(vmax, fabsf(UN[j]));
     if constexpr (kStoreD) DO[j] = fmaf(CC[j], CORR[j], DO[j]);
   }
-  cpml_seg_store<AX, W, SIDE>(unext, sg, UN);
-  if constexpr (kStoreD) cpml_seg_store<AX, W, SIDE>(dout, sg, DO);
+  cpml_seg_store<AX, W, SIDE>(unext, sg.u0, sg.ustep, sg.n, sc.inv_so, UN);
+  if constexpr (kStoreD) cpml_seg_store<AX, W, SIDE>(dout, sg.u0, sg.ustep, sg.n, 1.f, DO);
+  sc.commit(vmax);
 }
 
-template <int AX, int NPML, bool kStoreD = false>
+// T: the wavefields' storage (float, or 16-bit with the step's scales read
+// from d at absolute step step0 + n + koff); D is stored for FP32 only.
+template <int AX, int NPML, class T, bool kStoreD = false>
 __global__ void __launch_bounds__(128)
-    cpml_seg_kernel(CpmlGeom g, CpmlSideProf<NPML> pf, const float *__restrict__ u,
-                    float *__restrict__ unext, const float *__restrict__ c,
-                    float *__restrict__ dout = nullptr) {
+    cpml_seg_kernel(CpmlGeom g, CpmlSideProf<NPML> pf, const T *__restrict__ u,
+                    T *__restrict__ unext, const float *__restrict__ c,
+                    float *__restrict__ dout, const StepDesc *d, int koff) {
+  static_assert(!kStoreD || std::is_same<T, float>::value, "D is stored for FP32 only");
   if (blockIdx.z == 0)
-    cpml_seg_forward<AX, NPML, kStoreD, 0>(g, pf, u, unext, c, dout);
+    cpml_seg_forward<AX, NPML, T, kStoreD, 0>(g, pf, u, unext, c, dout, d, koff);
   else
-    cpml_seg_forward<AX, NPML, kStoreD, 1>(g, pf, u, unext, c, dout);
+    cpml_seg_forward<AX, NPML, T, kStoreD, 1>(g, pf, u, unext, c, dout, d, koff);
 }
 
 // The adjoint's segment form (cpml_adjoint_line_kernel, unrolled): nu and
@@ -551,7 +677,7 @@ __device__ __forceinline__ void cpml_seg_adjoint(const CpmlGeom &g, const CpmlSi
   // two phases as in the forward: p^{k+1}, nu, mu -> nu, mu and the
   // corrections; then C, p^k -> p^k updated
   float P[W], G[W], NU[NPML], MU[NPML], AN[NPML], AM[NPML], CORR[W];
-  cpml_seg_load<AX, W, SIDE>(p1, sg, P);
+  cpml_seg_load<AX, W, SIDE>(p1, sg.u0, sg.ustep, sg.n, 1.f, P);
 #pragma unroll
   for (int j = 0; j < NPML; ++j) {
     NU[j] = nu[j * sg.sstep];
@@ -585,11 +711,11 @@ __device__ __forceinline__ void cpml_seg_adjoint(const CpmlGeom &g, const CpmlSi
     mu[j * sg.sstep] = MU[j];
   }
   float CC[W], PO[W];
-  cpml_seg_load<AX, W, SIDE>(c, sg, CC);
-  cpml_seg_load<AX, W, SIDE>(p0, sg, PO);
+  cpml_seg_load<AX, W, SIDE>(c, sg.u0, sg.ustep, sg.n, 1.f, CC);  // FP32: pxu == px
+  cpml_seg_load<AX, W, SIDE>(p0, sg.u0, sg.ustep, sg.n, 1.f, PO);
 #pragma unroll
   for (int j = 0; j < W; ++j) PO[j] = fmaf(CC[j], CORR[j], PO[j]);
-  cpml_seg_store<AX, W, SIDE>(p0, sg, PO);
+  cpml_seg_store<AX, W, SIDE>(p0, sg.u0, sg.ustep, sg.n, 1.f, PO);
 }
 
 template <int AX, int NPML>
@@ -603,18 +729,23 @@ __global__ void __launch_bounds__(128)
     cpml_seg_adjoint<AX, NPML, 1>(g, pf, p1, p0, c, nus, mus);
 }
 
-// Receivers within w of a face: {x, y, z, receiver id}.
-__global__ void cpml_record_kernel(CpmlGeom g, const float *__restrict__ unext,
+// Receivers within w of a face: {x, y, z, receiver id}, recorded from the
+// field after the three axis passes (16-bit: the stored value times its
+// scale).
+template <class T>
+__global__ void cpml_record_kernel(CpmlGeom g, const T *__restrict__ unext,
                                    const StepDesc *d, const int4 *srec,
                                    const int *nsrec, int koff) {
   const int nr = *nsrec;
   if (nr == 0) return;
   const long long n = d->n + koff;
+  CpmlScale<T> sc;
+  sc.init(d, koff);
   for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < nr;
        t += gridDim.x * blockDim.x) {
     const int4 e = srec[t];
     d->traces[(size_t)n * d->nrec + e.w] =
-        unext[((size_t)e.z * g.ny + e.y) * g.px + e.x];
+        cpml_get(unext + ((size_t)e.z * g.ny + e.y) * g.pxu + e.x, sc.so);
   }
 }
 

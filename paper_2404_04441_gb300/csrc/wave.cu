@@ -252,27 +252,42 @@ void set_coeffs(wave_ctx *c) {
 
 // The layer's pass along axis AX of one forward step (dout: the layer's
 // term also into the stored increment D), and of one adjoint step.
-template <int AX, bool kD>
-void launch_cpml_axis(const wave_ctx *c, const CpmlGeom &g, cudaStream_t st, const float *u,
-                      float *un, float *dout) {
+// T: the wavefields' storage; d, koff: the step's descriptor and offset
+// (the 16-bit fields' scales).
+template <int AX, class T, bool kD>
+void launch_cpml_axis(const wave_ctx *c, const CpmlGeom &g, cudaStream_t st, const T *u,
+                      T *un, float *dout, const StepDesc *d, int koff) {
   const int inner = AX == 0 ? c->ny : c->nx, outer = AX == 2 ? c->ny : c->nz;
   const bool seg = (c->cpml_seg_axes >> AX) & 1;
   const dim3 grid((inner + 127) / 128, outer, seg ? 2 : 1);
   if (!seg)
-    cpml_line_kernel<AX, kD><<<grid, 128, 0, st>>>(g, u, un, c->c, dout);
+    cpml_line_kernel<AX, T, kD><<<grid, 128, 0, st>>>(g, u, un, c->c, dout, d, koff);
   else if (g.npml == 8)
-    cpml_seg_kernel<AX, 8, kD><<<grid, 128, 0, st>>>(g, c->prof8[AX], u, un, c->c, dout);
+    cpml_seg_kernel<AX, 8, T, kD><<<grid, 128, 0, st>>>(g, c->prof8[AX], u, un, c->c, dout, d,
+                                                        koff);
   else
-    cpml_seg_kernel<AX, 16, kD><<<grid, 128, 0, st>>>(g, c->prof16[AX], u, un, c->c, dout);
+    cpml_seg_kernel<AX, 16, T, kD><<<grid, 128, 0, st>>>(g, c->prof16[AX], u, un, c->c, dout,
+                                                         d, koff);
 }
 
 // g: the context's layer, or the same layer on other memory-variable slabs
-template <bool kD>
-void launch_cpml_forward(const wave_ctx *c, const CpmlGeom &g, cudaStream_t st, const float *u,
-                         float *un, float *dout) {
-  launch_cpml_axis<0, kD>(c, g, st, u, un, dout);
-  launch_cpml_axis<1, kD>(c, g, st, u, un, dout);
-  launch_cpml_axis<2, kD>(c, g, st, u, un, dout);
+template <class T, bool kD>
+void launch_cpml_forward(const wave_ctx *c, const CpmlGeom &g, cudaStream_t st, const T *u,
+                         T *un, float *dout, const StepDesc *d, int koff) {
+  launch_cpml_axis<0, T, kD>(c, g, st, u, un, dout, d, koff);
+  launch_cpml_axis<1, T, kD>(c, g, st, u, un, dout, d, koff);
+  launch_cpml_axis<2, T, kD>(c, g, st, u, un, dout, d, koff);
+}
+
+// One step's layer passes and shell receivers on the context's fields, in
+// their storage type.
+template <class T>
+void launch_cpml_step(const wave_ctx *c, cudaStream_t st, int cur, int koff) {
+  const T *u = static_cast<const T *>(c->buf[cur]);
+  T *un = static_cast<T *>(c->buf[cur ^ 1]);
+  launch_cpml_forward<T, false>(c, c->cg, st, u, un, nullptr, c->d_desc, koff);
+  cpml_record_kernel<T><<<c->sms, 256, 0, st>>>(c->cg, un, c->d_desc, (const int4 *)c->srec.p,
+                                               c->d_nsrec, koff);
 }
 
 template <int AX>
@@ -300,12 +315,12 @@ void enqueue_step(wave_ctx *c, cudaStream_t st, int cur, int koff) {
   a.koff = koff;
   c->var.launch(c->grid, st, c->tm_halo[cur], c->tm_tile[cur ^ 1], c->tm_c, a);
   if (c->cpml) {
-    const float *u = (const float *)c->buf[cur];
-    float *un = (float *)c->buf[cur ^ 1];
-    const CpmlGeom &g = c->cg;
-    launch_cpml_forward<false>(c, g, st, u, un, nullptr);
-    cpml_record_kernel<<<c->sms, 256, 0, st>>>(g, un, c->d_desc,
-                                               (const int4 *)c->srec.p, c->d_nsrec, koff);
+    if (c->storage == WAVE_STORAGE_BF16)
+      launch_cpml_step<__nv_bfloat16>(c, st, cur, koff);
+    else if (c->storage == WAVE_STORAGE_F16)
+      launch_cpml_step<__half>(c, st, cur, koff);
+    else
+      launch_cpml_step<float>(c, st, cur, koff);
   }
 }
 
@@ -1175,9 +1190,8 @@ int wave_set_cpml(wave_ctx *c, int npml, double R, double f_cps) {
     if (2 * npml > std::min(c->nx, std::min(c->ny, c->nz)) || !(R > 0.0 && R < 1.0) ||
         !(f_cps >= 0.0) || !std::isfinite(f_cps))
       return WAVE_EINVAL;
-    // FP32 fields only; the axis kernels index one grid row of blocks per y or z.
-    if (c->storage != WAVE_STORAGE_F32 || c->ny > 65535 || c->nz > 65535)
-      return WAVE_ENOTSUP;
+    // the axis kernels index one grid row of blocks per y or z
+    if (c->ny > 65535 || c->nz > 65535) return WAVE_ENOTSUP;
     WAVE_TRY_CUDA(cudaStreamSynchronize(c->stream));
     free_cpml(c);
     CpmlGeom &g = c->cg;
@@ -1185,6 +1199,7 @@ int wave_set_cpml(wave_ctx *c, int npml, double R, double f_cps) {
     g.ny = c->ny;
     g.nz = c->nz;
     g.px = c->px;
+    g.pxu = c->pxu;
     g.npml = npml;
     g.w = npml + 4;
     const size_t sl[3] = {2ull * npml * c->ny * c->nz, 2ull * npml * c->nz * c->nx,
@@ -1230,7 +1245,8 @@ int wave_set_cpml(wave_ctx *c, int npml, double R, double f_cps) {
       // everywhere (the two give bitwise equal results).
       const char *gen = std::getenv("GBWAVE_CPML_GENERIC");
       // field and slab steps along the axis (the kernels' 32-bit offsets)
-      const long long fstep[3] = {1, c->px, (long long)c->ny * c->px};
+      // (the wavefields' pitch, which is at least that of v^2 dt^2)
+      const long long fstep[3] = {1, c->pxu, (long long)c->ny * c->pxu};
       const long long sstep[3] = {(long long)c->nz * c->ny, (long long)c->nz * c->nx,
                                   (long long)c->ny * c->nx};
       if ((npml == 8 || npml == 16) && dims[ax] >= 2 * (npml + 4) &&
@@ -1567,7 +1583,8 @@ int gradient_impl(wave_ctx *c, const wave_shot *shot, int N,
       a.dout = dslot + (size_t)(n - s0) * fe;
       launch_mode<kModeStoreD>(c, rs, grid_d, rhalo[cur], rtile[cur ^ 1], a);
       if (c->cpml)  // the layer's terms, into u^{n+1} and D^n
-        launch_cpml_forward<true>(c, rg, rs, rbuf[cur], rbuf[cur ^ 1], a.dout);
+        launch_cpml_forward<float, true>(c, rg, rs, rbuf[cur], rbuf[cur ^ 1], a.dout, nullptr,
+                                         0);
       cur ^= 1;
     }
     if (nslot == 2) WAVE_TRY_CUDA(cudaEventRecord(gs.rec_done[sgm & 1], rs));

@@ -217,7 +217,7 @@ def test_switching_off_and_reset(wave_lib):
         s.close()
 
 
-def test_invalid_and_unsupported(wave_lib):
+def test_invalid_arguments(wave_lib):
     import torch
     E = wave_lib.WaveError
     nx, ny, nz = 24, 20, 16
@@ -234,13 +234,66 @@ def test_invalid_and_unsupported(wave_lib):
         s.set_cpml(8, 1e-3, 15.0)  # 2 npml == nz: allowed
     finally:
         s.close()
-    h = wave_lib.WaveSolver((nx, ny, nz), sp, dt, vel, storage=2)
-    try:
-        with pytest.raises(E) as ei:
-            h.set_cpml(4)
-        assert ei.value.code == -8
-    finally:
-        h.close()
+
+
+# 16-bit storage with the layer: the axis passes read and write the stored
+# fields through the step's power-of-two scales (one extra rounding per pass
+# at the shell points, up to three at corners) and keep psi, zeta in FP32.
+STORAGE16 = {"bf16": 1, "f16": 2}
+EPS16 = {"bf16": 2.0 ** -8, "f16": 2.0 ** -11}
+
+
+@pytest.mark.parametrize("mode", ["bf16", "f16"])
+@pytest.mark.parametrize("shape,npml", [((75, 52, 44), 8), ((70, 37, 23), 5), ((72, 41, 40), 16)])
+def test_16bit_storage_with_the_layer(wave_lib, oracle_mod, monkeypatch, mode, shape, npml):
+    """Against the oracle's layered run from the state as stored, within
+    12 EPS sqrt(n): twice the plain 16-bit short-run bound, for the shell
+    points' extra roundings; and the unrolled segment kernels (npml 8 and 16)
+    equal the line walks bit for bit in 16-bit storage too."""
+    import torch
+    nx, ny, nz = shape
+    sp = (10.0, 12.0, 9.0)
+    rng = np.random.default_rng(nx + npml)
+    vel = rng.uniform(1500.0, 4000.0, size=(nz, ny, nx)).astype(np.float32)
+    u0, up0 = wl.random_state((nz, ny, nx), seed=ny)
+    dt = 0.45 * wave_lib.wave_cfl_dt(sp, float(vel.max()))
+    shot = (nx // 3, ny - 4, 3, 20.0, -1.0, 1e2)
+    rec = shell_receivers(nx, ny, nz, npml + 4)
+    n, R, fcps = 25, 1e-3, 15.0
+
+    def run():
+        s = wave_lib.WaveSolver((nx, ny, nz), sp, dt, torch.from_numpy(vel).cuda(),
+                                storage=STORAGE16[mode])
+        try:
+            s.set_cpml(npml, R, fcps)
+            s.set_state(u0, up0, 4)
+            su = np.empty((nz, ny, nx), np.float32)
+            sup = np.empty((nz, ny, nx), np.float32)
+            s.get_field(0, su)
+            s.get_field(1, sup)
+            tr = torch.zeros((n, rec.shape[0]), device="cuda")
+            s.propagate(shot, n, torch.from_numpy(rec).cuda(), tr)
+            u = np.empty((nz, ny, nx), np.float32)
+            s.get_field(0, u)
+            s.synchronize()
+            return su, sup, u, tr.cpu().numpy()
+        finally:
+            s.close()
+
+    su, sup, u, tr = run()
+    if npml in (8, 16):
+        monkeypatch.setenv("GBWAVE_CPML_GENERIC", "1")
+        _, _, gu, gtr = run()
+        monkeypatch.delenv("GBWAVE_CPML_GENERIC")
+        assert np.array_equal(u, gu) and np.array_equal(tr, gtr)
+    ou, _, _, _, otr = oracle_mod.propagate_cpml(vel, sp, dt, n, npml, R=R, fcps=fcps,
+                                                 u=su, u_prev=sup, step0=4, source=shot,
+                                                 receivers=rec)
+    tol = 12 * EPS16[mode] * np.sqrt(n)
+    eu, et = rel_l2(u, ou), rel_l2(tr, otr)
+    print("\n16-bit %s CPML %s npml %d: field %.3e traces %.3e (bound %.3e)"
+          % (mode, shape, npml, eu, et, tol))
+    assert eu <= tol and et <= tol
 
 
 def _sub_box_cpml(oracle_mod, vel, u0, up0, sp, dt, n, p, shot, npml, R, fcps, vmax):

@@ -183,3 +183,40 @@ def test_cpml_full_size_directional_derivative(wave_lib):
               "FD(1e-3) %.6g" % (name, j0, dot, f1, f2))
         assert f1 == pytest.approx(f2, rel=2e-3)
         assert dot == pytest.approx(f1, rel=1e-3)
+
+
+def test_autograd_with_the_layer(wave_lib, oracle_mod):
+    """wave_traces(m, ..., cpml=(npml, R, f_cps)) under torch.autograd: the
+    misfit and dJ/dm equal the oracle's layered run and adjoint within the
+    gradient bar, and wave_gradient on the same velocities within 1e-4 (the
+    library squares v in FP32 there)."""
+    import torch
+    cfg = wl.CFG_GRAD_SMALL
+    nx, ny, nz = 32, 32, 32
+    npml = 6
+    sp = cfg["spacing"]
+    n = cfg["nsteps"]
+    true = wl.anomaly_model(nx, ny, nz, seed=cfg["seed"], anomaly=cfg["anomaly_mps"])
+    start = wl.smoothed_start(true)
+    rec = wl.receiver_plane(nx, ny, 4, 2)
+    shot = (nx // 2, ny // 3, 3, 25.0, -1.0, 1e3)
+    dt = 0.5 * wave_lib.wave_cfl_dt(sp, max(float(true.max()), float(start.max())) * 1.02)
+    _, _, _, _, obs = oracle_mod.propagate_cpml(true, sp, dt, n, npml, R=R, fcps=FCPS,
+                                                source=shot, receivers=rec)
+    obs32 = torch.from_numpy(obs.astype(np.float32)).cuda()
+    m = torch.from_numpy(start.astype(np.float32)).cuda() ** 2
+    m.requires_grad_(True)
+    tr = wave_lib.wave_traces(m, sp, dt, shot, n, torch.from_numpy(rec).cuda(), ckpt_every=7,
+                              cpml=(npml, R, FCPS))
+    loss = 0.5 * ((tr.double() - obs32.double()) ** 2).sum()
+    (gm,) = torch.autograd.grad(loss, m)
+    vmax = float(start.max())
+    _, _, _, _, otr = oracle_mod.propagate_cpml(start, sp, dt, n, npml, R=R, fcps=FCPS,
+                                                vmax=vmax, source=shot, receivers=rec)
+    og = oracle_mod.gradient_cpml(start, sp, dt, n, npml, shot, rec, otr - obs, R=R,
+                                  fcps=FCPS, vmax=vmax)
+    assert float(loss.detach()) == pytest.approx(0.5 * float(np.sum((otr - obs) ** 2)),
+                                                 rel=1e-4)
+    assert rel_l2(gm.cpu().numpy(), og) <= 2e-4
+    _, g, _ = _gpu(wave_lib, start, sp, dt, npml, shot, n, rec, obs.astype(np.float32), 7)
+    assert rel_l2(gm.cpu().numpy(), g) <= 1e-4
