@@ -19,7 +19,12 @@
  *
  * Memory: each admitted shot holds its wavefields (2 fields, FP32 or 16-bit),
  * v^2 dt^2 (FP32), and its tables (source wavelet, receiver table, and a
- * trace staging buffer when `traces` is host memory). Admission is first in,
+ * trace staging buffer when `traces` is host memory); a shot with the CPML
+ * layer also holds the layer's memory variables (psi, zeta in FP32 slabs of
+ * 2 npml cells per axis) and profiles, the profile set from that shot's
+ * largest velocity and time step. After each batched step, the layered
+ * shots of a storage type take their layer passes in one launch per axis
+ * and their shell receivers in one more. Admission is first in,
  * first out: the head request waits until its bytes fit in the budget next to
  * the resident shots, a slot is free, and one batched step over the resident
  * shots and it would launch no more than six waves of CTAs (four per SM),
@@ -51,6 +56,11 @@ typedef struct {
   int nrec;             /* >= 0 */
   float *traces;        /* nsteps*nrec float32, host or device, caller-owned;
                            complete when the request completes */
+  int npml;             /* CPML layer cells per face (wave_set_cpml's layer);
+                           0: none, else 2 npml <= nx, ny, nz and ny, nz <=
+                           65535 */
+  double reflection;    /* the layer's target reflection, 0 < R < 1 */
+  double f_cps;         /* the layer's frequency shift (Hz, >= 0) */
 } wave_request;
 
 typedef struct {

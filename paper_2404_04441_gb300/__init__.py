@@ -55,7 +55,8 @@ class _Request(ctypes.Structure):
     _fields_ = [("grid", _Grid), ("spacing", _Spacing), ("dt", ctypes.c_double),
                 ("velocity", ctypes.c_void_p), ("storage", ctypes.c_int), ("shot", _Shot),
                 ("nsteps", ctypes.c_int), ("rec_xyz", ctypes.c_void_p), ("nrec", ctypes.c_int),
-                ("traces", ctypes.c_void_p)]
+                ("traces", ctypes.c_void_p), ("npml", ctypes.c_int),
+                ("reflection", ctypes.c_double), ("f_cps", ctypes.c_double)]
 
 
 class _Result(ctypes.Structure):
@@ -436,8 +437,16 @@ class ShotServer:
         self._keep = {}
 
     def submit(self, grid, spacing, velocity, shot, nsteps, rec=None, traces=None,
-               storage=0, dt=0.0):
+               storage=0, dt=0.0, cpml=None):
+        """cpml: None, npml, or (npml, reflection, f_cps): the shot's CPML
+        layer (reflection 1e-3 and f_cps 15 Hz when only npml is given)."""
         nx, ny, nz = map(int, grid)
+        if cpml is None:
+            npml, refl, fcps = 0, 1e-3, 15.0
+        elif isinstance(cpml, int):
+            npml, refl, fcps = cpml, 1e-3, 15.0
+        else:
+            npml, refl, fcps = cpml
         nrec = 0 if rec is None else int(rec.shape[0])
         if any(type(a).__module__.startswith("torch") and a.is_cuda
                for a in (velocity, rec, traces) if a is not None):
@@ -450,7 +459,8 @@ class ShotServer:
             _Shot(int(sx), int(sy), int(sz), float(f), -1.0 if t0 is None else float(t0),
                   float(amp)),
             int(nsteps), _ptr(rec, "int32", 3 * nrec, "rec") if nrec else None, nrec,
-            _ptr(traces, "float32", int(nsteps) * nrec, "traces") if nrec else None)
+            _ptr(traces, "float32", int(nsteps) * nrec, "traces") if nrec else None,
+            int(npml), float(refl), float(fcps))
         ticket = ctypes.c_uint64()
         _check(load().serve_submit(self.handle, ctypes.byref(req), ctypes.byref(ticket)),
                "serve_submit")

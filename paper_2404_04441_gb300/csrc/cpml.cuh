@@ -22,8 +22,11 @@
 // no race. Receivers within w of a face are then re-recorded.
 #pragma once
 
+#include <algorithm>
+#include <cmath>
 #include <cstdint>
 
+#include "common.cuh"
 #include "sweep.cuh"
 
 namespace gbw {
@@ -38,6 +41,42 @@ struct CpmlGeom {
   float c2[3][5];  // D2 weights / h_a^2 (index 0: centre)
   float c1[3][5];  // D1 weights / h_a (index 1..4)
 };
+
+// The layer's profile along one axis of n cells (npml layer cells at each
+// end), computed in FP64 and stored FP32: b = exp(-(d + alpha) dt) and
+// a = d / (d + alpha) (b - 1), with d = d0 xi^2, d0 = 3 vmax ln(1/R) /
+// (2 npml h), alpha = pi f_cps (1 - xi) and xi in (0, 1] the depth into the
+// layer (1 at the face); b = 1 and a = 0 outside the layer.
+inline void cpml_profile(int n, int npml, double R, double f_cps, double vmax, double h,
+                         double dt, float *b, float *a) {
+  const double pi = 3.14159265358979323846;
+  const double d0 = 3.0 * vmax * std::log(1.0 / R) / (2.0 * npml * h);
+  for (int i = 0; i < n; ++i) {
+    double xi = 0.0;
+    if (i < npml) xi = (double)(npml - i) / npml;
+    if (i >= n - npml) xi = std::max(xi, (double)(i - (n - npml - 1)) / npml);
+    if (xi <= 0.0) {
+      b[i] = 1.f;
+      a[i] = 0.f;
+      continue;
+    }
+    const double dd = d0 * xi * xi, al = pi * f_cps * (1.0 - xi);
+    const double bb = std::exp(-(dd + al) * dt);
+    b[i] = (float)bb;
+    a[i] = (float)(dd + al > 0.0 ? dd / (dd + al) * (bb - 1.0) : 0.0);
+  }
+}
+
+// The layer's D2 (Eq. 1's axis part) and D1 weights along axis ax of
+// spacing h.
+inline void cpml_axis_coefs(CpmlGeom &g, int ax, double h) {
+  g.c2[ax][0] = (float)(kW[0] / (h * h));
+  g.c1[ax][0] = 0.f;
+  for (int m = 1; m <= 4; ++m) {
+    g.c2[ax][m] = (float)(kW[m] / (h * h));
+    g.c1[ax][m] = (float)(kW1[m] / h);
+  }
+}
 
 // Slab storage, cell-major: cell in [0, 2 npml) counts the low slab's npml
 // cells, then the high slab's; the x slabs hold ((cell nz + z) ny + y), the y
@@ -168,16 +207,16 @@ __device__ __forceinline__ void cpml_row4(const T *row, int p, int n, float *v, 
 // is also added to dout, the step's forward increment D = u^{n+1} - 2u^n +
 // u^{n-1} stored by the sweep (field layout).
 // T: the wavefields' storage (float, or 16-bit with the step's scales read
-// from d at absolute step step0 + n + koff).
-template <int AX, class T, bool kStoreD = false>
-__global__ void __launch_bounds__(128)
-    cpml_line_kernel(CpmlGeom g, const T *__restrict__ u, T *__restrict__ unext,
-                     const float *__restrict__ c, float *__restrict__ dout,
-                     const StepDesc *d, int koff) {
+// from d at absolute step step0 + n + koff). The walk of line t (index
+// across the lines) in row q of lines (z for x and y lines, y for z lines).
+template <int AX, class T, bool kStoreD>
+__device__ __forceinline__ void cpml_line_walk(const CpmlGeom &g, int t, int q,
+                                               const T *__restrict__ u, T *__restrict__ unext,
+                                               const float *__restrict__ c,
+                                               float *__restrict__ dout, const StepDesc *d,
+                                               int koff) {
   static_assert(!kStoreD || std::is_same<T, float>::value, "D is stored for FP32 only");
   constexpr int F = kCpmlChunk;
-  const int t = blockIdx.x * blockDim.x + threadIdx.x;
-  const int q = blockIdx.y;  // z for x and y lines, y for z lines
   int n;
   // field offset and stride (pitch pxu), v^2 dt^2 offset and stride (px),
   // slab offset and stride
@@ -325,6 +364,78 @@ __global__ void __launch_bounds__(128)
     }
   }
   sc.commit(vmax);
+}
+
+template <int AX, class T, bool kStoreD = false>
+__global__ void __launch_bounds__(128)
+    cpml_line_kernel(CpmlGeom g, const T *__restrict__ u, T *__restrict__ unext,
+                     const float *__restrict__ c, float *__restrict__ dout,
+                     const StepDesc *d, int koff) {
+  cpml_line_walk<AX, T, kStoreD>(g, blockIdx.x * blockDim.x + threadIdx.x, blockIdx.y, u,
+                                 unext, c, dout, d, koff);
+}
+
+// One served shot's layer in the shot server's batched layer launches: its
+// geometry and slabs, fields, descriptor, shell receivers, step bookkeeping
+// (batch step b0 is the shot's step 0, as in the batched sweep), and its
+// first block in each axis launch (a 1D grid that concatenates the shots'
+// blocks: ceil(lines across / 128) per row of lines).
+struct CpmlBatchShot {
+  CpmlGeom g;
+  void *buf[2];  // buf[0] holds the shot's step 0
+  const float *c;
+  const StepDesc *desc;
+  const int4 *srec;  // receivers within w of a face: {x, y, z, id}
+  int nsrec;
+  long long b0;
+  int nsteps;
+  int blk_begin[3];
+};
+
+__device__ __forceinline__ int cpml_batch_find(const CpmlBatchShot *shots, int nshots, int ax,
+                                               int blk) {
+  int lo = 0, hi = nshots - 1;
+  while (lo < hi) {
+    const int mid = (lo + hi + 1) >> 1;
+    if (shots[mid].blk_begin[ax] <= blk) lo = mid; else hi = mid - 1;
+  }
+  return lo;
+}
+
+// The axis-AX pass of batch step k over every shot of the table (line walks;
+// shots outside their steps return at once).
+template <int AX, class T>
+__global__ void __launch_bounds__(128)
+    cpml_line_batched_kernel(const CpmlBatchShot *__restrict__ shots, int nshots, long long k) {
+  const CpmlBatchShot &sh = shots[cpml_batch_find(shots, nshots, AX, blockIdx.x)];
+  const long long n = k - sh.b0;
+  if (n < 0 || n >= sh.nsteps) return;
+  const int cur = (int)(n & 1);
+  const int across = AX == 0 ? sh.g.ny : sh.g.nx;
+  const int bpr = (across + 127) / 128;  // blocks per row of lines
+  const int local = blockIdx.x - sh.blk_begin[AX];
+  const int q = local / bpr;
+  const int t = (local - q * bpr) * 128 + threadIdx.x;
+  cpml_line_walk<AX, T, false>(sh.g, t, q, static_cast<const T *>(sh.buf[cur]),
+                               static_cast<T *>(sh.buf[cur ^ 1]), sh.c, nullptr, sh.desc,
+                               (int)n);
+}
+
+// Shell receivers of batch step k, one block per shot.
+template <class T>
+__global__ void cpml_record_batched_kernel(const CpmlBatchShot *__restrict__ shots, long long k) {
+  const CpmlBatchShot &sh = shots[blockIdx.x];
+  const long long n = k - sh.b0;
+  if (n < 0 || n >= sh.nsteps || sh.nsrec == 0) return;
+  const StepDesc *d = sh.desc;
+  CpmlScale<T> sc;
+  sc.init(d, (int)n);
+  const T *un = static_cast<const T *>(sh.buf[(n & 1) ^ 1]);
+  for (int r = threadIdx.x; r < sh.nsrec; r += blockDim.x) {
+    const int4 e = sh.srec[r];
+    d->traces[(size_t)(d->n + n) * d->nrec + e.w] =
+        cpml_get(un + ((size_t)e.z * sh.g.ny + e.y) * sh.g.pxu + e.x, sc.so);
+  }
 }
 
 // Discrete adjoint of the layer (the gradient's backward steps), in the

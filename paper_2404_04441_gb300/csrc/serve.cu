@@ -13,6 +13,7 @@
 
 #include "../../include/wave_serve.h"
 #include "common.cuh"
+#include "cpml.cuh"
 #include "sweep.cuh"
 
 using namespace gbw;
@@ -99,7 +100,19 @@ struct Request {
   BatchShot shot{};
   int ctas = 0;
   double points = 0;
+  // CPML layer (npml > 0): slabs, profiles, shell receivers, batch entry.
+  void *layer_mem[13] = {};
+  CpmlBatchShot layer{};
 };
+
+// Device bytes of a request's CPML layer: psi and zeta slabs of 2 npml cells
+// per axis, the per-axis profiles b and a, and the shell receiver list.
+size_t layer_bytes(const wave_request &r) {
+  if (r.npml <= 0) return 0;
+  const size_t nx = r.grid.nx, ny = r.grid.ny, nz = r.grid.nz, p = (size_t)r.npml;
+  return 2 * 2 * p * (ny * nz + nz * nx + ny * nx) * 4 + 2 * (nx + ny + nz) * 4 +
+         (size_t)r.nrec * sizeof(int4);
+}
 
 // Device bytes of a request once resident (the budget unit).
 // z layers of a batched shot: at most kLayerPlanes planes each, equal sizes.
@@ -130,6 +143,7 @@ size_t request_bytes(const wave_request &r) {
   b += round_up(nx, 4) * ny * nz * 4;               // v^2 dt^2
   b += sizeof(StepDesc) + (size_t)r.nsteps * 4;     // descriptor, wavelet
   b += (size_t)r.nrec * sizeof(int4) + (ntiles + 1) * 4;
+  b += layer_bytes(r);
   return b;  // plus a staging buffer for host traces (added at submit)
 }
 
@@ -165,6 +179,10 @@ struct serve_ctx {
   long long k = 0;  // batch steps taken
   BatchShot *d_table[kKinds] = {nullptr, nullptr, nullptr};
   std::vector<BatchShot> h_table[kKinds];
+  // layered shots per storage type: batch table and blocks per axis launch
+  CpmlBatchShot *d_layer[kKinds] = {nullptr, nullptr, nullptr};
+  std::vector<CpmlBatchShot> h_layer[kKinds];
+  int layer_blocks[kKinds][3] = {};
   std::vector<Group> groups;
   bool dirty = true;
   void *d_scan = nullptr;     // 16 bytes: velocity max, invalid count
@@ -191,6 +209,10 @@ void release(serve_ctx *s, Request *q) {
                 q->wavelet, q->rec,   q->rec_start, q->stage};
   for (void *p : ps)
     if (p) cudaFreeAsync(p, s->stream);
+  for (void *&p : q->layer_mem) {
+    if (p) cudaFreeAsync(p, s->stream);
+    p = nullptr;
+  }
   q->buf[0] = q->buf[1] = nullptr;
   q->c = nullptr;
   q->desc = nullptr;
@@ -209,6 +231,71 @@ void finish(serve_ctx *s, Request *q, int status) {
   else
     s->st.failed++;
   s->cv_done.notify_all();
+}
+
+// The CPML layer of an admitted request: zeroed memory-variable slabs,
+// profiles from the shot's largest velocity and time step (as
+// wave_set_cpml), derivative weights, and the receivers within w of a face.
+int admit_layer(serve_ctx *s, Request *q, float vmax, double dt,
+                const std::vector<int32_t> &xyz) {
+  const wave_request &r = q->r;
+  cudaStream_t st = s->stream;
+  const int nx = r.grid.nx, ny = r.grid.ny, nz = r.grid.nz, npml = r.npml;
+  CpmlBatchShot &L = q->layer;
+  CpmlGeom &g = L.g;
+  g = CpmlGeom{};
+  g.nx = nx;
+  g.ny = ny;
+  g.nz = nz;
+  g.px = (int)round_up(nx, 4);
+  g.pxu = r.storage == WAVE_STORAGE_F32 ? g.px : (int)round_up(nx, 8);
+  g.npml = npml;
+  g.w = npml + 4;
+  const size_t sl[3] = {2ull * npml * ny * nz, 2ull * npml * nz * nx, 2ull * npml * ny * nx};
+  const int dims[3] = {nx, ny, nz};
+  const double hs[3] = {r.spacing.dx, r.spacing.dy, r.spacing.dz};
+  int e, m = 0;
+  for (int ax = 0; ax < 3; ++ax) {
+    if ((e = serve_alloc(s, &q->layer_mem[m++], sl[ax] * 4)) ||
+        (e = serve_alloc(s, &q->layer_mem[m++], sl[ax] * 4)) ||
+        (e = serve_alloc(s, &q->layer_mem[m++], (size_t)dims[ax] * 4)) ||
+        (e = serve_alloc(s, &q->layer_mem[m++], (size_t)dims[ax] * 4)))
+      return e;
+    g.psi[ax] = static_cast<float *>(q->layer_mem[m - 4]);
+    g.zeta[ax] = static_cast<float *>(q->layer_mem[m - 3]);
+    g.bprof[ax] = static_cast<float *>(q->layer_mem[m - 2]);
+    g.aprof[ax] = static_cast<float *>(q->layer_mem[m - 1]);
+    WAVE_TRY_CUDA(cudaMemsetAsync(g.psi[ax], 0, sl[ax] * 4, st));
+    WAVE_TRY_CUDA(cudaMemsetAsync(g.zeta[ax], 0, sl[ax] * 4, st));
+    std::vector<float> hb(dims[ax]), ha(dims[ax]);
+    cpml_profile(dims[ax], npml, r.reflection, r.f_cps, (double)vmax, hs[ax], dt, hb.data(),
+                 ha.data());
+    WAVE_TRY_CUDA(cudaMemcpyAsync((void *)g.bprof[ax], hb.data(), dims[ax] * 4,
+                                  cudaMemcpyHostToDevice, st));
+    WAVE_TRY_CUDA(cudaMemcpyAsync((void *)g.aprof[ax], ha.data(), dims[ax] * 4,
+                                  cudaMemcpyHostToDevice, st));
+    cpml_axis_coefs(g, ax, hs[ax]);
+  }
+  // receivers within w of a face are re-recorded after the layer passes
+  std::vector<int4> shell;
+  for (int i = 0; i < r.nrec; ++i) {
+    const int x = xyz[3 * i], y = xyz[3 * i + 1], z = xyz[3 * i + 2];
+    if (x < g.w || x >= nx - g.w || y < g.w || y >= ny - g.w || z < g.w || z >= nz - g.w)
+      shell.push_back(make_int4(x, y, z, i));
+  }
+  if ((e = serve_alloc(s, &q->layer_mem[m++], shell.size() * sizeof(int4)))) return e;
+  if (!shell.empty())
+    WAVE_TRY_CUDA(cudaMemcpyAsync(q->layer_mem[m - 1], shell.data(),
+                                  shell.size() * sizeof(int4), cudaMemcpyHostToDevice, st));
+  L.buf[0] = q->buf[0];
+  L.buf[1] = q->buf[1];
+  L.c = q->c;
+  L.desc = q->desc;
+  L.srec = static_cast<const int4 *>(q->layer_mem[m - 1]);
+  L.nsrec = (int)shell.size();
+  L.b0 = q->shot.b0;
+  L.nsteps = r.nsteps;
+  return WAVE_OK;
 }
 
 // Make a queued request resident: buffers, v^2 dt^2, tables, tensor maps.
@@ -342,6 +429,7 @@ int admit(serve_ctx *s, Request *q) {
   b.nty = nty;
   q->ctas = ntiles * (int)layers.size();
   q->points = (double)nx * ny * nz;
+  if (r.npml > 0 && (e = admit_layer(s, q, vmax, dt, xyz))) return e;
   return WAVE_OK;
 }
 
@@ -379,9 +467,41 @@ int upload_tables(serve_ctx *s) {
       WAVE_TRY_CUDA(cudaMemcpyAsync(s->d_table[kd], t.data(),
                                     t.size() * sizeof(BatchShot),
                                     cudaMemcpyHostToDevice, s->stream));
+    // the layered shots of this storage type: blocks of each axis launch
+    auto &lt = s->h_layer[kd];
+    lt.clear();
+    int *nb = s->layer_blocks[kd];
+    nb[0] = nb[1] = nb[2] = 0;
+    for (Request *q : shots) {
+      if (q->r.npml <= 0) continue;
+      CpmlBatchShot L = q->layer;
+      const int nx = q->r.grid.nx, ny = q->r.grid.ny, nz = q->r.grid.nz;
+      const int rows[3] = {nz, nz, ny}, across[3] = {ny, nx, nx};
+      for (int ax = 0; ax < 3; ++ax) {
+        L.blk_begin[ax] = nb[ax];
+        nb[ax] += rows[ax] * ((across[ax] + 127) / 128);
+      }
+      lt.push_back(L);
+    }
+    if (!lt.empty())
+      WAVE_TRY_CUDA(cudaMemcpyAsync(s->d_layer[kd], lt.data(), lt.size() * sizeof(CpmlBatchShot),
+                                    cudaMemcpyHostToDevice, s->stream));
   }
   s->dirty = false;
   return WAVE_OK;
+}
+
+// The layer passes and shell receivers of batch step k over the layered
+// shots of storage type kd.
+template <class T>
+void launch_layers(serve_ctx *s, int kd, long long k) {
+  const CpmlBatchShot *t = s->d_layer[kd];
+  const int n = (int)s->h_layer[kd].size();
+  const int *nb = s->layer_blocks[kd];
+  cpml_line_batched_kernel<0, T><<<nb[0], 128, 0, s->stream>>>(t, n, k);
+  cpml_line_batched_kernel<1, T><<<nb[1], 128, 0, s->stream>>>(t, n, k);
+  cpml_line_batched_kernel<2, T><<<nb[2], 128, 0, s->stream>>>(t, n, k);
+  cpml_record_batched_kernel<T><<<n, 128, 0, s->stream>>>(t, k);
 }
 
 // Complete a resident shot whose steps are all done (stream synchronized).
@@ -468,10 +588,17 @@ void engine_main(serve_ctx *s) {
     for (Request *q : s->resident)
       K = (int)std::max<int64_t>(K, std::min<int64_t>(kMaxGroup,
                                                       q->r.nsteps - q->steps_done));
-    for (int kk = 0; kk < K && status == WAVE_OK; ++kk)
+    for (int kk = 0; kk < K && status == WAVE_OK; ++kk) {
       for (const Group &g : s->groups)
         kind_of(g.kind).launch(g.ctas, s->stream, s->d_table[g.kind] + g.first,
                                g.count, s->k + kk, g.co);
+      if (!s->h_layer[WAVE_STORAGE_F32].empty())
+        launch_layers<float>(s, WAVE_STORAGE_F32, s->k + kk);
+      if (!s->h_layer[WAVE_STORAGE_BF16].empty())
+        launch_layers<__nv_bfloat16>(s, WAVE_STORAGE_BF16, s->k + kk);
+      if (!s->h_layer[WAVE_STORAGE_F16].empty())
+        launch_layers<__half>(s, WAVE_STORAGE_F16, s->k + kk);
+    }
     cudaError_t e = cudaGetLastError();
     if (e == cudaSuccess) e = cudaStreamSynchronize(s->stream);
     if (status == WAVE_OK && e != cudaSuccess) status = cuda_status(e);
@@ -525,6 +652,14 @@ int validate_request(const wave_request *r) {
       sh.sz < 0 || sh.sz >= r->grid.nz || !finite_pos(sh.f_peak) ||
       !std::isfinite(sh.t0) || !std::isfinite(sh.amp))
     return WAVE_EINVAL;
+  if (r->npml < 0) return WAVE_EINVAL;
+  if (r->npml > 0) {  // the layer: as wave_set_cpml
+    if (2 * r->npml > std::min(r->grid.nx, std::min(r->grid.ny, r->grid.nz)) ||
+        !(r->reflection > 0.0 && r->reflection < 1.0) || !(r->f_cps >= 0.0) ||
+        !std::isfinite(r->f_cps))
+      return WAVE_EINVAL;
+    if (r->grid.ny > 65535 || r->grid.nz > 65535) return WAVE_ENOTSUP;
+  }
   return WAVE_OK;
 }
 
@@ -575,6 +710,9 @@ int serve_create(size_t hbm_budget_bytes, int max_slots, void *stream,
     if (e == WAVE_OK)
       e = cuda_status(cudaMalloc((void **)&s->d_table[kd],
                                  sizeof(BatchShot) * (size_t)max_slots));
+    if (e == WAVE_OK)
+      e = cuda_status(cudaMalloc((void **)&s->d_layer[kd],
+                                 sizeof(CpmlBatchShot) * (size_t)max_slots));
   }
   if (e == WAVE_OK) e = cuda_status(cudaMalloc(&s->d_scan, 16));
   if (e == WAVE_OK) {
@@ -591,7 +729,10 @@ int serve_create(size_t hbm_budget_bytes, int max_slots, void *stream,
   if (const char *f = std::getenv("GBWAVE_SERVE_FAULT_ALLOC"))
     s->fault_alloc = std::atoll(f);
   if (e != WAVE_OK) {
-    for (int kd = 0; kd < kKinds; ++kd) cudaFree(s->d_table[kd]);
+    for (int kd = 0; kd < kKinds; ++kd) {
+      cudaFree(s->d_table[kd]);
+      cudaFree(s->d_layer[kd]);
+    }
     cudaFree(s->d_scan);
     if (s->pool) cudaMemPoolDestroy(s->pool);
     if (s->own_stream) cudaStreamDestroy(s->stream);
@@ -669,7 +810,10 @@ void serve_destroy(serve_ctx *s) {
   }
   if (s->engine.joinable()) s->engine.join();
   cudaStreamSynchronize(s->stream);
-  for (int kd = 0; kd < kKinds; ++kd) cudaFree(s->d_table[kd]);
+  for (int kd = 0; kd < kKinds; ++kd) {
+    cudaFree(s->d_table[kd]);
+    cudaFree(s->d_layer[kd]);
+  }
   cudaFree(s->d_scan);
   if (s->pool) cudaMemPoolDestroy(s->pool);
   if (s->own_stream) cudaStreamDestroy(s->stream);

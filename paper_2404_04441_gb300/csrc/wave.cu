@@ -1223,23 +1223,7 @@ int wave_set_cpml(wave_ctx *c, int npml, double R, double f_cps) {
       }
       // Profiles (FP64, stored FP32) and derivative coefficients.
       std::vector<float> hb(dims[ax]), ha(dims[ax]);
-      const double pi = 3.14159265358979323846;
-      const double d0 = 3.0 * c->vmax * std::log(1.0 / R) / (2.0 * npml * hs[ax]);
-      for (int i = 0; i < dims[ax]; ++i) {
-        double xi = 0.0;
-        if (i < npml) xi = (double)(npml - i) / npml;
-        if (i >= dims[ax] - npml)
-          xi = std::max(xi, (double)(i - (dims[ax] - npml - 1)) / npml);
-        if (xi <= 0.0) {
-          hb[i] = 1.f;
-          ha[i] = 0.f;
-          continue;
-        }
-        const double dd = d0 * xi * xi, al = pi * f_cps * (1.0 - xi);
-        const double bb = std::exp(-(dd + al) * c->dt);
-        hb[i] = (float)bb;
-        ha[i] = (float)(dd + al > 0.0 ? dd / (dd + al) * (bb - 1.0) : 0.0);
-      }
+      cpml_profile(dims[ax], npml, R, f_cps, c->vmax, hs[ax], c->dt, hb.data(), ha.data());
       // The unrolled segment kernels take npml 8 or 16 on axes where the two
       // end segments are disjoint; GBWAVE_CPML_GENERIC=1 keeps the line walks
       // everywhere (the two give bitwise equal results).
@@ -1269,12 +1253,7 @@ int wave_set_cpml(wave_ctx *c, int npml, double R, double f_cps) {
                                cudaMemcpyHostToDevice));
       WAVE_TRY_CUDA(cudaMemcpy((void *)g.aprof[ax], ha.data(), dims[ax] * 4,
                                cudaMemcpyHostToDevice));
-      g.c2[ax][0] = (float)(kW[0] / (hs[ax] * hs[ax]));
-      g.c1[ax][0] = 0.f;
-      for (int m = 1; m <= 4; ++m) {
-        g.c2[ax][m] = (float)(kW[m] / (hs[ax] * hs[ax]));
-        g.c1[ax][m] = (float)(kW1[m] / hs[ax]);
-      }
+      cpml_axis_coefs(g, ax, hs[ax]);
     }
     if (!c->d_nsrec) WAVE_TRY_CUDA(cudaMalloc((void **)&c->d_nsrec, sizeof(int)));
     WAVE_TRY_CUDA(cudaMemset(c->d_nsrec, 0, sizeof(int)));
