@@ -280,8 +280,9 @@ def serve_stream(gw, torch, storage, n_requests, max_slots=32):
 
 def serve_saturated(gw, torch, n_requests=48):
     """Capacity on the stream's shot mix: the first n requests submitted at
-    once to the server (FP32 and FP16 storage) against the same shots run one
-    after another through the plain FP32 single-grid path."""
+    once to the server (FP32 and FP16 storage, then the same with a 16-cell
+    CPML layer on every shot) against the same shots run one after another
+    through the plain FP32 single-grid path."""
     reqs = wl.serving_requests(**dict(wl.SERVE_STREAM, n=n_requests))
     made = []
     for r in reqs:
@@ -306,7 +307,8 @@ def serve_saturated(gw, torch, n_requests=48):
             s.synchronize()
             s.close()
         out["plain_f32_sequential_gpts"] = work / (time.perf_counter() - t0) / 1e9
-    for name in ("f32", "f16"):
+    # served, then the same shots each with a 16-cell CPML layer
+    for name, npml in (("f32", 0), ("f16", 0), ("f32", 16), ("f16", 16)):
         srv = gw.ShotServer(wl.SERVE_STREAM["budget_bytes"], 64)
         trs = []
         t0 = time.perf_counter()
@@ -314,11 +316,17 @@ def serve_saturated(gw, torch, n_requests=48):
             tr = torch.empty((r["nsteps"], rec.shape[0]), device="cuda")
             trs.append((srv.submit(r["grid"], (10.0, 10.0, 10.0), vel,
                                    (*r["source"], 15.0, -1.0, 1.0), r["nsteps"], rec, tr,
-                                   storage=STORAGE[name]), tr))
+                                   storage=STORAGE[name],
+                                   cpml=(npml, 1e-3, 15.0) if npml else None), tr))
         ok = all(srv.wait(t)[0] == 0 for t, _ in trs)
         el = time.perf_counter() - t0
         srv.close()
-        out["served_%s_gpts" % name] = work / el / 1e9 if ok else None
+        key = "served_%s_gpts" % name if not npml else "served_%s_npml%d_gpts" % (name, npml)
+        out[key] = work / el / 1e9 if ok else None
+    for name in ("f32", "f16"):
+        if out["served_%s_npml16_gpts" % name] and out["served_%s_gpts" % name]:
+            out["served_%s_npml16_vs_served" % name] = (out["served_%s_npml16_gpts" % name]
+                                                        / out["served_%s_gpts" % name])
     out["served_f32_vs_plain_f32"] = out["served_f32_gpts"] / out["plain_f32_sequential_gpts"]
     out["served_f16_vs_plain_f32"] = out["served_f16_gpts"] / out["plain_f32_sequential_gpts"]
     return out

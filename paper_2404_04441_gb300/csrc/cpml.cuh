@@ -25,6 +25,7 @@
 #include <algorithm>
 #include <cmath>
 #include <cstdint>
+#include <cstdlib>
 
 #include "common.cuh"
 #include "sweep.cuh"
@@ -76,6 +77,18 @@ inline void cpml_axis_coefs(CpmlGeom &g, int ax, double h) {
     g.c2[ax][m] = (float)(kW[m] / (h * h));
     g.c1[ax][m] = (float)(kW1[m] / h);
   }
+}
+
+// Whether an axis of n cells takes the unrolled segment kernels: a layer of
+// 8 or 16 cells, two disjoint end segments (n >= 2 (npml + 4)), and 32-bit
+// per-position offsets (fstep, sstep: the axis's field and slab steps);
+// GBWAVE_CPML_GENERIC=1 keeps the line walks everywhere (the two forms give
+// bitwise equal results).
+inline bool cpml_seg_fits(int npml, int n, long long fstep, long long sstep) {
+  const char *gen = std::getenv("GBWAVE_CPML_GENERIC");
+  return (npml == 8 || npml == 16) && n >= 2 * (npml + 4) &&
+         (long long)(npml + 3) * fstep <= INT32_MAX &&
+         (long long)(npml - 1) * sstep <= INT32_MAX && !(gen && std::atoi(gen) == 1);
 }
 
 // Slab storage, cell-major: cell in [0, 2 npml) counts the low slab's npml
@@ -375,68 +388,6 @@ __global__ void __launch_bounds__(128)
                                  unext, c, dout, d, koff);
 }
 
-// One served shot's layer in the shot server's batched layer launches: its
-// geometry and slabs, fields, descriptor, shell receivers, step bookkeeping
-// (batch step b0 is the shot's step 0, as in the batched sweep), and its
-// first block in each axis launch (a 1D grid that concatenates the shots'
-// blocks: ceil(lines across / 128) per row of lines).
-struct CpmlBatchShot {
-  CpmlGeom g;
-  void *buf[2];  // buf[0] holds the shot's step 0
-  const float *c;
-  const StepDesc *desc;
-  const int4 *srec;  // receivers within w of a face: {x, y, z, id}
-  int nsrec;
-  long long b0;
-  int nsteps;
-  int blk_begin[3];
-};
-
-__device__ __forceinline__ int cpml_batch_find(const CpmlBatchShot *shots, int nshots, int ax,
-                                               int blk) {
-  int lo = 0, hi = nshots - 1;
-  while (lo < hi) {
-    const int mid = (lo + hi + 1) >> 1;
-    if (shots[mid].blk_begin[ax] <= blk) lo = mid; else hi = mid - 1;
-  }
-  return lo;
-}
-
-// The axis-AX pass of batch step k over every shot of the table (line walks;
-// shots outside their steps return at once).
-template <int AX, class T>
-__global__ void __launch_bounds__(128)
-    cpml_line_batched_kernel(const CpmlBatchShot *__restrict__ shots, int nshots, long long k) {
-  const CpmlBatchShot &sh = shots[cpml_batch_find(shots, nshots, AX, blockIdx.x)];
-  const long long n = k - sh.b0;
-  if (n < 0 || n >= sh.nsteps) return;
-  const int cur = (int)(n & 1);
-  const int across = AX == 0 ? sh.g.ny : sh.g.nx;
-  const int bpr = (across + 127) / 128;  // blocks per row of lines
-  const int local = blockIdx.x - sh.blk_begin[AX];
-  const int q = local / bpr;
-  const int t = (local - q * bpr) * 128 + threadIdx.x;
-  cpml_line_walk<AX, T, false>(sh.g, t, q, static_cast<const T *>(sh.buf[cur]),
-                               static_cast<T *>(sh.buf[cur ^ 1]), sh.c, nullptr, sh.desc,
-                               (int)n);
-}
-
-// Shell receivers of batch step k, one block per shot.
-template <class T>
-__global__ void cpml_record_batched_kernel(const CpmlBatchShot *__restrict__ shots, long long k) {
-  const CpmlBatchShot &sh = shots[blockIdx.x];
-  const long long n = k - sh.b0;
-  if (n < 0 || n >= sh.nsteps || sh.nsrec == 0) return;
-  const StepDesc *d = sh.desc;
-  CpmlScale<T> sc;
-  sc.init(d, (int)n);
-  const T *un = static_cast<const T *>(sh.buf[(n & 1) ^ 1]);
-  for (int r = threadIdx.x; r < sh.nsrec; r += blockDim.x) {
-    const int4 e = sh.srec[r];
-    d->traces[(size_t)(d->n + n) * d->nrec + e.w] =
-        cpml_get(un + ((size_t)e.z * sh.g.ny + e.y) * sh.g.pxu + e.x, sc.so);
-  }
-}
 
 // Discrete adjoint of the layer (the gradient's backward steps), in the
 // form the sweep runs it, p = C q. After the plain adjoint sweep has written
@@ -566,6 +517,18 @@ struct CpmlSideProf {
   float b[2][NPML], a[2][NPML];  // [face][j], j counted from the face
 };
 
+// Profile values of an axis of n cells (b, a along the axis) by face and
+// depth from the face.
+template <int NPML>
+inline void cpml_side_prof(const float *b, const float *a, int n, CpmlSideProf<NPML> &pf) {
+  for (int j = 0; j < NPML; ++j)
+    for (int sd = 0; sd < 2; ++sd) {
+      const int i = sd ? n - 1 - j : j;
+      pf.b[sd][j] = b[i];
+      pf.a[sd][j] = a[i];
+    }
+}
+
 // Segment addressing shared by the unrolled kernels: line offset of
 // position j (field layout) and of slab cell j (slab layout).
 // The per-position steps are 32-bit (the host takes these kernels only
@@ -582,10 +545,11 @@ struct CpmlSeg {
   int n;
 };
 
+// t: index across the lines, q: row of lines (z for x and y lines, y for
+// z lines).
 template <int AX, int NPML>
-__device__ __forceinline__ bool cpml_seg_setup(const CpmlGeom &g, int side, CpmlSeg &sg) {
-  const int t = blockIdx.x * blockDim.x + threadIdx.x;
-  const int q = blockIdx.y;
+__device__ __forceinline__ bool cpml_seg_setup(const CpmlGeom &g, int side, int t, int q,
+                                               CpmlSeg &sg) {
   long long ub, us, cb, cs, sb, ss;
   if (AX == 0) {
     if (t >= g.ny) return false;
@@ -692,14 +656,14 @@ __device__ __forceinline__ float cpml_seg_d2(const float *v, int j, const float 
 
 template <int AX, int NPML, class T, bool kStoreD, int SIDE>
 __device__ __forceinline__ void cpml_seg_forward(const CpmlGeom &g, const CpmlSideProf<NPML> &pf,
-                                                 const T *__restrict__ u,
+                                                 int t, int q, const T *__restrict__ u,
                                                  T *__restrict__ unext,
                                                  const float *__restrict__ c,
                                                  float *__restrict__ dout,
                                                  const StepDesc *d, int koff) {
   constexpr int W = NPML + 4;
   CpmlSeg sg;
-  if (!cpml_seg_setup<AX, NPML>(g, SIDE, sg)) return;
+  if (!cpml_seg_setup<AX, NPML>(g, SIDE, t, q, sg)) return;
   CpmlScale<T> sc;
   sc.init(d, koff);
   float *psi = g.psi[AX] + sg.s0;
@@ -764,10 +728,11 @@ __global__ void __launch_bounds__(128)
                     T *__restrict__ unext, const float *__restrict__ c,
                     float *__restrict__ dout, const StepDesc *d, int koff) {
   static_assert(!kStoreD || std::is_same<T, float>::value, "D is stored for FP32 only");
+  const int t = blockIdx.x * blockDim.x + threadIdx.x, q = blockIdx.y;
   if (blockIdx.z == 0)
-    cpml_seg_forward<AX, NPML, T, kStoreD, 0>(g, pf, u, unext, c, dout, d, koff);
+    cpml_seg_forward<AX, NPML, T, kStoreD, 0>(g, pf, t, q, u, unext, c, dout, d, koff);
   else
-    cpml_seg_forward<AX, NPML, T, kStoreD, 1>(g, pf, u, unext, c, dout, d, koff);
+    cpml_seg_forward<AX, NPML, T, kStoreD, 1>(g, pf, t, q, u, unext, c, dout, d, koff);
 }
 
 // The adjoint's segment form (cpml_adjoint_line_kernel, unrolled): nu and
@@ -782,7 +747,9 @@ __device__ __forceinline__ void cpml_seg_adjoint(const CpmlGeom &g, const CpmlSi
                                                  float *__restrict__ mus) {
   constexpr int W = NPML + 4;
   CpmlSeg sg;
-  if (!cpml_seg_setup<AX, NPML>(g, SIDE, sg)) return;
+  if (!cpml_seg_setup<AX, NPML>(g, SIDE, blockIdx.x * blockDim.x + threadIdx.x, blockIdx.y,
+                                sg))
+    return;
   float *nu = nus + sg.s0;
   float *mu = mus + sg.s0;
   // two phases as in the forward: p^{k+1}, nu, mu -> nu, mu and the
@@ -857,6 +824,109 @@ __global__ void cpml_record_kernel(CpmlGeom g, const T *__restrict__ unext,
     const int4 e = srec[t];
     d->traces[(size_t)n * d->nrec + e.w] =
         cpml_get(unext + ((size_t)e.z * g.ny + e.y) * g.pxu + e.x, sc.so);
+  }
+}
+
+// One served shot's layer in the shot server's batched layer launches: its
+// geometry and slabs, fields, descriptor, shell receivers, step bookkeeping
+// (batch step b0 is the shot's step 0, as in the batched sweep), and its
+// first block in each axis launch (a 1D grid that concatenates the shots'
+// blocks: ceil(lines across / 128) per row of lines).
+struct CpmlBatchShot {
+  CpmlGeom g;
+  void *buf[2];  // buf[0] holds the shot's step 0
+  const float *c;
+  const StepDesc *desc;
+  const int4 *srec;  // receivers within w of a face: {x, y, z, id}
+  int nsrec;
+  long long b0;
+  int nsteps;
+  int blk_begin[3];
+  // per axis: 0 for the line walk, or 8 / 16 for the unrolled segment form
+  // (both faces' segments in blocks of their own), with its profile values
+  int seg[3];
+  CpmlSideProf<16> p16[3];
+  CpmlSideProf<8> p8[3];
+};
+
+__device__ __forceinline__ int cpml_batch_find(const CpmlBatchShot *shots, int nshots, int ax,
+                                               int blk) {
+  int lo = 0, hi = nshots - 1;
+  while (lo < hi) {
+    const int mid = (lo + hi + 1) >> 1;
+    if (shots[mid].blk_begin[ax] <= blk) lo = mid; else hi = mid - 1;
+  }
+  return lo;
+}
+
+// The axis-AX pass of batch step k over every shot of the table, each in
+// its form (shots outside their steps return at once): a shot's blocks are
+// rows x ceil(lines across / 128) for the line walk, twice that for the
+// segment form (the low face's blocks, then the high face's).
+template <int AX, class T>
+__global__ void __launch_bounds__(128, 3)
+    cpml_line_batched_kernel(const CpmlBatchShot *__restrict__ shots, int nshots, long long k) {
+  const CpmlBatchShot &sh = shots[cpml_batch_find(shots, nshots, AX, blockIdx.x)];
+  const long long n = k - sh.b0;
+  if (n < 0 || n >= sh.nsteps) return;
+  const int cur = (int)(n & 1);
+  const int across = AX == 0 ? sh.g.ny : sh.g.nx;
+  const int rows = AX == 2 ? sh.g.ny : sh.g.nz;
+  const int bpr = (across + 127) / 128;  // blocks per row of lines
+  int local = blockIdx.x - sh.blk_begin[AX];
+  const T *u = static_cast<const T *>(sh.buf[cur]);
+  T *un = static_cast<T *>(sh.buf[cur ^ 1]);
+  const int form = sh.seg[AX];
+  const int side = (form != 0 && local >= rows * bpr) ? 1 : 0;
+  local -= side * rows * bpr;
+  const int q = local / bpr;
+  const int t = (local - q * bpr) * 128 + threadIdx.x;
+  // the shot's profile values staged in shared memory (block-uniform form),
+  // read with immediate offsets where the single-grid kernels take them as
+  // constant operands
+  __shared__ CpmlSideProf<16> s16;
+  __shared__ CpmlSideProf<8> s8;
+  if (form == 16) {
+    constexpr int NV = sizeof(CpmlSideProf<16>) / 4;
+    for (int i = threadIdx.x; i < NV; i += blockDim.x)
+      reinterpret_cast<float *>(&s16)[i] = reinterpret_cast<const float *>(&sh.p16[AX])[i];
+    __syncthreads();
+    if (side == 0)
+      cpml_seg_forward<AX, 16, T, false, 0>(sh.g, s16, t, q, u, un, sh.c, nullptr, sh.desc,
+                                            (int)n);
+    else
+      cpml_seg_forward<AX, 16, T, false, 1>(sh.g, s16, t, q, u, un, sh.c, nullptr, sh.desc,
+                                            (int)n);
+  } else if (form == 8) {
+    constexpr int NV = sizeof(CpmlSideProf<8>) / 4;
+    for (int i = threadIdx.x; i < NV; i += blockDim.x)
+      reinterpret_cast<float *>(&s8)[i] = reinterpret_cast<const float *>(&sh.p8[AX])[i];
+    __syncthreads();
+    if (side == 0)
+      cpml_seg_forward<AX, 8, T, false, 0>(sh.g, s8, t, q, u, un, sh.c, nullptr, sh.desc,
+                                           (int)n);
+    else
+      cpml_seg_forward<AX, 8, T, false, 1>(sh.g, s8, t, q, u, un, sh.c, nullptr, sh.desc,
+                                           (int)n);
+  } else {
+    cpml_line_walk<AX, T, false>(sh.g, t, q, u, un, sh.c, nullptr, sh.desc, (int)n);
+  }
+}
+
+// Shell receivers of batch step k, one block per shot.
+template <class T>
+__global__ void cpml_record_batched_kernel(const CpmlBatchShot *__restrict__ shots, long long k) {
+  const CpmlBatchShot &sh = shots[blockIdx.x];
+  const long long n = k - sh.b0;
+  if (n < 0 || n >= sh.nsteps || sh.nsrec == 0) return;
+  const StepDesc *d = sh.desc;
+  CpmlScale<T> sc;
+  sc.init(d, (int)n);
+  const T *un = static_cast<const T *>(sh.buf[(n & 1) ^ 1]);
+  for (int r = threadIdx.x; r < sh.nsrec; r += blockDim.x) {
+    const int4 e = sh.srec[r];
+    d->traces[(size_t)(d->n + n) * d->nrec + e.w] =
+        cpml_get(un + ((size_t)e.z * sh.g.ny + e.y) * sh.g.pxu + e.x, sc.so);
   }
 }
 

@@ -242,8 +242,8 @@ int admit_layer(serve_ctx *s, Request *q, float vmax, double dt,
   cudaStream_t st = s->stream;
   const int nx = r.grid.nx, ny = r.grid.ny, nz = r.grid.nz, npml = r.npml;
   CpmlBatchShot &L = q->layer;
+  L = CpmlBatchShot{};
   CpmlGeom &g = L.g;
-  g = CpmlGeom{};
   g.nx = nx;
   g.ny = ny;
   g.nz = nz;
@@ -270,6 +270,11 @@ int admit_layer(serve_ctx *s, Request *q, float vmax, double dt,
     std::vector<float> hb(dims[ax]), ha(dims[ax]);
     cpml_profile(dims[ax], npml, r.reflection, r.f_cps, (double)vmax, hs[ax], dt, hb.data(),
                  ha.data());
+    const long long fstep[3] = {1, g.pxu, (long long)ny * g.pxu};
+    const long long sstep[3] = {(long long)nz * ny, (long long)nz * nx, (long long)ny * nx};
+    L.seg[ax] = cpml_seg_fits(npml, dims[ax], fstep[ax], sstep[ax]) ? npml : 0;
+    if (L.seg[ax] == 16) cpml_side_prof(hb.data(), ha.data(), dims[ax], L.p16[ax]);
+    if (L.seg[ax] == 8) cpml_side_prof(hb.data(), ha.data(), dims[ax], L.p8[ax]);
     WAVE_TRY_CUDA(cudaMemcpyAsync((void *)g.bprof[ax], hb.data(), dims[ax] * 4,
                                   cudaMemcpyHostToDevice, st));
     WAVE_TRY_CUDA(cudaMemcpyAsync((void *)g.aprof[ax], ha.data(), dims[ax] * 4,
@@ -477,9 +482,9 @@ int upload_tables(serve_ctx *s) {
       CpmlBatchShot L = q->layer;
       const int nx = q->r.grid.nx, ny = q->r.grid.ny, nz = q->r.grid.nz;
       const int rows[3] = {nz, nz, ny}, across[3] = {ny, nx, nx};
-      for (int ax = 0; ax < 3; ++ax) {
+      for (int ax = 0; ax < 3; ++ax) {  // the segment form: a block set per face
         L.blk_begin[ax] = nb[ax];
-        nb[ax] += rows[ax] * ((across[ax] + 127) / 128);
+        nb[ax] += rows[ax] * ((across[ax] + 127) / 128) * (L.seg[ax] ? 2 : 1);
       }
       lt.push_back(L);
     }

@@ -1224,30 +1224,18 @@ int wave_set_cpml(wave_ctx *c, int npml, double R, double f_cps) {
       // Profiles (FP64, stored FP32) and derivative coefficients.
       std::vector<float> hb(dims[ax]), ha(dims[ax]);
       cpml_profile(dims[ax], npml, R, f_cps, c->vmax, hs[ax], c->dt, hb.data(), ha.data());
-      // The unrolled segment kernels take npml 8 or 16 on axes where the two
-      // end segments are disjoint; GBWAVE_CPML_GENERIC=1 keeps the line walks
-      // everywhere (the two give bitwise equal results).
-      const char *gen = std::getenv("GBWAVE_CPML_GENERIC");
-      // field and slab steps along the axis (the kernels' 32-bit offsets)
-      // (the wavefields' pitch, which is at least that of v^2 dt^2)
+      // the unrolled segment kernels where they apply (cpml_seg_fits), with
+      // the field and slab steps along the axis (the wavefields' pitch is at
+      // least that of v^2 dt^2)
       const long long fstep[3] = {1, c->pxu, (long long)c->ny * c->pxu};
       const long long sstep[3] = {(long long)c->nz * c->ny, (long long)c->nz * c->nx,
                                   (long long)c->ny * c->nx};
-      if ((npml == 8 || npml == 16) && dims[ax] >= 2 * (npml + 4) &&
-          (long long)(npml + 3) * fstep[ax] <= INT32_MAX &&
-          (long long)(npml - 1) * sstep[ax] <= INT32_MAX && !(gen && std::atoi(gen) == 1)) {
+      if (cpml_seg_fits(npml, dims[ax], fstep[ax], sstep[ax])) {
         c->cpml_seg_axes |= 1 << ax;
-        for (int j = 0; j < npml; ++j)
-          for (int sd = 0; sd < 2; ++sd) {
-            const int i = sd ? dims[ax] - 1 - j : j;
-            if (npml == 8) {
-              c->prof8[ax].b[sd][j] = hb[i];
-              c->prof8[ax].a[sd][j] = ha[i];
-            } else {
-              c->prof16[ax].b[sd][j] = hb[i];
-              c->prof16[ax].a[sd][j] = ha[i];
-            }
-          }
+        if (npml == 8)
+          cpml_side_prof(hb.data(), ha.data(), dims[ax], c->prof8[ax]);
+        else
+          cpml_side_prof(hb.data(), ha.data(), dims[ax], c->prof16[ax]);
       }
       WAVE_TRY_CUDA(cudaMemcpy((void *)g.bprof[ax], hb.data(), dims[ax] * 4,
                                cudaMemcpyHostToDevice));
