@@ -379,3 +379,74 @@ def test_full_size_sampled_points(wave_lib, oracle_mod):
         _, want_tr = _sub_box_cpml(oracle_mod, vel, u0h, up0h, sp, dt, n,
                                    tuple(int(v) for v in rec_all[r]), shot, npml, R, fcps, vmax)
         np.testing.assert_allclose(trh[:, r], want_tr, rtol=2e-5, atol=2e-5)
+
+
+def test_full_size_fp16_with_the_layer(wave_lib, oracle_mod):
+    """The benchmark's FP16 + CPML form (1024 x 1024 x 512, npml 16) in its
+    launch configuration: 3 steps from a random state read back as stored,
+    sampled points in the layer (faces, edges, corners, both ends of the
+    correction segments) and receivers against the oracle's layered run on
+    sub-boxes. Bound 88 EPS M: the plain 16-bit full-size bound (44 EPS M,
+    each step's rounding carried at most 7-fold) doubled for the layer
+    passes' extra roundings at shell points. That worst-case bound is of the
+    order of the layer's own effect after 3 steps from rest memory variables,
+    so the test also requires the layer's effect at the layer points (oracle
+    with the layer against without) to exceed 20 times the largest measured
+    error: a missing or misplaced layer term makes the error about as large
+    as the effect."""
+    import torch
+    from test_gpu_parity import _sub_box_oracle
+    cfg = wl.CFG_1024
+    nx, ny, nz = cfg["shape"]
+    vel = wl.velocity_for(cfg)
+    sp = cfg["spacing"]
+    dt = cfg["cfl_fraction"] * wave_lib.wave_cfl_dt(sp, float(vel.max()))
+    npml, R, fcps = 16, 1e-3, cfg["f_peak"]
+    g = torch.Generator(device="cuda")
+    g.manual_seed(2468)
+    u0 = torch.rand((nz, ny, nx), generator=g, device="cuda") * 2 - 1
+    up0 = torch.rand((nz, ny, nx), generator=g, device="cuda") * 2 - 1
+    n = 3
+    shot = (*cfg["source"], cfg["f_peak"], -1.0, 1e2)
+    rec_all = wl.receiver_plane(nx, ny, cfg["rec_z"], cfg["rec_stride"])
+    s = wave_lib.WaveSolver((nx, ny, nz), sp, dt, torch.from_numpy(vel).cuda(), storage=2)
+    s.set_cpml(npml, R, fcps)
+    s.set_state(u0, up0, 0)
+    su = torch.empty((nz, ny, nx), device="cuda")
+    sup = torch.empty((nz, ny, nx), device="cuda")
+    s.get_field(0, su)
+    s.get_field(1, sup)
+    tr = torch.zeros((n, rec_all.shape[0]), device="cuda")
+    s.propagate(shot, n, torch.from_numpy(rec_all).cuda(), tr)
+    out = torch.empty((nz, ny, nx), device="cuda")
+    s.get_field(0, out)
+    s.synchronize()
+    s.close()
+    u0h, up0h = su.cpu().numpy(), sup.cpu().numpy()
+    outh, trh = out.cpu().numpy(), tr.cpu().numpy()
+    M = max(float(np.abs(outh).max()), float(np.abs(u0h).max()))
+    tol = 88 * EPS16["f16"] * M
+    vmax = float(vel.max())
+    w = npml + 4
+    layer_pts = [(0, 0, 0), (nx - 1, ny - 1, nz - 1), (nx - 1, 0, nz // 2), (0, ny // 2, nz - 1),
+                 (npml - 1, 300, 200), (npml, 301, 201), (w - 1, 302, 202), (nx - w, 500, 100),
+                 (700, npml - 1, 250), (701, ny - w, 251), (400, 402, nz - npml),
+                 (401, 403, w - 1), (5, 7, 9), (nx - 3, ny - 9, 2), cfg["source"]]
+    worst, effect = 0.0, 0.0
+    for p in layer_pts + [(512, 512, 256)]:
+        want, _ = _sub_box_cpml(oracle_mod, vel, u0h, up0h, sp, dt, n, p, shot, npml, R, fcps,
+                                vmax)
+        got = outh[p[2], p[1], p[0]]
+        worst = max(worst, abs(got - want))
+        assert abs(got - want) <= tol, (p, got, want, tol)
+        if p in layer_pts:
+            plain, _ = _sub_box_oracle(oracle_mod, vel, u0h, up0h, sp, dt, n, p, shot)
+            effect = max(effect, abs(want - plain))
+    rng = np.random.default_rng(3)
+    for r in [0, rec_all.shape[0] - 1] + list(rng.integers(0, rec_all.shape[0], 4)):
+        _, want_tr = _sub_box_cpml(oracle_mod, vel, u0h, up0h, sp, dt, n,
+                                   tuple(int(v) for v in rec_all[r]), shot, npml, R, fcps, vmax)
+        assert np.max(np.abs(trh[:, r] - want_tr)) <= tol, r
+    print("\nfull-size FP16 + CPML: worst |error| %.3e, bound %.3e, layer effect %.3e"
+          % (worst, tol, effect))
+    assert effect > 20 * worst
