@@ -249,7 +249,8 @@ def test_16bit_storage_with_the_layer(wave_lib, oracle_mod, monkeypatch, mode, s
     """Against the oracle's layered run from the state as stored, within
     12 EPS sqrt(n): twice the plain 16-bit short-run bound, for the shell
     points' extra roundings; and the unrolled segment kernels (npml 8 and 16)
-    equal the line walks bit for bit in 16-bit storage too."""
+    equal the line walks bit for bit in 16-bit storage too. 3 + 34 steps in
+    two calls (the second runs a captured 32-step graph)."""
     import torch
     nx, ny, nz = shape
     sp = (10.0, 12.0, 9.0)
@@ -259,7 +260,8 @@ def test_16bit_storage_with_the_layer(wave_lib, oracle_mod, monkeypatch, mode, s
     dt = 0.45 * wave_lib.wave_cfl_dt(sp, float(vel.max()))
     shot = (nx // 3, ny - 4, 3, 20.0, -1.0, 1e2)
     rec = shell_receivers(nx, ny, nz, npml + 4)
-    n, R, fcps = 25, 1e-3, 15.0
+    chunks = (3, 34)  # split calls, the second through a 32-step graph
+    n, R, fcps = sum(chunks), 1e-3, 15.0
 
     def run():
         s = wave_lib.WaveSolver((nx, ny, nz), sp, dt, torch.from_numpy(vel).cuda(),
@@ -271,12 +273,15 @@ def test_16bit_storage_with_the_layer(wave_lib, oracle_mod, monkeypatch, mode, s
             sup = np.empty((nz, ny, nx), np.float32)
             s.get_field(0, su)
             s.get_field(1, sup)
-            tr = torch.zeros((n, rec.shape[0]), device="cuda")
-            s.propagate(shot, n, torch.from_numpy(rec).cuda(), tr)
+            rows = []
+            for k in chunks:
+                tr = torch.zeros((k, rec.shape[0]), device="cuda")
+                s.propagate(shot, k, torch.from_numpy(rec).cuda(), tr)
+                rows.append(tr.cpu().numpy())
             u = np.empty((nz, ny, nx), np.float32)
             s.get_field(0, u)
             s.synchronize()
-            return su, sup, u, tr.cpu().numpy()
+            return su, sup, u, np.concatenate(rows)
         finally:
             s.close()
 
