@@ -114,3 +114,30 @@ def test_layer_request_checks(wave_lib):
         assert st == 0
     finally:
         srv.close()
+
+
+def test_layered_shot_with_host_buffers(wave_lib):
+    """A layered shot whose receivers and traces are host arrays (the server
+    stages the traces on the device and copies them back at completion),
+    FP16 with npml 8: the same traces as the single-grid path."""
+    import torch
+    grid, storage, nsteps, seed, npml = (56, 44, 40), 2, 30, 9, 8
+    vel, rec, shot = _inputs(grid, seed, npml)
+    rec_h = rec.cpu().numpy()
+    tr_h = np.zeros((nsteps, rec_h.shape[0]), dtype=np.float32)
+    srv = wave_lib.ShotServer(GB, 4)
+    try:
+        t = srv.submit(grid, SP, vel, shot, nsteps, rec_h, tr_h, storage=storage,
+                       cpml=(npml, R, FCPS))
+        st, res = srv.wait(t, 60.0)
+        assert st == 0, res
+    finally:
+        srv.close()
+    s = wave_lib.WaveSolver(grid, SP, res["dt"], vel, storage=storage)
+    s.set_cpml(npml, R, FCPS)
+    tr = torch.zeros((nsteps, rec_h.shape[0]), device="cuda")
+    s.propagate(shot, nsteps, rec, tr)
+    s.synchronize()
+    s.close()
+    assert np.array_equal(tr.cpu().numpy(), tr_h)
+    assert np.abs(tr_h).max() > 0
