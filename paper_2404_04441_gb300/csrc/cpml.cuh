@@ -913,17 +913,21 @@ __global__ void __launch_bounds__(128, 3)
   }
 }
 
-// Shell receivers of batch step k, one block per shot.
+// Shell receivers of batch step k: blocks_per_shot blocks per shot (a
+// receiver plane inside the layer puts all of a shot's receivers here).
 template <class T>
-__global__ void cpml_record_batched_kernel(const CpmlBatchShot *__restrict__ shots, long long k) {
-  const CpmlBatchShot &sh = shots[blockIdx.x];
+__global__ void cpml_record_batched_kernel(const CpmlBatchShot *__restrict__ shots, long long k,
+                                           int blocks_per_shot) {
+  const CpmlBatchShot &sh = shots[blockIdx.x / blocks_per_shot];
+  const int part = blockIdx.x % blocks_per_shot;
   const long long n = k - sh.b0;
   if (n < 0 || n >= sh.nsteps || sh.nsrec == 0) return;
   const StepDesc *d = sh.desc;
   CpmlScale<T> sc;
   sc.init(d, (int)n);
   const T *un = static_cast<const T *>(sh.buf[(n & 1) ^ 1]);
-  for (int r = threadIdx.x; r < sh.nsrec; r += blockDim.x) {
+  for (int r = part * blockDim.x + threadIdx.x; r < sh.nsrec;
+       r += blocks_per_shot * blockDim.x) {
     const int4 e = sh.srec[r];
     d->traces[(size_t)(d->n + n) * d->nrec + e.w] =
         cpml_get(un + ((size_t)e.z * sh.g.ny + e.y) * sh.g.pxu + e.x, sc.so);

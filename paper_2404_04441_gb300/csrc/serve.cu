@@ -183,6 +183,7 @@ struct serve_ctx {
   CpmlBatchShot *d_layer[kKinds] = {nullptr, nullptr, nullptr};
   std::vector<CpmlBatchShot> h_layer[kKinds];
   int layer_blocks[kKinds][3] = {};
+  int layer_rec_blocks[kKinds] = {1, 1, 1};  // record blocks per layered shot
   std::vector<Group> groups;
   bool dirty = true;
   void *d_scan = nullptr;     // 16 bytes: velocity max, invalid count
@@ -477,9 +478,11 @@ int upload_tables(serve_ctx *s) {
     lt.clear();
     int *nb = s->layer_blocks[kd];
     nb[0] = nb[1] = nb[2] = 0;
+    int max_srec = 0;
     for (Request *q : shots) {
       if (q->r.npml <= 0) continue;
       CpmlBatchShot L = q->layer;
+      max_srec = std::max(max_srec, L.nsrec);
       const int nx = q->r.grid.nx, ny = q->r.grid.ny, nz = q->r.grid.nz;
       const int rows[3] = {nz, nz, ny}, across[3] = {ny, nx, nx};
       for (int ax = 0; ax < 3; ++ax) {  // the segment form: a block set per face
@@ -488,6 +491,8 @@ int upload_tables(serve_ctx *s) {
       }
       lt.push_back(L);
     }
+    // about 256 shell receivers per record block, at most 64 blocks a shot
+    s->layer_rec_blocks[kd] = std::min(64, std::max(1, (max_srec + 255) / 256));
     if (!lt.empty())
       WAVE_TRY_CUDA(cudaMemcpyAsync(s->d_layer[kd], lt.data(), lt.size() * sizeof(CpmlBatchShot),
                                     cudaMemcpyHostToDevice, s->stream));
@@ -506,7 +511,8 @@ void launch_layers(serve_ctx *s, int kd, long long k) {
   cpml_line_batched_kernel<0, T><<<nb[0], 128, 0, s->stream>>>(t, n, k);
   cpml_line_batched_kernel<1, T><<<nb[1], 128, 0, s->stream>>>(t, n, k);
   cpml_line_batched_kernel<2, T><<<nb[2], 128, 0, s->stream>>>(t, n, k);
-  cpml_record_batched_kernel<T><<<n, 128, 0, s->stream>>>(t, k);
+  const int rb = s->layer_rec_blocks[kd];
+  cpml_record_batched_kernel<T><<<n * rb, 128, 0, s->stream>>>(t, k, rb);
 }
 
 // Complete a resident shot whose steps are all done (stream synchronized).
