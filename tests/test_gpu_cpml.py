@@ -244,7 +244,8 @@ EPS16 = {"bf16": 2.0 ** -8, "f16": 2.0 ** -11}
 
 
 @pytest.mark.parametrize("mode", ["bf16", "f16"])
-@pytest.mark.parametrize("shape,npml", [((75, 52, 44), 8), ((70, 37, 23), 5), ((72, 41, 40), 16)])
+@pytest.mark.parametrize("shape,npml", [((75, 52, 44), 8), ((70, 37, 23), 5), ((72, 41, 40), 16),
+                                        ((9, 8, 2), 1)])
 def test_16bit_storage_with_the_layer(wave_lib, oracle_mod, monkeypatch, mode, shape, npml):
     """Against the oracle's layered run from the state as stored, within
     12 EPS sqrt(n): twice the plain 16-bit short-run bound, for the shell
@@ -258,7 +259,7 @@ def test_16bit_storage_with_the_layer(wave_lib, oracle_mod, monkeypatch, mode, s
     vel = rng.uniform(1500.0, 4000.0, size=(nz, ny, nx)).astype(np.float32)
     u0, up0 = wl.random_state((nz, ny, nx), seed=ny)
     dt = 0.45 * wave_lib.wave_cfl_dt(sp, float(vel.max()))
-    shot = (nx // 3, ny - 4, 3, 20.0, -1.0, 1e2)
+    shot = (nx // 3, ny - 4, min(3, nz - 1), 20.0, -1.0, 1e2)
     rec = shell_receivers(nx, ny, nz, npml + 4)
     chunks = (3, 34)  # split calls, the second through a 32-step graph
     n, R, fcps = sum(chunks), 1e-3, 15.0

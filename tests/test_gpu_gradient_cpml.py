@@ -44,8 +44,9 @@ def _gpu(pkg, vel, sp, dt, npml, shot, n, rec, obs, ckpt):
 # (shape (nx, ny, nz), npml, checkpoint interval): the 32^3 x 60 case with
 # ragged segments; a box whose y and z lines are one segment of the whole
 # line (2 (npml + 4) > n) and whose x lines have two segments that read into
-# each other's slab.
-CASES = [((32, 32, 32), 6, 7), ((21, 18, 12), 6, 11)]
+# each other's slab; a checkpoint every step (60 segments cycling the two D
+# slots and the layer's checkpointed memory variables).
+CASES = [((32, 32, 32), 6, 7), ((21, 18, 12), 6, 11), ((24, 22, 20), 4, 1)]
 
 
 # npml 8 and 16 on axes of at least 2 (npml + 4) cells run the unrolled
