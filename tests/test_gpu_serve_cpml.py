@@ -141,3 +141,39 @@ def test_layered_shot_with_host_buffers(wave_lib):
     s.close()
     assert np.array_equal(tr.cpu().numpy(), tr_h)
     assert np.abs(tr_h).max() > 0
+
+
+def test_layer_allocation_failure_fails_that_shot_alone(wave_lib, monkeypatch):
+    """Host-side fault injection: the 11th device allocation of the server
+    (one of the first shot's layer slabs, after its 7 field and table
+    allocations) fails. That request ends with WAVE_ENOMEM, its memory is
+    given back, and the other layered shots complete with the traces of the
+    single-grid path."""
+    import torch
+    monkeypatch.setenv("GBWAVE_SERVE_FAULT_ALLOC", "10")
+    srv = wave_lib.ShotServer(GB, 4)
+    monkeypatch.delenv("GBWAVE_SERVE_FAULT_ALLOC")
+    specs = [((40, 36, 32), 0, 12, 30 + i, 8) for i in range(3)]
+    tickets, outs = [], []
+    try:
+        for grid, storage, nsteps, seed, npml in specs:
+            vel, rec, shot = _inputs(grid, seed, npml)
+            tr = torch.zeros((nsteps, rec.shape[0]), device="cuda")
+            tickets.append(srv.submit(grid, SP, vel, shot, nsteps, rec, tr, storage=storage,
+                                      cpml=(npml, R, FCPS)))
+            outs.append(tr)
+        results = [srv.wait(t, 60) for t in tickets]
+        stats = srv.stats()
+    finally:
+        srv.close()
+    assert [r[0] for r in results] == [-2, 0, 0]
+    assert stats["bytes_resident"] == 0 and stats["failed"] == 1
+    for (grid, storage, nsteps, seed, npml), tr, (st, res) in list(zip(specs, outs, results))[1:]:
+        vel, rec, shot = _inputs(grid, seed, npml)
+        s = wave_lib.WaveSolver(grid, SP, res["dt"], vel, storage=storage)
+        s.set_cpml(npml, R, FCPS)
+        want = torch.zeros((nsteps, rec.shape[0]), device="cuda")
+        s.propagate(shot, nsteps, rec, want)
+        s.synchronize()
+        s.close()
+        assert np.array_equal(tr.cpu().numpy(), want.cpu().numpy())
