@@ -501,6 +501,77 @@ def run_reference(args, cfg):
     return 0
 
 
+def run_case(args):
+    """Small fixed cases for profiler captures (no bench line): each runs one
+    piece of the path on the bench's synthetic inputs and prints one line.
+    sweep      --workload W --storage S --steps K [--variant V] [--npml P]: one
+               context (with a CPML layer of P cells), K steps of
+               wave_propagate (the captured launches are its sweeps)
+    gradient   --steps K [--npml P]: the 256^3 gradient workload's start model
+               with a layer of P cells, one wave_gradient call of K steps,
+               checkpoint every 40 (observed traces zero)
+    serve_cpml --serve-requests N: the first N requests of the serving stream
+               at once, each with a 16-cell layer and at most 64 steps"""
+    import torch
+    import paper_2404_04441_gb300 as gw
+    gw.load()
+    if args.case == "sweep":
+        cfg = WORKLOADS[args.workload]
+        nx, ny, nz = cfg["shape"]
+        vel = wl.velocity_for(cfg)
+        dt = cfg["cfl_fraction"] * gw.wave_cfl_dt(cfg["spacing"], float(vel.max()))
+        s = gw.WaveSolver((nx, ny, nz), cfg["spacing"], dt, torch.from_numpy(vel).cuda(),
+                          storage=args.storage)
+        if args.npml:
+            s.set_cpml(args.npml, 1e-3, cfg["f_peak"])
+        rec = torch.from_numpy(wl.receiver_plane(nx, ny, cfg["rec_z"], cfg["rec_stride"])).cuda()
+        tr = torch.empty((args.steps, rec.shape[0]), device="cuda")
+        s.propagate((*cfg["source"], cfg["f_peak"], -1.0, 1.0), args.steps, rec, tr)
+        s.synchronize()
+        out = {"case": "sweep", "workload": cfg["name"], "storage": args.storage,
+               "npml": args.npml, "steps": args.steps, "launch": s.launch_info(),
+               "finite": bool(torch.isfinite(tr).all().item())}
+        s.close()
+    elif args.case == "gradient":
+        cfg = wl.CFG_GRAD
+        nx, ny, nz = cfg["shape"]
+        true = wl.anomaly_model(nx, ny, nz, seed=cfg["seed"], anomaly=cfg["anomaly_mps"])
+        start = wl.smoothed_start(true)
+        rec = torch.from_numpy(wl.receiver_plane(nx, ny, cfg["rec_z"], cfg["rec_stride"])).cuda()
+        shot = (nx // 2, ny // 2, 10, cfg["f_peak"], -1.0, 1.0)
+        dt = 0.5 * gw.wave_cfl_dt(cfg["spacing"], max(float(true.max()), float(start.max())))
+        obs = torch.zeros((args.steps, rec.shape[0]), device="cuda")
+        s = gw.WaveSolver((nx, ny, nz), cfg["spacing"], dt, torch.from_numpy(start).cuda())
+        if args.npml:
+            s.set_cpml(args.npml, 1e-3, cfg["f_peak"])
+        g = torch.empty((nz, ny, nx), device="cuda")
+        mis = s.gradient(shot, args.steps, rec, obs, g, ckpt_every=cfg["ckpt_every"])
+        s.close()
+        out = {"case": "gradient", "steps": args.steps, "npml": args.npml, "misfit": mis,
+               "finite": bool(torch.isfinite(g).all().item())}
+    else:
+        reqs = wl.serving_requests(**dict(wl.SERVE_STREAM, n=args.serve_requests))
+        srv = gw.ShotServer(wl.SERVE_STREAM["budget_bytes"], 64)
+        tickets = []
+        for r in reqs:
+            nx, ny, nz = r["grid"]
+            vz = torch.from_numpy(wl.layered_profile(nz, r["vel_seed"])).cuda()
+            vel = vz[:, None, None].expand(nz, ny, nx).contiguous()
+            rec = torch.from_numpy(wl.receiver_plane(
+                nx, ny, min(wl.SERVE_STREAM["rec_z"], nz - 1),
+                wl.SERVE_STREAM["rec_stride"])).cuda()
+            n = min(r["nsteps"], 64)
+            tr = torch.empty((n, rec.shape[0]), device="cuda")
+            tickets.append((srv.submit(r["grid"], (10.0, 10.0, 10.0), vel,
+                                       (*r["source"], 15.0, -1.0, 1.0), n, rec, tr,
+                                       cpml=16), vel, rec, tr))
+        status = [srv.wait(t)[0] for t, *_ in tickets]
+        srv.close()
+        out = {"case": "serve_cpml", "requests": len(reqs), "failed": sum(x != 0 for x in status)}
+    print(json.dumps(out), flush=True)
+    return 0 if out.get("finite", True) and not out.get("failed") else 1
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -520,8 +591,16 @@ def main():
                     help="skip the adjoint-gradient workload")
     ap.add_argument("--no-cpml", action="store_true",
                     help="skip the CPML absorbing-layer measurement")
+    ap.add_argument("--case", default=None, choices=["sweep", "gradient", "serve_cpml"],
+                    help="run one small case for a profiler capture instead of the bench")
+    ap.add_argument("--storage", type=int, default=0, help="--case sweep: 0 FP32, 1 BF16, 2 FP16")
+    ap.add_argument("--npml", type=int, default=0, help="--case sweep, gradient: layer width")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
+    if args.case is not None:
+        if args.variant is not None:
+            os.environ["GBWAVE_VARIANT"] = str(args.variant)
+        return run_case(args)
     cfg = WORKLOADS[args.workload]
     if args.impl == "reference":
         return run_reference(args, cfg)
