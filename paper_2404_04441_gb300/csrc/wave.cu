@@ -1359,12 +1359,24 @@ __global__ void reverse_rows_kernel(const float *res, float *inj, int N,
 
 // FP64 time sum += the double-float partial hi + lo (exact in FP64), and the
 // partial restarts from zero.
-__global__ void grad_fold_kernel(double *gacc, float *ghi, float *glo, long long n) {
-  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
+// sum += hi + lo (FP64) and the partial reset, 4 points per thread and
+// iteration (n4 groups; the fields' rows are multiples of 4 elements).
+__global__ void grad_fold_kernel(double *gacc, float *ghi, float *glo, long long n4) {
+  float4 *h4 = reinterpret_cast<float4 *>(ghi), *l4 = reinterpret_cast<float4 *>(glo);
+  double2 *a2 = reinterpret_cast<double2 *>(gacc);
+  const float4 zero = make_float4(0.f, 0.f, 0.f, 0.f);
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n4;
        i += (long long)gridDim.x * blockDim.x) {
-    gacc[i] += (double)ghi[i] + (double)glo[i];
-    ghi[i] = 0.f;
-    glo[i] = 0.f;
+    const float4 h = h4[i], l = l4[i];
+    double2 a0 = a2[2 * i], a1 = a2[2 * i + 1];
+    a0.x += (double)h.x + (double)l.x;
+    a0.y += (double)h.y + (double)l.y;
+    a1.x += (double)h.z + (double)l.z;
+    a1.y += (double)h.w + (double)l.w;
+    a2[2 * i] = a0;
+    a2[2 * i + 1] = a1;
+    h4[i] = zero;
+    l4[i] = zero;
   }
 }
 
@@ -1377,17 +1389,32 @@ __global__ void grad_fold_kernel(double *gacc, float *ghi, float *glo, long long
 // for 800 steps with blocks of 32).
 constexpr int kGradFold = 128;
 
-// dJ/dm = sum / (m^2 dt^2) = sum * dt^2 / c^2 with c = m dt^2; dense output.
+// dJ/dm = sum / (m^2 dt^2) = sum * dt^2 / c^2 with c = m dt^2; dense output,
+// one row (y, z) per block iteration. 1/c^2 by Newton-Raphson for the
+// reciprocal, r <- r (2 - q r), from the FP32 reciprocal (relative error at
+// most 2^-24, so one step leaves about 2^-48, far below the FP32 rounding of
+// the result): FP64 division is a long sequence on this GPU, whose FP64 rate
+// is a small fraction of its FP32 rate. c outside the FP32 normal range
+// (not reached by a model that passes wave_create) takes the division.
 __global__ void grad_assemble_kernel(const double *gacc, const float *c,
                                      float *grad, int nx, int px,
                                      long long rows, double dt2) {
-  const long long total = rows * (long long)nx;
-  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
-       i < total; i += (long long)gridDim.x * blockDim.x) {
-    const long long r = i / nx;
-    const int x = (int)(i - r * nx);
-    const double cv = c[r * px + x];
-    grad[i] = (float)(gacc[r * px + x] * dt2 / (cv * cv));
+  for (long long r = blockIdx.x; r < rows; r += gridDim.x) {
+    const double *ga = gacc + r * px;
+    const float *cr = c + r * px;
+    float *gr = grad + r * nx;
+    for (int x = threadIdx.x; x < nx; x += blockDim.x) {
+      const double cv = cr[x];
+      const double q = cv * cv;
+      double inv;
+      if (q > 1e-36 && q < 1e36) {
+        inv = (double)__frcp_rn((float)q);
+        inv = inv * fma(-q, inv, 2.0);
+      } else {
+        inv = 1.0 / q;
+      }
+      gr[x] = (float)(ga[x] * dt2 * inv);
+    }
   }
 }
 
@@ -1641,7 +1668,7 @@ int gradient_impl(wave_ctx *c, const wave_shot *shot, int N,
       launch_cpml_adjoint_axis<2>(c, st, p1, p0, nus[2], mus[2]);
     }
     if (dsrc && k % kGradFold == 0)
-      grad_fold_kernel<<<c->sms * 4, 256, 0, st>>>(gacc, ghi, glo, (long long)fe);
+      grad_fold_kernel<<<c->sms * 4, 256, 0, st>>>(gacc, ghi, glo, (long long)(fe / 4));
     ca ^= 1;
   };
   adjoint_step(N, nullptr);  // p^N (no D^N term)
