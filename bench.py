@@ -379,7 +379,7 @@ def gradient_workload(gw, torch, cfg=wl.CFG_GRAD, npml=0):
             "grad_finite": bool(torch.isfinite(g).all().item()),
             "grad_max_abs": float(g.abs().max().item()),
             "device_memory_fields": 2 * ((n + cfg["ckpt_every"] - 1) // cfg["ckpt_every"])
-            + 2 * cfg["ckpt_every"] + 5}
+            + 2 * cfg["ckpt_every"] + 6}
 
 
 def cpml_gradient_bytes_per_step(shape, npml):

@@ -305,8 +305,9 @@ int wave_selftest_wait(int64_t limit_ns, void *stream);
  *   rec_xyz      nrec*3 int32 receivers (host or device), as wave_propagate
  *   resid        nsteps*nrec float32 dJ/dtraces (host or device)
  *   ckpt_every   steps per checkpoint segment (>= 1); device memory holds
- *                2 * ceil(nsteps/ckpt_every) + 2 * ckpt_every + 5 fields
- *                (ckpt_every + 5 when one segment covers nsteps)
+ *                2 * ceil(nsteps/ckpt_every) + 2 * ckpt_every + 6 float32
+ *                fields (ckpt_every + 8 when one segment covers nsteps; the
+ *                FP64 time sum counts as two), plus the traces
  *   grad_v2      nx*ny*nz float32 output (host or device), dense, x fastest
  *   traces       optional nsteps*nrec float32 output of the forward traces
  * FP32 storage and the default kernel variant only (else WAVE_ENOTSUP). The

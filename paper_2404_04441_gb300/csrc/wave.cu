@@ -1455,14 +1455,14 @@ int gradient_impl(wave_ctx *c, const wave_shot *shot, int N,
   StepDesc *dadj, *dfwd;
   int e;
   // two D buffers (slots) when there are several segments: the recompute of
-  // one segment runs beside the adjoint steps of the next. The recompute has
-  // fields (rbuf) and layer slabs of its own, so that the last segment's
-  // recompute can also run beside the forward's last segment.
+  // one segment runs beside the adjoint steps of the next. A segment's
+  // recompute steps its checkpoint's two fields (and layer slabs) in place:
+  // each checkpoint is read by that recompute alone, and the forward keeps
+  // its own fields, so the last segment's recompute can also run beside the
+  // forward's last segment.
   const int nslot = ncp > 1 ? 2 : 1;
-  float *rbuf[2];
   if ((e = mem.alloc(&ckpt, fb * 2 * ncp)) || (e = mem.alloc(&dbuf, fb * K * nslot)) ||
       (e = mem.alloc(&padj[0], fb)) || (e = mem.alloc(&padj[1], fb)) ||
-      (e = mem.alloc(&rbuf[0], fb)) || (e = mem.alloc(&rbuf[1], fb)) ||
       (e = mem.alloc(&trd, tn * 4)) || (e = mem.alloc(&res, tn * 4)) ||
       (e = mem.alloc(&inj, (tn + nrec) * 4)) || (e = mem.alloc(&wl, (size_t)N * 4)) ||
       (e = mem.alloc(&gacc, fe * 8)) || (e = mem.alloc(&dmis, 8)) ||
@@ -1471,10 +1471,9 @@ int gradient_impl(wave_ctx *c, const wave_shot *shot, int N,
       (e = mem.alloc(&dfwd, sizeof(StepDesc))))
     return e;
   // With the CPML layer: the memory variables psi, zeta (per axis) are saved
-  // with each checkpoint, the recompute steps them on slabs of its own (rg),
-  // and the adjoint carries its nu, mu slabs.
+  // with each checkpoint, the recompute steps the saved copies in place, and
+  // the adjoint carries its nu, mu slabs.
   const CpmlGeom &cg = c->cg;
-  CpmlGeom rg = cg;
   size_t sl[3] = {0, 0, 0};
   float *ckpt_l = nullptr, *nus[3] = {}, *mus[3] = {};
   if (c->cpml) {
@@ -1483,20 +1482,29 @@ int gradient_impl(wave_ctx *c, const wave_shot *shot, int N,
     sl[2] = 2ull * cg.npml * c->ny * c->nx;
     if ((e = mem.alloc(&ckpt_l, (sl[0] + sl[1] + sl[2]) * 2 * 4 * ncp))) return e;
     for (int ax = 0; ax < 3; ++ax)
-      if ((e = mem.alloc(&nus[ax], sl[ax] * 4)) || (e = mem.alloc(&mus[ax], sl[ax] * 4)) ||
-          (e = mem.alloc(&rg.psi[ax], sl[ax] * 4)) || (e = mem.alloc(&rg.zeta[ax], sl[ax] * 4)))
+      if ((e = mem.alloc(&nus[ax], sl[ax] * 4)) || (e = mem.alloc(&mus[ax], sl[ax] * 4)))
         return e;
   }
-  // copies the memory variables of layer slabs gg to (save) or from a
-  // checkpoint
-  auto layer_ckpt = [&](int sgm, bool save, cudaStream_t cs, const CpmlGeom &gg) -> int {
+  // the layer slabs held by a segment's checkpoint (per axis psi, then zeta)
+  auto layer_of = [&](int sgm) {
+    CpmlGeom gg = cg;
     float *q = ckpt_l + (sl[0] + sl[1] + sl[2]) * 2 * sgm;
-    for (int ax = 0; ax < 3; ++ax)
-      for (float *f : {gg.psi[ax], gg.zeta[ax]}) {
-        WAVE_TRY_CUDA(cudaMemcpyAsync(save ? q : f, save ? f : q, sl[ax] * 4,
-                                      cudaMemcpyDeviceToDevice, cs));
-        q += sl[ax];
-      }
+    for (int ax = 0; ax < 3; ++ax) {
+      gg.psi[ax] = q;
+      gg.zeta[ax] = q + sl[ax];
+      q += 2 * sl[ax];
+    }
+    return gg;
+  };
+  // copies the context's memory variables into a segment's checkpoint
+  auto layer_ckpt = [&](int sgm, cudaStream_t cs) -> int {
+    const CpmlGeom gg = layer_of(sgm);
+    for (int ax = 0; ax < 3; ++ax) {
+      WAVE_TRY_CUDA(cudaMemcpyAsync(gg.psi[ax], cg.psi[ax], sl[ax] * 4,
+                                    cudaMemcpyDeviceToDevice, cs));
+      WAVE_TRY_CUDA(cudaMemcpyAsync(gg.zeta[ax], cg.zeta[ax], sl[ax] * 4,
+                                    cudaMemcpyDeviceToDevice, cs));
+    }
     return WAVE_OK;
   };
   GradStreams gs;
@@ -1509,20 +1517,18 @@ int gradient_impl(wave_ctx *c, const wave_shot *shot, int N,
   for (const void *f : fns)
     WAVE_TRY_CUDA(cudaFuncSetAttribute(
         f, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)Cfg0::SMEM_BYTES));
-  // tensor maps of the adjoint fields and of the recompute's fields
-  CUtensorMap ahalo[2], atile[2], rhalo[2], rtile[2];
-  for (int b = 0; b < 2; ++b) {
-    const void *bufs[2] = {padj[b], rbuf[b]};
-    CUtensorMap *halos[2] = {&ahalo[b], &rhalo[b]}, *tiles[2] = {&atile[b], &rtile[b]};
-    for (int i = 0; i < 2; ++i) {
-      if ((e = make_map(halos[i], bufs[i], c, c->var.tx + 2 * c->var.halo_x,
-                        c->var.ty + 2 * kR, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, c->pxu, 4)))
-        return e;
-      if ((e = make_map(tiles[i], bufs[i], c, c->var.tx, c->var.ty,
-                        CU_TENSOR_MAP_DATA_TYPE_FLOAT32, c->pxu, 4)))
-        return e;
-    }
-  }
+  // tensor maps (halo and tile boxes) of a field
+  auto field_maps = [&](const void *f, CUtensorMap *halo, CUtensorMap *tile) -> int {
+    int me = make_map(halo, f, c, c->var.tx + 2 * c->var.halo_x, c->var.ty + 2 * kR,
+                      CU_TENSOR_MAP_DATA_TYPE_FLOAT32, c->pxu, 4);
+    if (!me)
+      me = make_map(tile, f, c, c->var.tx, c->var.ty, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, c->pxu,
+                    4);
+    return me;
+  };
+  CUtensorMap ahalo[2], atile[2];
+  for (int b = 0; b < 2; ++b)
+    if ((e = field_maps(padj[b], &ahalo[b], &atile[b]))) return e;
 
   // Layer plans of the recompute (D stored) and adjoint sweeps. Preroll
   // weights timed on 256^3 x 800 steps, checkpoint every 40 (wave_gradient,
@@ -1562,12 +1568,14 @@ int gradient_impl(wave_ctx *c, const wave_shot *shot, int N,
   auto recompute = [&](int sgm, cudaStream_t rs) -> int {
     const int s0 = sgm * K, s1 = std::min(N, s0 + K);
     float *dslot = dslot_of(sgm);
-    WAVE_TRY_CUDA(cudaMemcpyAsync(rbuf[0], ckpt + (size_t)2 * sgm * fe, fb,
-                                  cudaMemcpyDeviceToDevice, rs));
-    WAVE_TRY_CUDA(cudaMemcpyAsync(rbuf[1], ckpt + (size_t)(2 * sgm + 1) * fe, fb,
-                                  cudaMemcpyDeviceToDevice, rs));
-    int le;
-    if (c->cpml && (le = layer_ckpt(sgm, false, rs, rg))) return le;
+    // the checkpoint's fields: rbuf[0] = u^{s0}, rbuf[1] = u^{s0-1}
+    float *rbuf[2] = {ckpt + (size_t)2 * sgm * fe, ckpt + (size_t)(2 * sgm + 1) * fe};
+    CUtensorMap rhalo[2], rtile[2];
+    for (int b = 0; b < 2; ++b) {
+      const int me = field_maps(rbuf[b], &rhalo[b], &rtile[b]);
+      if (me) return me;
+    }
+    const CpmlGeom rg = c->cpml ? layer_of(sgm) : cg;
     int cur = 0;
     for (int n = s0; n < s1; ++n) {
       SweepArgs a = args_d;
@@ -1600,7 +1608,7 @@ int gradient_impl(wave_ctx *c, const wave_shot *shot, int N,
     WAVE_TRY_CUDA(cudaMemcpyAsync(ckpt + (size_t)(2 * sgm + 1) * fe,
                                   c->buf[c->cur ^ 1], fb,
                                   cudaMemcpyDeviceToDevice, st));
-    if (c->cpml && (e = layer_ckpt(sgm, true, st, cg))) return e;
+    if (c->cpml && (e = layer_ckpt(sgm, st))) return e;
     if (sgm == ncp - 1 && nslot == 2) {
       WAVE_TRY_CUDA(cudaEventRecord(gs.start, st));
       WAVE_TRY_CUDA(cudaStreamWaitEvent(gs.rs, gs.start, 0));
