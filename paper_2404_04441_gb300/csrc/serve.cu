@@ -24,8 +24,8 @@ namespace {
 // single-grid defaults: FP32 32 x 16 tiles of 4 warps, 16-bit on the tensor
 // cores with 64 x 16 tiles of 8 warps.
 using ServeF32 = SweepCfg<32, 16, 1, 4, 4>;
-using ServeB16 = TcCfg<64, 4, 2, __nv_bfloat16>;
-using ServeH16 = TcCfg<64, 4, 2, __half>;
+using ServeB16 = TcCfg<64, 4, 2, __nv_bfloat16, 9>;
+using ServeH16 = TcCfg<64, 4, 2, __half, 9>;
 constexpr int kKinds = 3;
 constexpr int kMaxGroup = 16;     // batch steps between two engine checks
 constexpr int kLayerPlanes = 256; // target z planes per CTA for batched shots

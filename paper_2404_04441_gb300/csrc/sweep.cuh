@@ -249,19 +249,24 @@ struct SweepCfg {
 // (112, 176 or 304 bytes: the 8 rows of an ldmatrix land on 8 disjoint
 // groups of 4 banks), u_prev and v^2 dt^2 rows of TX + 8 (the extra columns
 // are the next tile's, read from L2).
-template <int TX_, int PF_, int MINB_, class T_>
+// RING_ = 9: the u_prev / v^2 dt^2 ring and the barriers are 9 deep like
+// the u ring (the plane loop's unroll), so every slot and barrier parity of
+// the loop is a compile-time constant instead of a division by PF + 1 per
+// plane; it needs the shared memory of 2 CTAs per SM or fewer.
+template <int TX_, int PF_, int MINB_, class T_, int RING_ = 0>
 struct TcCfg {
   using T = T_;
   static_assert(sizeof(T) == 2, "16-bit storage only");
   static_assert(TX_ == 32 || TX_ == 64 || TX_ == 128, "tile width");
+  static_assert(RING_ == 0 || RING_ == 9, "ring depth: PF + 1, or 9");
   static constexpr bool kScaled = true;
   static constexpr bool kTensor = true;
   static constexpr int TX = TX_, TY = 16, VY = 1, PF = PF_, MINB = MINB_;
   static constexpr int HX = Elem<T>::kHaloX;  // 8: 16-byte aligned box start
   static constexpr int THREADS = 4 * TX;      // one warp per 8 columns
   static constexpr int SU = PF + 5;
-  static constexpr int SP = PF + 1;
-  static constexpr int NB = PF + 1;
+  static constexpr int SP = RING_ ? RING_ : PF + 1;
+  static constexpr int NB = RING_ ? RING_ : PF + 1;
   static constexpr int UW = TX + 24;      // u slot row (elements): x0-8 .. x0+TX+15
   static constexpr int UH = TY + 2 * kR;
   static constexpr int PW = TX + 8;       // u_prev / v^2 dt^2 slot row
@@ -950,22 +955,25 @@ __device__ __forceinline__ void sweep_cta_tc(const CUtensorMap *tm_u,
   __syncthreads();
 
   // Stage t brings u plane zb-4+t (slot t % 9) and, once t >= 8, u_prev and
-  // v^2 dt^2 of plane zb-8+t (the plane computed at iteration t).
-  auto issue = [&](int t) {
-    uint64_t *bar = &bars[t % C::NB];
+  // v^2 dt^2 of plane zb-8+t (the plane computed at iteration t). slot:
+  // t % 9, passed as a constant from the unrolled loop (the ring slots and
+  // barriers are t % 9 when SP == NB == 9).
+  auto issue = [&](int t, int slot9) {
+    const int bslot = C::NB == 9 ? slot9 : t % C::NB;
+    const int pslot = C::SP == 9 ? slot9 : t % C::SP;
+    uint64_t *bar = &bars[bslot];
     const int j = zb - 2 * kR + t;
     const bool full = j >= zb;
     mbar_arrive_expect_tx(bar,
                           C::U_BYTES + (full ? C::UP_BYTES + C::C_BYTES : 0));
-    tma_load_3d(su + (t % C::SU) * C::U_SLOT, tm_u, bar, x0 - C::HX, y0 - kR,
-                j + kR);
+    tma_load_3d(su + slot9 * C::U_SLOT, tm_u, bar, x0 - C::HX, y0 - kR, j + kR);
     if (full) {
-      tma_load_3d(sp + (t % C::SP) * C::P_SLOT, tm_up, bar, x0, y0, j);
-      tma_load_3d(sc + (t % C::SP) * C::P_SLOT, tm_c, bar, x0, y0, j);
+      tma_load_3d(sp + pslot * C::P_SLOT, tm_up, bar, x0, y0, j);
+      tma_load_3d(sc + pslot * C::P_SLOT, tm_c, bar, x0, y0, j);
     }
   };
   if (tid == 0)
-    for (int t = 0; t < C::PF && t < NS; ++t) issue(t);
+    for (int t = 0; t < C::PF && t < NS; ++t) issue(t, t);
 
   // q[k]: u of the thread's points (row g: x, y; row g+8: z, w)
   float4 q[9];
@@ -973,7 +981,8 @@ __device__ __forceinline__ void sweep_cta_tc(const CUtensorMap *tm_u,
   for (int k = 0; k < 9; ++k) q[k] = make_float4(0.f, 0.f, 0.f, 0.f);
 
   int s = 0;
-  for (int s0 = 0; s0 < NS; s0 += 9) {
+  uint32_t par9 = 0;  // barrier parity of this round of 9 stages (NB == 9)
+  for (int s0 = 0; s0 < NS; s0 += 9, par9 ^= 1u) {
 #pragma unroll
     for (int p = 0; p < 9; ++p) {
       s = s0 + p;
@@ -982,9 +991,10 @@ __device__ __forceinline__ void sweep_cta_tc(const CUtensorMap *tm_u,
       // uniform verdict, so a timeout leaves the loop everywhere) and every
       // thread is done with plane s-1, whose slots the next issue reuses.
       const bool ok =
-          mbar_wait_bounded(&bars[s % C::NB], (s / C::NB) & 1, kWaitLimitNs);
+          C::NB == 9 ? mbar_wait_bounded(&bars[p], par9, kWaitLimitNs)
+                     : mbar_wait_bounded(&bars[s % C::NB], (s / C::NB) & 1, kWaitLimitNs);
       if (__syncthreads_or(!ok)) goto wait_failed;
-      if (tid == 0 && s + C::PF < NS) issue(s + C::PF);
+      if (tid == 0 && s + C::PF < NS) issue(s + C::PF, (p + C::PF) % 9);
       {
         const T *uf = su + p * C::U_SLOT;  // SU == 9: slot of stage s is s % 9
         const float2 fa = pair_to_f32<T>(*reinterpret_cast<const unsigned *>(uf + ua));
@@ -994,8 +1004,9 @@ __device__ __forceinline__ void sweep_cta_tc(const CUtensorMap *tm_u,
       const int j = zb - 2 * kR + s;
       if (j >= zb) {
         const T *uc = su + ((p + 5) % 9) * C::U_SLOT;  // plane j
-        const T *pp = sp + (s % C::SP) * C::P_SLOT;
-        const float *pc = sc + (s % C::SP) * C::P_SLOT;
+        const int pslot = C::SP == 9 ? p : s % C::SP;
+        const T *pp = sp + pslot * C::P_SLOT;
+        const float *pc = sc + pslot * C::P_SLOT;
         // x and y parts on the tensor cores (integer weights, stored units)
         float dyv[4] = {0.f, 0.f, 0.f, 0.f}, dxv[4] = {0.f, 0.f, 0.f, 0.f};
         {

@@ -40,12 +40,12 @@ using Cfg3 = SweepCfg<32, 16, 1, 3, 4>;
 //  496 / 495, 128 x 16 with 1 CTA/SM 462 / 454. Forcing more CTAs per SM
 //  spilled registers and was slower (32 x 16 with 5: 439 / 401; 64 x 16
 //  with 3: 453 / 374), so those forms are not built.
-using CfgBT64 = TcCfg<64, 4, 2, __nv_bfloat16>;
-using CfgHT64 = TcCfg<64, 4, 2, __half>;
+using CfgBT64 = TcCfg<64, 4, 2, __nv_bfloat16, 9>;
+using CfgHT64 = TcCfg<64, 4, 2, __half, 9>;
 using CfgBT = TcCfg<32, 4, 4, __nv_bfloat16>;
 using CfgHT = TcCfg<32, 4, 4, __half>;
-using CfgBT128 = TcCfg<128, 4, 1, __nv_bfloat16>;
-using CfgHT128 = TcCfg<128, 4, 1, __half>;
+using CfgBT128 = TcCfg<128, 4, 1, __nv_bfloat16, 9>;
+using CfgHT128 = TcCfg<128, 4, 1, __half, 9>;
 //  16-bit on the CUDA cores (the stencil's pair sums as mixed-precision
 //  adds): 64-wide tiles, so a half-warp reads one contiguous 128-byte row of
 //  16-bit elements (no shared-memory bank conflicts). 478 / 487 Gpts/s.
