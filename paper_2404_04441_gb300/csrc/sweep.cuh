@@ -942,6 +942,9 @@ __device__ __forceinline__ void sweep_cta_tc(const CUtensorMap *tm_u,
   const size_t plane_stride = (size_t)a.ny * a.px;
   const size_t oa = (size_t)(y0 + g) * a.px + (x0 + xt);
   const size_t ob = oa + 8 * (size_t)a.px;
+  // the thread's two output rows at plane zb, advanced one plane per plane
+  T *outa = reinterpret_cast<T *>(unext) + (size_t)zb * plane_stride + oa;
+  T *outb = reinterpret_cast<T *>(unext) + (size_t)zb * plane_stride + ob;
   const bool in_x = x0 + xt < a.px;
   const bool wa = in_x && y0 + g < a.ny, wb = in_x && y0 + g + 8 < a.ny;
 
@@ -981,6 +984,7 @@ __device__ __forceinline__ void sweep_cta_tc(const CUtensorMap *tm_u,
   for (int k = 0; k < 9; ++k) q[k] = make_float4(0.f, 0.f, 0.f, 0.f);
 
   int s = 0;
+  const int ns_issue = NS - C::PF;  // stages s below it issue stage s + PF
   uint32_t par9 = 0;  // barrier parity of this round of 9 stages (NB == 9)
   for (int s0 = 0; s0 < NS; s0 += 9, par9 ^= 1u) {
 #pragma unroll
@@ -994,7 +998,7 @@ __device__ __forceinline__ void sweep_cta_tc(const CUtensorMap *tm_u,
           C::NB == 9 ? mbar_wait_bounded(&bars[p], par9, kWaitLimitNs)
                      : mbar_wait_bounded(&bars[s % C::NB], (s / C::NB) & 1, kWaitLimitNs);
       if (__syncthreads_or(!ok)) goto wait_failed;
-      if (tid == 0 && s + C::PF < NS) issue(s + C::PF, (p + C::PF) % 9);
+      if (tid == 0 && s < ns_issue) issue(s + C::PF, (p + C::PF) % 9);
       {
         const T *uf = su + p * C::U_SLOT;  // SU == 9: slot of stage s is s % 9
         const float2 fa = pair_to_f32<T>(*reinterpret_cast<const unsigned *>(uf + ua));
@@ -1060,11 +1064,10 @@ __device__ __forceinline__ void sweep_cta_tc(const CUtensorMap *tm_u,
         }
         vmax_out = fmaxf(vmax_out, fmaxf(fmaxf(fabsf(ol.x), fabsf(ol.y)),
                                          fmaxf(fabsf(oh.x), fabsf(oh.y))));
-        {
-          T *out = reinterpret_cast<T *>(unext) + (size_t)j * plane_stride;
-          if (wa) __stcs(reinterpret_cast<unsigned *>(out + oa), pack_pair<T>(ol.x, ol.y));
-          if (wb) __stcs(reinterpret_cast<unsigned *>(out + ob), pack_pair<T>(oh.x, oh.y));
-        }
+        if (wa) __stcs(reinterpret_cast<unsigned *>(outa), pack_pair<T>(ol.x, ol.y));
+        if (wb) __stcs(reinterpret_cast<unsigned *>(outb), pack_pair<T>(oh.x, oh.y));
+        outa += plane_stride;
+        outb += plane_stride;
         // Receivers on this plane: each thread records the entries at its
         // own points (no staging, so no barrier across the warps).
         if (j == rz) {
