@@ -866,6 +866,7 @@ __device__ __forceinline__ void sweep_cta_tc(const CUtensorMap *tm_u,
   const bool src_here = d->src_active && sx >= 0 && sx < C::TX && sy >= 0 &&
                         sy < C::TY && sz >= zb && sz < ze;
   float wsrc = src_here ? d->wavelet[n] : 0.f;
+  const int src_j = src_here ? sz : -1;  // plane of the source in this CTA
   int rcur = 0, rend = 0;
   const int4 *rec = d->rec;
   if (nrec > 0) {
@@ -1006,7 +1007,9 @@ __device__ __forceinline__ void sweep_cta_tc(const CUtensorMap *tm_u,
         q[p] = make_float4(fa.x, fa.y, fb.x, fb.y);
       }
       const int j = zb - 2 * kR + s;
-      if (j >= zb) {
+      // j >= zb, i.e. s >= 8: every stage after the first 8 (s0 is a
+      // multiple of 9, so only the first round holds the queue's fill)
+      if (p == 8 || s0 != 0) {
         const T *uc = su + ((p + 5) % 9) * C::U_SLOT;  // plane j
         const int pslot = C::SP == 9 ? p : s % C::SP;
         const T *pp = sp + pslot * C::P_SLOT;
@@ -1051,7 +1054,7 @@ __device__ __forceinline__ void sweep_cta_tc(const CUtensorMap *tm_u,
                                __fmul2_rn(s2v, make_float2(-upa.x, -upa.y)));
         float2 oh = __ffma2_rn(s1v, __ffma2_rn(cvh, hi, __fadd2_rn(uh, uh)),
                                __fmul2_rn(s2v, make_float2(-upb.x, -upb.y)));
-        if (src_here && j == sz) {
+        if (j == src_j) {
           const int e = sx - xt;
           if (sy == g) {
             if (e == 0) ol.x = fmaf(cvl.x, wsrc, ol.x);
