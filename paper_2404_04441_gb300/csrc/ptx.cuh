@@ -49,18 +49,37 @@ __device__ __forceinline__ uint64_t global_timer_ns() {
   return t;
 }
 
-// Wait for the barrier phase with the given parity. Gives up after about
-// limit_ns of wall time (or a fixed iteration cap) and returns false.
-__device__ __forceinline__ bool mbar_wait_bounded(uint64_t *bar,
-                                                  uint32_t parity,
-                                                  uint64_t limit_ns) {
-  if (mbar_try_wait(bar, parity)) return true;
+// As mbar_try_wait, with the barrier's shared-space address.
+__device__ __forceinline__ bool mbar_try_wait_s(uint32_t bar, uint32_t parity) {
+  uint32_t ok;
+  asm volatile(
+      "{\n\t.reg .pred p;\n\t"
+      "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+      "selp.u32 %0, 1, 0, p;\n\t}"
+      : "=r"(ok)
+      : "r"(bar), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+
+// Wait for the barrier phase with the given parity (the barrier by its
+// shared-space address). Gives up after about limit_ns of wall time (or a
+// fixed iteration cap) and returns false.
+__device__ __forceinline__ bool mbar_wait_bounded_s(uint32_t bar, uint32_t parity,
+                                                    uint64_t limit_ns) {
+  if (mbar_try_wait_s(bar, parity)) return true;
   const uint64_t t0 = global_timer_ns();
   for (uint32_t i = 1; i < (1u << 28); ++i) {
-    if (mbar_try_wait(bar, parity)) return true;
+    if (mbar_try_wait_s(bar, parity)) return true;
     if ((i & 1023u) == 0 && global_timer_ns() - t0 > limit_ns) return false;
   }
   return false;
+}
+
+__device__ __forceinline__ bool mbar_wait_bounded(uint64_t *bar,
+                                                  uint32_t parity,
+                                                  uint64_t limit_ns) {
+  return mbar_wait_bounded_s(smem_addr(bar), parity, limit_ns);
 }
 
 // 3D tiled TMA load of one box into shared memory; completion is signalled

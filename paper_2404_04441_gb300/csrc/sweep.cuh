@@ -934,6 +934,12 @@ __device__ __forceinline__ void sweep_cta_tc(const CUtensorMap *tm_u,
   const int off_x0 = ((lane & 7) + 8 * (lj & 1) + kR) * C::UW + 8 * warp +
                      8 * (lj >> 1);               // window 0: block column - 8
   const int off_x1 = off_x0 + C::HX;              // window 1: block column
+  // shared-space addresses: the u ring's ldmatrix rows of this lane (slot 0)
+  // and the barriers, so that a plane's addresses are these plus constants
+  const uint32_t su_s = smem_addr(su), bars_s = smem_addr(bars);
+  constexpr uint32_t es = sizeof(T);
+  const uint32_t ly_s = su_s + es * off_y, lx0_s = su_s + es * off_x0,
+                 lx1_s = su_s + es * off_x1;
   // the thread's points in a u slot and in a tile slot (elements)
   const int ua = (g + kR) * C::UW + C::HX + xt, ub = ua + 8 * C::UW;
   const int pa = g * C::PW + xt, pb = pa + 8 * C::PW;
@@ -996,7 +1002,7 @@ __device__ __forceinline__ void sweep_cta_tc(const CUtensorMap *tm_u,
       // uniform verdict, so a timeout leaves the loop everywhere) and every
       // thread is done with plane s-1, whose slots the next issue reuses.
       const bool ok =
-          C::NB == 9 ? mbar_wait_bounded(&bars[p], par9, kWaitLimitNs)
+          C::NB == 9 ? mbar_wait_bounded_s(bars_s + 8u * p, par9, kWaitLimitNs)
                      : mbar_wait_bounded(&bars[s % C::NB], (s / C::NB) & 1, kWaitLimitNs);
       if (__syncthreads_or(!ok)) goto wait_failed;
       if (tid == 0 && s < ns_issue) issue(s + C::PF, (p + C::PF) % 9);
@@ -1018,12 +1024,13 @@ __device__ __forceinline__ void sweep_cta_tc(const CUtensorMap *tm_u,
         float dyv[4] = {0.f, 0.f, 0.f, 0.f}, dxv[4] = {0.f, 0.f, 0.f, 0.f};
         {
           unsigned r[4];
-          ldsm_x4_trans(r, smem_addr(uc + off_y));
+          const uint32_t cofs = ((p + 5) % 9) * C::U_BYTES;  // plane j's slot
+          ldsm_x4_trans(r, ly_s + cofs);
           mma_16816<T>(dyv, ya[0], r[0], r[1]);
           mma_16816<T>(dyv, ya[1], r[2], r[3]);
-          ldsm_x4(r, smem_addr(uc + off_x0));
+          ldsm_x4(r, lx0_s + cofs);
           mma_16816<T>(dxv, r, xbw[0][0], xbw[0][1]);
-          ldsm_x4(r, smem_addr(uc + off_x1));
+          ldsm_x4(r, lx1_s + cofs);
           mma_16816<T>(dxv, r, xbw[1][0], xbw[1][1]);
         }
         const float2 upa = pair_to_f32<T>(*reinterpret_cast<const unsigned *>(pp + pa));
