@@ -287,7 +287,7 @@ int wave_selftest_wait(int64_t limit_ns, void *stream);
  * with the residuals injected at the receivers, on the same sweep kernel;
  * the forward fields come from checkpoints every ckpt_every steps, one
  * segment recomputed at a time; the time sum is accumulated in FP64 (each
- * block of 128 steps, counted from step 0, is first summed as an FP32
+ * block of 256 steps, counted from step 0, is first summed as an FP32
  * double-float pair of about 48 significant bits, then added to the FP64
  * sum).
  * With the CPML layer (wave_set_cpml) the forward map includes the memory

@@ -1382,38 +1382,37 @@ __global__ void grad_fold_kernel(double *gacc, float *ghi, float *glo, long long
 
 // Steps per FP64 fold of the gradient's time sum, counted in absolute steps
 // so the sum's rounding does not depend on the checkpoint interval. The
-// double-float partial keeps about 48 bits over a block (its lo word rounds
-// at 2^-24 of itself, about 2^-48 of the sum, per step), so a block of 128
-// steps loses nothing an FP64 sum would keep; each fold reads and writes 32
-// bytes per point, so fewer folds save bandwidth (25 folds of 132 us at 256^3
-// for 800 steps with blocks of 32).
-constexpr int kGradFold = 128;
+// double-float partial carries the rounding errors of its hi word in its lo
+// word, which after k steps is at most about k 2^-24 of the sum and rounds at
+// 2^-24 of itself: over a block of B steps at most about B^2 2^-49 of the
+// sum, 2^-33 for B = 256, far below the FP32 rounding of the gradient (2^-24)
+// and usually much less; each fold reads and writes 32 bytes per point, so
+// fewer folds save bandwidth (25 folds of 132 us at 256^3 for 800 steps with
+// blocks of 32, 3 with blocks of 256).
+constexpr int kGradFold = 256;
 
 // dJ/dm = sum / (m^2 dt^2) = sum * dt^2 / c^2 with c = m dt^2; dense output,
-// one row (y, z) per block iteration. 1/c^2 by Newton-Raphson for the
-// reciprocal, r <- r (2 - q r), from the FP32 reciprocal (relative error at
-// most 2^-24, so one step leaves about 2^-48, far below the FP32 rounding of
-// the result): FP64 division is a long sequence on this GPU, whose FP64 rate
-// is a small fraction of its FP32 rate. c outside the FP32 normal range
-// (not reached by a model that passes wave_create) takes the division.
+// one row (y, z) per block iteration. The FP64 time sum is rounded to FP32
+// once and scaled in FP32 by dt^2 / c^2 (a few FP32 roundings, within 2 ulp
+// of the FP32 output): this GPU's FP64 rate is a small fraction of its FP32
+// rate, and FP64 products and a division per point made this kernel take
+// 738 us at 256^3. c^2 outside the FP32 normal range (not reached by a
+// model that passes wave_create) is scaled in FP64.
 __global__ void grad_assemble_kernel(const double *gacc, const float *c,
                                      float *grad, int nx, int px,
                                      long long rows, double dt2) {
+  const float dt2f = (float)dt2;
   for (long long r = blockIdx.x; r < rows; r += gridDim.x) {
     const double *ga = gacc + r * px;
     const float *cr = c + r * px;
     float *gr = grad + r * nx;
     for (int x = threadIdx.x; x < nx; x += blockDim.x) {
-      const double cv = cr[x];
-      const double q = cv * cv;
-      double inv;
-      if (q > 1e-36 && q < 1e36) {
-        inv = (double)__frcp_rn((float)q);
-        inv = inv * fma(-q, inv, 2.0);
-      } else {
-        inv = 1.0 / q;
-      }
-      gr[x] = (float)(ga[x] * dt2 * inv);
+      const float cv = cr[x];
+      const float q = cv * cv;
+      if (q > 1e-30f && q < 1e30f)
+        gr[x] = (float)ga[x] * (dt2f * __frcp_rn(q));
+      else
+        gr[x] = (float)(ga[x] * dt2 / ((double)cv * (double)cv));
     }
   }
 }
