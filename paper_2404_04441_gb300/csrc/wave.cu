@@ -1358,9 +1358,8 @@ __global__ void reverse_rows_kernel(const float *res, float *inj, int N,
 }
 
 // FP64 time sum += the double-float partial hi + lo (exact in FP64), and the
-// partial restarts from zero.
-// sum += hi + lo (FP64) and the partial reset, 4 points per thread and
-// iteration (n4 groups; the fields' rows are multiples of 4 elements).
+// partial restarts from zero; 4 points per thread and iteration (n4 groups:
+// the fields' rows are multiples of 4 elements).
 __global__ void grad_fold_kernel(double *gacc, float *ghi, float *glo, long long n4) {
   float4 *h4 = reinterpret_cast<float4 *>(ghi), *l4 = reinterpret_cast<float4 *>(glo);
   double2 *a2 = reinterpret_cast<double2 *>(gacc);
@@ -1395,9 +1394,10 @@ constexpr int kGradFold = 256;
 // one row (y, z) per block iteration. The FP64 time sum is rounded to FP32
 // once and scaled in FP32 by dt^2 / c^2 (a few FP32 roundings, within 2 ulp
 // of the FP32 output): this GPU's FP64 rate is a small fraction of its FP32
-// rate, and FP64 products and a division per point made this kernel take
-// 738 us at 256^3. c^2 outside the FP32 normal range (not reached by a
-// model that passes wave_create) is scaled in FP64.
+// rate, and with FP64 products, an FP64 division and a 64-bit integer
+// division (of the flat index by nx) per point this kernel took 738 us at
+// 256^3. c^2 outside the FP32 normal range (not reached by a model that
+// passes wave_create) is scaled in FP64.
 __global__ void grad_assemble_kernel(const double *gacc, const float *c,
                                      float *grad, int nx, int px,
                                      long long rows, double dt2) {
