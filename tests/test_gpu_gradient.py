@@ -84,6 +84,30 @@ def test_checkpoint_interval_does_not_change_the_gradient(wave_lib, oracle_mod):
         assert np.array_equal(got[1], ref[1])
 
 
+def test_long_run_across_fold_boundaries(wave_lib, oracle_mod):
+    """300 steps: the double-float partial of the time sum is folded into the
+    FP64 sum at absolute step 256 and at the end. The gradient matches the
+    oracle adjoint within the bar, and a checkpoint every 7 steps gives it
+    bitwise equal to one segment (the fold points do not depend on the
+    interval)."""
+    cfg = dict(wl.CFG_GRAD_SMALL, shape=(24, 22, 20), nsteps=300)
+    true, start, rec, shot = _case(cfg)
+    dt = _dt(wave_lib, cfg, true, start)
+    n = cfg["nsteps"]
+    _, _, obs = oracle_mod.propagate(true, cfg["spacing"], dt, n, source=shot, receivers=rec)
+    obs = obs.astype(np.float32)
+    mis, g, tr = _gpu_gradient(wave_lib, start, cfg, dt, shot, rec, obs, 7)
+    mis1, g1, _ = _gpu_gradient(wave_lib, start, cfg, dt, shot, rec, obs, n)
+    assert np.array_equal(g, g1)
+    assert mis == pytest.approx(mis1, rel=1e-12)
+    _, _, otr = oracle_mod.propagate(start, cfg["spacing"], dt, n, source=shot, receivers=rec)
+    og = oracle_mod.gradient(start, cfg["spacing"], dt, n, shot, rec, otr - obs)
+    assert rel_l2(tr, otr) <= 1e-5 * n / 60
+    err = rel_l2(g, og)
+    print("\n300-step gradient rel-L2 vs oracle adjoint: %.3e" % err)
+    assert err <= 2e-4
+
+
 def test_directional_derivative_matches_finite_differences(wave_lib, oracle_mod):
     """<g, dm> against (J(m + e dm) - J(m - e dm)) / 2e with the GPU misfit
     (FP32 fields: step e = 1e-3 relative keeps rounding ~1e-4 and
